@@ -1,0 +1,165 @@
+/*
+ * flb.h -- C ABI of the GB300 fluctuating lattice Boltzmann library (libflb.so).
+ *
+ * The method (Kaehler & Wagner, "Cross Correlators and Galilean Invariance in
+ * Fluctuating Ideal Gas Lattice Boltzmann Simulations"): the lattice Boltzmann
+ * equation with a diagonal collision in the Hermite-orthonormal moment basis
+ * (Eqs. 1, 3-5), Gaussian noise with the fluctuation-dissipation amplitude of
+ * Eq. 8 on every non-conserved moment (stress and ghost moments, Sec. 2), and
+ * the equal-time structure factors and cross correlators of Eqs. 11-12.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FLB_OK (0) or a negative FLB_E* code; flb_last_error()
+ *     returns a thread-local message describing the last failure.  No C++
+ *     exception crosses this boundary.
+ *   - Device memory is owned by the caller (a single workspace block, sized by
+ *     flb_workspace_bytes); the library never calls cudaMalloc.  The opaque
+ *     flb_ctx is host memory owned by the library (flb_destroy frees it).
+ *   - Work is issued on the caller's CUDA stream and is stream-ordered;
+ *     asynchronous kernel errors surface at the next flb_sync / flb_get_*.
+ *   - An invalid argument returns FLB_EINVAL before any work is issued and
+ *     leaves the context unchanged.
+ *   - Host arrays are plain FP64 in C order; a lattice field is [ny][nx]
+ *     (x fastest), populations are [q][ny][nx].
+ */
+#ifndef FLB_H
+#define FLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FLB_OK         0
+#define FLB_EINVAL    (-1)  /* invalid argument or unsupported configuration */
+#define FLB_ENOMEM    (-2)  /* workspace smaller than flb_workspace_bytes     */
+#define FLB_ECUDA     (-3)  /* CUDA launch or runtime error                   */
+#define FLB_EUNSTABLE (-4)  /* non-finite state detected                      */
+#define FLB_ETIMEOUT  (-5)  /* a bounded device wait gave up                  */
+#define FLB_ESTATE    (-6)  /* call not valid in the context's current state  */
+
+/* ---- lattices and storage precisions --------------------------------- */
+#define FLB_D1Q3 1          /* v = (0, +1, -1); moments rho, sqrt3 j, (3v^2-1)/sqrt2 */
+#define FLB_D2Q9 2          /* Sec. 3 velocity set and the moment matrix of Eq. 9   */
+#define FLB_FP64     0      /* full f_i in FP64, all arithmetic FP64                 */
+#define FLB_FP32_DEV 1      /* f_i - w_i rho0 stored and processed in FP32;
+                               correlators accumulated in FP64                      */
+
+/* ---- sampled fields (bit f of flb_replica.field_mask) -----------------
+ * f = 0..q-1 : moment M^a - M^{a,0}(rho0, u0)   (M^0 = rho, M^1,2 = sqrt3 j)
+ * f = 9, 10  : u_x - u0_x, u_y - u0_y           (u = j / rho)
+ * Fields are taken from the pre-collision (post-streaming) state.            */
+#define FLB_FIELD_UX 9
+#define FLB_FIELD_UY 10
+#define FLB_MAX_FIELDS 11
+
+/* One independent periodic lattice (a replica).  Several replicas with the
+ * same lattice type and precision can run in one context (batched launch). */
+typedef struct {
+  int32_t  lattice;     /* FLB_D1Q3 or FLB_D2Q9                                  */
+  int32_t  nx, ny;      /* lattice size; ny = 1 for D1Q3.  nx even.  Sampling
+                           needs powers of two: 2 <= nx <= 16384, ny <= 16384  */
+  double   tau[9];      /* relaxation time per moment a (Eq. 5); entries of the
+                           conserved moments are ignored, the others must be > 1/2 */
+  double   rho0;        /* mean density rho-bar (> 0)                            */
+  double   kT;          /* temperature; mu = 3 kT scales the noise of Eq. 8      */
+  double   u0[2];       /* mean velocity of the initial state                    */
+  uint64_t seed;        /* Philox key                                            */
+  uint32_t stream;      /* Philox counter word 3 (replica stream id)             */
+  uint32_t noise_mask;  /* bit a = noise on moment a; bits of conserved moments
+                           must be 0.  All non-conserved bits = the scheme of
+                           Sec. 2; D2Q9 without bits 6..8 = the Ladd scheme    */
+  uint32_t init_mode;   /* 0: f^0(rho0, u0) on every site; 1: thermal (moment
+                           fluctuations N(0, mu rho0), mean of rho and j removed) */
+  uint32_t field_mask;  /* fields to sample (see above); 0 = no sampling         */
+} flb_replica;
+
+typedef struct flb_ctx flb_ctx;
+
+/* Bytes of device workspace a context needs (alignment 256 B).
+ * precision: FLB_FP64 / FLB_FP32_DEV.  reps: n_replicas host descriptors. */
+int flb_workspace_bytes(int precision, const flb_replica* reps, int n_replicas,
+                        size_t* bytes_out);
+
+/* Create a context on the current CUDA device.  dev_workspace: caller-owned
+ * device memory of at least flb_workspace_bytes bytes, 256-B aligned, kept
+ * alive until flb_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default).
+ * Initialises every replica's populations (init_mode) and zeroes the
+ * correlator sums; global step counter = 0. */
+int flb_create(int precision, const flb_replica* reps, int n_replicas,
+               void* dev_workspace, size_t workspace_bytes, void* cuda_stream,
+               flb_ctx** out);
+
+/* Advance every replica by n_steps (Eq. 1 with the collision of Eq. 5 and the
+ * noise of Eq. 8).  A step whose global index t satisfies sample_every != 0 and
+ * t % sample_every == 0 first samples the fields of its pre-collision state and
+ * adds X_a(k) X_b(k)^* of every field pair to FP64 sums (Eqs. 11-12).
+ * Asynchronous: returns after issuing the work. */
+int flb_run(flb_ctx* ctx, uint64_t n_steps, uint32_t sample_every);
+
+/* Wait for the context's stream and report any asynchronous error, including a
+ * non-finite state detected by the conservation check (FLB_EUNSTABLE). */
+int flb_sync(flb_ctx* ctx);
+
+/* Zero the correlator sums, the k = 0 means and the sample count. */
+int flb_reset_stats(flb_ctx* ctx);
+
+/* Normalised correlator C_ab(k) = N^ab (<X_a(k) X_b(k)^*> - delta_k0 <X_a(0)><X_b(0)>^*)
+ * on the full grid: host_out[(ky*nx + kx)*2 + {0,1}] = {Re, Im}, with
+ * k = 2 pi (kx/nx, ky/ny).  N^ab = 1/(V sqrt(var_a var_b)), var = mu rho0 for a
+ * moment field, kT/rho0 for a velocity field (both fields must be sampled).
+ * n_samples (may be NULL) receives the number of samples.  Synchronises. */
+int flb_get_correlator(flb_ctx* ctx, int replica, int field_a, int field_b,
+                       double* host_out, uint64_t* n_samples);
+
+/* Copy the stored (post-collision) populations f_i of a replica to / from host
+ * FP64 [q][ny][nx].  For FLB_FP32_DEV they are converted from / to f - w rho0
+ * in FP32.  Synchronises. */
+int flb_get_populations(flb_ctx* ctx, int replica, double* host_out);
+int flb_set_populations(flb_ctx* ctx, int replica, const double* host_in);
+
+/* FP64 sums over the lattice of rho, j_x, j_y (j_y = 0 for D1Q3) of the stored
+ * state; out[3].  Synchronises. */
+int flb_get_conserved(flb_ctx* ctx, int replica, double* out3);
+
+/* Global step counter (number of steps taken). */
+int flb_get_step(flb_ctx* ctx, uint64_t* step_out);
+
+/* Noise-scale network (learned extension, not in the paper): D2Q9 only.
+ * s_a = 1 + o_a(u_x, u_y, rho - rho0) multiplies the Eq. 8 amplitude of moment
+ * a = 3..8, o = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with W1 32x3, W2 32x32,
+ * W3 6x32 (row-major, bfloat16 bit patterns, 96 + 1024 + 192 values in that
+ * order) and FP32 biases b1(32) b2(32) b3(6).  enable = 0 switches it off
+ * (s = 1, bit-identical to the plain method).  Copies the weights. */
+int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int enable);
+
+/* Checkpoint: the state is the populations, the step counter and the
+ * correlator sums.  flb_save with host_buf = NULL reports the size. */
+int flb_save(flb_ctx* ctx, void* host_buf, size_t* bytes_inout);
+int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Destroy the context (does not free the caller's workspace). */
+void flb_destroy(flb_ctx* ctx);
+
+/* Message of the last error on this thread ("" if none). */
+const char* flb_last_error(void);
+
+/* ---- device-pointer entry points (diagnostics and training) ----------- */
+
+/* Philox4x32-10 words and unit normals exactly as the step kernels draw them.
+ * For i < n: counter = (site[i], step, call | tag << 8, stream), key = seed.
+ * words_out: device uint32[4*n] (may be NULL); normals_out: device double[n*2*...]:
+ * if normals_out != NULL it receives, per i, the 2 Box-Muller normals of the
+ * pair (w0, w1) and (w2, w3) of that call: 4 doubles, in FP64 (fp32 = 0) or in
+ * the FP32 recipe (fp32 = 1, stored as double).  site: device uint32[n]. */
+int flb_philox(const uint32_t* site_dev, int n, uint32_t step, uint32_t call, uint32_t tag,
+               uint32_t stream, uint64_t seed, int fp32, uint32_t* words_out_dev,
+               double* normals_out_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLB_H */

@@ -60,6 +60,7 @@ class Params:
     init_mode: int = 0                       # 0 = uniform f^0(rho0, u0); 1 = thermal
     fields: Sequence[int] = field(default_factory=list)
     mlp: Optional[dict] = None               # {"W1","b1","W2","b2","W3","b3"} FP64 arrays
+    mlp_bf16: bool = False                   # round network operands to bfloat16 (tensor-core precision)
 
     @property
     def lat(self):
@@ -141,7 +142,7 @@ def noise_scale(p, rho, u):
     if p.mlp is not None:
         from . import mlp as _mlp
         feats = np.stack([u[0], u[1], rho - p.rho0], axis=-1).reshape(-1, 3)
-        out = _mlp.forward(p.mlp, feats)["s"]                  # (sites, 6)
+        out = _mlp.forward(p.mlp, feats, bf16_operands=p.mlp_bf16)["s"]     # (sites, 6)
         for c, a in enumerate(lat.nonconserved):
             s[a] = out[:, c].reshape(rho.shape)
     return s

@@ -1,0 +1,77 @@
+"""ctypes binding of libflb.so (include/flb.h): argument marshalling only.
+
+The library is built in-tree by ``paper_1010_1233_gb300.build``.  There is no
+fallback: if the shared library cannot be loaded every call raises.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_size_t, c_uint16, c_uint32, c_uint64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libflb.so")
+
+FLB_OK, FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_EUNSTABLE, FLB_ETIMEOUT, FLB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+FLB_D1Q3, FLB_D2Q9 = 1, 2
+FLB_FP64, FLB_FP32_DEV = 0, 1
+FIELD_UX, FIELD_UY = 9, 10
+
+
+class FlbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"flb error {code}: {msg}")
+        self.code = code
+
+
+class flb_replica(ctypes.Structure):
+    _fields_ = [("lattice", c_int32), ("nx", c_int32), ("ny", c_int32), ("tau", c_double * 9),
+                ("rho0", c_double), ("kT", c_double), ("u0", c_double * 2), ("seed", c_uint64),
+                ("stream", c_uint32), ("noise_mask", c_uint32), ("init_mode", c_uint32),
+                ("field_mask", c_uint32)]
+
+
+_SIGS = {
+    "flb_workspace_bytes": (c_int, [c_int, POINTER(flb_replica), c_int, POINTER(c_size_t)]),
+    "flb_create": (c_int, [c_int, POINTER(flb_replica), c_int, c_void_p, c_size_t, c_void_p, POINTER(c_void_p)]),
+    "flb_run": (c_int, [c_void_p, c_uint64, c_uint32]),
+    "flb_sync": (c_int, [c_void_p]),
+    "flb_reset_stats": (c_int, [c_void_p]),
+    "flb_get_correlator": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double), POINTER(c_uint64)]),
+    "flb_get_populations": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_set_populations": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_get_conserved": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_get_step": (c_int, [c_void_p, POINTER(c_uint64)]),
+    "flb_set_mlp": (c_int, [c_void_p, POINTER(c_uint16), POINTER(c_float), c_int]),
+    "flb_save": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
+    "flb_load": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "flb_destroy": (None, [c_void_p]),
+    "flb_last_error": (ctypes.c_char_p, []),
+    "flb_philox": (c_int, [c_void_p, c_int, c_uint32, c_uint32, c_uint32, c_uint32, c_uint64, c_int,
+                           c_void_p, c_void_p, c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libflb.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_1010_1233_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != FLB_OK:
+        raise FlbError(rc, lib().flb_last_error().decode())
+    return rc
+
+
+def exported_symbols():
+    return list(_SIGS)

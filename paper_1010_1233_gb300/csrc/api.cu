@@ -1,0 +1,602 @@
+// Host side of the C ABI declared in include/flb.h: validation, workspace
+// layout, launch sequencing and host I/O.  All compute runs in the kernels of
+// lb_step.cu and spectra.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "flb_internal.cuh"
+
+namespace flb {
+
+// launchers (lb_step.cu, spectra.cu)
+void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool sample, bool mlp, cudaStream_t st);
+void launch_init(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+                 double* sums, int64_t V, cudaStream_t st);
+void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity,
+                      double* sums, DevStatus* status, int64_t V, cudaStream_t st);
+void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,
+                   uint64_t seed, int fp32, uint32_t* words, double* normals, cudaStream_t st);
+size_t mlp_weights_bytes();
+void launch_twiddles(int precision, void* tw, int n, cudaStream_t st);
+int fft_rows_smem(int precision, int nx);
+int fft_cols_smem(int precision, int F, int ny, int ncol);
+cudaError_t set_fft_smem_limits();
+void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
+void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+static int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FLB_OK;
+  return set_error(FLB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static inline int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
+static inline bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+static inline int ilog2(int64_t x) { int l = 0; while ((int64_t(1) << l) < x) ++l; return l; }
+
+static const double kW9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static const int kVx9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int kVy9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double kW3[3] = {2.0 / 3, 1.0 / 6, 1.0 / 6};
+static const int kVx3[3] = {0, 1, -1};
+
+static constexpr int kStepBlock = 256;
+static constexpr int kColsBlock = 256;
+static constexpr int kColsSmemBudget = 200 * 1024;
+
+struct Layout {
+  std::vector<ReplicaDesc> desc;
+  int64_t off_descs = 0, off_vb_step = 0, off_vb_rows = 0, off_vb_cols = 0;
+  int64_t off_status = 0, off_sums = 0, off_feq0 = 0, off_mlp = 0;
+  int64_t total = 0;
+  int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0;
+  std::vector<int64_t> vb_step, vb_rows, vb_cols;
+  int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
+  bool any_fields = false;
+};
+
+static int field_valid(int lattice, int f) {
+  if (lattice == FLB_D2Q9) return f >= 0 && f <= 10;
+  return f == 0 || f == 1 || f == 2 || f == FLB_FIELD_UX;
+}
+
+static int validate(int precision, const flb_replica* reps, int n) {
+  if (precision != FLB_FP64 && precision != FLB_FP32_DEV) return set_error(FLB_EINVAL, "unknown precision %d", precision);
+  if (!reps || n <= 0) return set_error(FLB_EINVAL, "need at least one replica");
+  const int lat = reps[0].lattice;
+  if (lat != FLB_D1Q3 && lat != FLB_D2Q9) return set_error(FLB_EINVAL, "unknown lattice %d", lat);
+  for (int r = 0; r < n; ++r) {
+    const flb_replica& p = reps[r];
+    if (p.lattice != lat) return set_error(FLB_EINVAL, "replica %d: all replicas must share the lattice type", r);
+    const int q = lat == FLB_D2Q9 ? 9 : 3;
+    if (p.nx < 2 || p.nx % 2) return set_error(FLB_EINVAL, "replica %d: nx must be even and >= 2", r);
+    if (lat == FLB_D1Q3 && p.ny != 1) return set_error(FLB_EINVAL, "replica %d: D1Q3 needs ny = 1", r);
+    if (lat == FLB_D2Q9 && p.ny < 1) return set_error(FLB_EINVAL, "replica %d: ny must be >= 1", r);
+    if ((int64_t)p.nx * p.ny >= (int64_t(1) << 32)) return set_error(FLB_EINVAL, "replica %d: lattice too large", r);
+    if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return set_error(FLB_EINVAL, "replica %d: rho0 must be > 0", r);
+    if (!(p.kT >= 0) || !std::isfinite(p.kT)) return set_error(FLB_EINVAL, "replica %d: kT must be >= 0", r);
+    if (!std::isfinite(p.u0[0]) || !std::isfinite(p.u0[1])) return set_error(FLB_EINVAL, "replica %d: u0 not finite", r);
+    const int nc0 = lat == FLB_D2Q9 ? 3 : 2;
+    for (int a = nc0; a < q; ++a)
+      if (!(p.tau[a] > 0.5) || !std::isfinite(p.tau[a]))
+        return set_error(FLB_EINVAL, "replica %d: tau[%d] = %g must be > 1/2", r, a, p.tau[a]);
+    if (p.noise_mask & ((1u << nc0) - 1)) return set_error(FLB_EINVAL, "replica %d: noise on a conserved moment", r);
+    if (p.noise_mask >> q) return set_error(FLB_EINVAL, "replica %d: noise_mask has bits beyond moment %d", r, q - 1);
+    if (p.init_mode > 1) return set_error(FLB_EINVAL, "replica %d: init_mode must be 0 or 1", r);
+    for (int f = 0; f < 32; ++f)
+      if (((p.field_mask >> f) & 1) && !field_valid(lat, f))
+        return set_error(FLB_EINVAL, "replica %d: field %d not available on this lattice", r, f);
+    if (p.field_mask) {
+      if (!is_pow2(p.nx) || !is_pow2(p.ny)) return set_error(FLB_EINVAL, "replica %d: sampling needs power-of-two nx, ny", r);
+      if (fft_rows_smem(precision, p.nx) > 227 * 1024) return set_error(FLB_EINVAL, "replica %d: nx too large for the row FFT", r);
+      const int F = __builtin_popcount(p.field_mask);
+      if (fft_cols_smem(precision, F, p.ny, 1) > kColsSmemBudget)
+        return set_error(FLB_EINVAL, "replica %d: ny = %d too long for the column FFT with %d fields", r, p.ny, F);
+    }
+    if (p.init_mode == 1 && p.kT > 0 && (int64_t)p.nx * p.ny < 2) return set_error(FLB_EINVAL, "thermal init needs V >= 2");
+  }
+  return FLB_OK;
+}
+
+static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
+  memset(&d, 0, sizeof d);
+  const bool d2 = p.lattice == FLB_D2Q9;
+  d.nx = p.nx; d.ny = p.ny; d.log2nx = ilog2(p.nx); d.log2ny = ilog2(p.ny);
+  d.q = d2 ? 9 : 3;
+  d.seed_lo = (uint32_t)p.seed; d.seed_hi = (uint32_t)(p.seed >> 32);
+  d.stream = p.stream; d.noise_mask = p.noise_mask; d.field_mask = p.field_mask;
+  d.rho0 = p.rho0; d.kT = p.kT; d.mu = 3.0 * p.kT; d.u0x = p.u0[0]; d.u0y = d2 ? p.u0[1] : 0.0;
+  const int nc0 = d2 ? 3 : 2;
+  for (int a = nc0; a < d.q; ++a) {
+    d.inv_tau[a] = 1.0 / p.tau[a];
+    d.amp[a] = ((p.noise_mask >> a) & 1) ? std::sqrt(d.mu * p.rho0 * (2.0 * p.tau[a] - 1.0)) / p.tau[a] : 0.0;
+  }
+  // field reference values M^{a,0}(rho0, u0) (Eq. 10), minus rho0 on the density
+  // moment in deviation storage, where the stored moment is that of f - w rho0
+  const double ux = d.u0x, uy = d.u0y, r0 = p.rho0, s3 = std::sqrt(3.0);
+  if (d2) {
+    const double m[9] = {r0, s3 * r0 * ux, s3 * r0 * uy, 1.5 * r0 * (ux * ux - uy * uy), 3 * r0 * ux * uy,
+                         1.5 * r0 * (ux * ux + uy * uy), 0, 0, 0};
+    for (int a = 0; a < 9; ++a) d.mref[a] = m[a];
+  } else {
+    d.mref[0] = r0; d.mref[1] = s3 * r0 * ux; d.mref[2] = 3.0 * r0 * ux * ux / std::sqrt(2.0);
+  }
+  if (precision == FLB_FP32_DEV) d.mref[0] -= r0;
+  int F = 0;
+  for (int f = 0; f < kMaxFields; ++f)
+    if ((p.field_mask >> f) & 1) d.field_id[F++] = f;
+  d.n_fields = F;
+  int np = 0;
+  for (int a = 0; a < F; ++a)
+    for (int b = a; b < F; ++b) { d.pair_a[np] = a; d.pair_b[np] = b; ++np; }
+  d.n_pairs = np;
+  d.half_nx = p.nx / 2 + 1;
+  d.wpitch = (d.half_nx + 1) & ~1;
+}
+
+static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
+  int rc = validate(precision, reps, n);
+  if (rc) return rc;
+  const int lat = reps[0].lattice;
+  const int64_t rs = precision == FLB_FP64 ? 8 : 4;
+  L.q = lat == FLB_D2Q9 ? 9 : 3;
+  // vector width of the step kernel: all replicas share one launch
+  L.vec = 1;
+  if (precision == FLB_FP32_DEV && lat == FLB_D2Q9) {
+    bool all4 = true;
+    for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
+    L.vec = all4 ? 4 : 2;
+  }
+  L.desc.resize(n);
+  int64_t off = 0;
+  int maxF = 0, maxny = 1, maxnx = 2;
+  for (int r = 0; r < n; ++r) {
+    ReplicaDesc& d = L.desc[r];
+    fill_desc(precision, reps[r], d);
+    const int64_t V = (int64_t)d.nx * d.ny;
+    d.off_pop[0] = off; off = align256(off + L.q * V * rs);
+    d.off_pop[1] = off; off = align256(off + L.q * V * rs);
+    if (d.n_fields) {
+      L.any_fields = true;
+      maxF = std::max(maxF, (int)d.n_fields);
+      maxny = std::max(maxny, d.ny);
+      maxnx = std::max(maxnx, d.nx);
+      d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs);
+      d.off_spec = off; off = align256(off + (int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
+      for (int pr = 0; pr < d.n_pairs; ++pr) {
+        d.pair_off[pr] = off;
+        const int64_t el = d.pair_a[pr] == d.pair_b[pr] ? 8 : 16;
+        off = align256(off + (int64_t)d.ny * d.half_nx * el);
+      }
+      d.off_mean0 = off; off = align256(off + 8 * (int64_t)d.n_fields);
+      d.off_tw_x = off; off = align256(off + (int64_t)(d.nx / 2) * 2 * rs + 16);
+      d.off_tw_y = off; off = align256(off + (int64_t)(d.ny / 2) * 2 * rs + 16);
+    }
+    d.units_per_row = d.nx / (lat == FLB_D2Q9 ? L.vec : 1);
+    d.n_units = (int64_t)d.units_per_row * d.ny;
+  }
+  // virtual-block prefixes of the three launches
+  L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n);
+  if (L.any_fields) {
+    const int cs = precision == FLB_FP64 ? 16 : 8;
+    L.ncol = 16;
+    while (L.ncol > 1 && (int64_t)maxF * maxny * L.ncol * cs > kColsSmemBudget) L.ncol >>= 1;
+    L.rows_smem = maxnx * cs;
+    L.rows_block = std::max(32, std::min(512, maxnx / 2));
+    L.cols_smem = maxF * maxny * L.ncol * cs;
+  }
+  for (int r = 0; r < n; ++r) {
+    ReplicaDesc& d = L.desc[r];
+    L.vb_step[r] = L.n_vb_step; d.block_begin = L.n_vb_step;
+    L.n_vb_step += (d.n_units + kStepBlock - 1) / kStepBlock;
+    L.vb_rows[r] = L.n_vb_rows;
+    L.vb_cols[r] = L.n_vb_cols;
+    if (d.n_fields) {
+      L.n_vb_rows += (int64_t)((d.n_fields + 1) / 2) * d.ny;
+      L.n_vb_cols += (d.half_nx + L.ncol - 1) / L.ncol;
+    }
+  }
+  L.off_descs = off; off = align256(off + n * (int64_t)sizeof(ReplicaDesc));
+  L.off_vb_step = off; off = align256(off + 8 * (int64_t)n);
+  L.off_vb_rows = off; off = align256(off + 8 * (int64_t)n);
+  L.off_vb_cols = off; off = align256(off + 8 * (int64_t)n);
+  L.off_status = off; off = align256(off + (int64_t)sizeof(DevStatus));
+  L.off_sums = off; off = align256(off + 8 * 3 * (int64_t)n);
+  L.off_feq0 = off; off = align256(off + 8 * 18 * (int64_t)n);
+  L.off_mlp = off; off = align256(off + (int64_t)mlp_weights_bytes());
+  L.total = off;
+  return FLB_OK;
+}
+
+}  // namespace flb
+
+using namespace flb;
+
+struct flb_ctx {
+  int precision = 0, lattice = 0, n = 0;
+  std::vector<flb_replica> reps;
+  Layout L;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  uint64_t step = 0, n_samples = 0;
+  int sms = 1;
+  bool mlp_on = false;
+  std::vector<float> mlp_host;
+};
+
+static ReplicaDesc* descs_dev(flb_ctx* c) { return reinterpret_cast<ReplicaDesc*>(c->ws + c->L.off_descs); }
+static DevStatus* status_dev(flb_ctx* c) { return reinterpret_cast<DevStatus*>(c->ws + c->L.off_status); }
+
+static void feq0_host(const flb_replica& p, int precision, double out[18]) {
+  // Eq. 2 (c = 1) at (rho0, u0), and w_i rho0
+  const bool d2 = p.lattice == FLB_D2Q9;
+  const int q = d2 ? 9 : 3;
+  const double ux = p.u0[0], uy = d2 ? p.u0[1] : 0.0;
+  for (int i = 0; i < 18; ++i) out[i] = 0.0;
+  for (int i = 0; i < q; ++i) {
+    const double w = d2 ? kW9[i] : kW3[i];
+    const double cu = d2 ? kVx9[i] * ux + kVy9[i] * uy : kVx3[i] * ux;
+    out[i] = p.rho0 * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
+    out[9 + i] = w * p.rho0;
+  }
+  (void)precision;
+}
+
+static int reset_stats_async(flb_ctx* c) {
+  for (int r = 0; r < c->n; ++r) {
+    const ReplicaDesc& d = c->L.desc[r];
+    if (!d.n_fields) continue;
+    const int64_t a0 = d.pair_off[0];
+    const int64_t a1 = d.off_mean0 + 8 * (int64_t)d.n_fields;
+    int rc = cuda_check(cudaMemsetAsync(c->ws + a0, 0, a1 - a0, c->stream), "reset stats");
+    if (rc) return rc;
+  }
+  c->n_samples = 0;
+  return FLB_OK;
+}
+
+extern "C" {
+
+const char* flb_last_error(void) { return g_last_error.c_str(); }
+
+int flb_workspace_bytes(int precision, const flb_replica* reps, int n_replicas, size_t* bytes_out) {
+  if (!bytes_out) return set_error(FLB_EINVAL, "bytes_out is NULL");
+  Layout L;
+  const int rc = plan(precision, reps, n_replicas, L);
+  if (rc) return rc;
+  *bytes_out = (size_t)L.total;
+  return FLB_OK;
+}
+
+int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev_workspace,
+               size_t workspace_bytes, void* cuda_stream, flb_ctx** out) {
+  if (!out) return set_error(FLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  Layout L;
+  int rc = plan(precision, reps, n_replicas, L);
+  if (rc) return rc;
+  if (!dev_workspace) return set_error(FLB_EINVAL, "workspace is NULL");
+  if (((uintptr_t)dev_workspace) & 255) return set_error(FLB_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < (size_t)L.total)
+    return set_error(FLB_ENOMEM, "workspace %zu bytes < required %lld", workspace_bytes, (long long)L.total);
+  flb_ctx* c = new flb_ctx();
+  c->precision = precision; c->lattice = reps[0].lattice; c->n = n_replicas;
+  c->reps.assign(reps, reps + n_replicas);
+  c->L = std::move(L);
+  c->ws = static_cast<char*>(dev_workspace);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((rc = cuda_check(set_fft_smem_limits(), "smem limits"))) { delete c; return rc; }
+  cudaStream_t st = c->stream;
+  const Layout& Lc = c->L;
+  rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_descs, Lc.desc.data(), n_replicas * sizeof(ReplicaDesc),
+                                  cudaMemcpyHostToDevice, st), "copy descriptors");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_step, Lc.vb_step.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_rows, Lc.vb_rows.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_cols, Lc.vb_cols.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
+  std::vector<double> feq(18 * (size_t)n_replicas);
+  for (int r = 0; r < n_replicas; ++r) feq0_host(reps[r], precision, &feq[18 * (size_t)r]);
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_feq0, feq.data(), feq.size() * 8, cudaMemcpyHostToDevice, st), "copy feq0");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + Lc.off_status, 0, sizeof(DevStatus), st), "status");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + Lc.off_mlp, 0, mlp_weights_bytes(), st), "mlp");
+  for (int r = 0; r < n_replicas && !rc; ++r) {
+    const ReplicaDesc& d = Lc.desc[r];
+    const int64_t V = (int64_t)d.nx * d.ny;
+    double* sums = reinterpret_cast<double*>(c->ws + Lc.off_sums) + 3 * r;
+    rc = cuda_check(cudaMemsetAsync(sums, 0, 24, st), "sums");
+    if (rc) break;
+    launch_init(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode,
+                reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + 18 * r, sums, V, st);
+    if (d.n_fields) {
+      launch_twiddles(precision, c->ws + d.off_tw_x, d.nx, st);
+      launch_twiddles(precision, c->ws + d.off_tw_y, d.ny, st);
+    }
+  }
+  if (!rc) rc = reset_stats_async(c);
+  if (!rc) rc = cuda_check(cudaGetLastError(), "init launch");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "init sync");
+  if (rc) { delete c; return rc; }
+  *out = c;
+  return FLB_OK;
+}
+
+int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  const Layout& L = c->L;
+  StepLaunch S;
+  S.descs = descs_dev(c);
+  S.vb_begin = reinterpret_cast<const int64_t*>(c->ws + L.off_vb_step);
+  S.n_reps = c->n;
+  S.n_vblocks = L.n_vb_step;
+  S.ws = c->ws;
+  S.mlp = c->ws + L.off_mlp;
+  S.block = kStepBlock;
+  S.grid = (int)std::min<int64_t>(L.n_vb_step, (int64_t)c->sms * 16);
+  const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
+  const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
+  for (uint64_t i = 0; i < n_steps; ++i) {
+    const uint64_t t = c->step;
+    const bool sample = sample_every && L.any_fields && (t % sample_every) == 0;
+    S.parity = (int)(t & 1);
+    S.step = (uint32_t)t;
+    launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, c->stream);
+    if (sample) {
+      launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
+                      L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, c->stream);
+      launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
+                      L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, c->stream);
+      ++c->n_samples;
+    }
+    ++c->step;
+  }
+  return cuda_check(cudaGetLastError(), "flb_run launch");
+}
+
+int flb_sync(flb_ctx* c) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "flb_sync");
+  if (rc) return rc;
+  DevStatus s;
+  rc = cuda_check(cudaMemcpy(&s, status_dev(c), sizeof s, cudaMemcpyDeviceToHost), "status read");
+  if (rc) return rc;
+  if (s.error) return set_error(s.error, "device reported status %d on replica %d", s.error, s.replica);
+  return FLB_OK;
+}
+
+int flb_reset_stats(flb_ctx* c) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  return reset_stats_async(c);
+}
+
+int flb_get_step(flb_ctx* c, uint64_t* step_out) {
+  if (!c || !step_out) return set_error(FLB_EINVAL, "NULL argument");
+  *step_out = c->step;
+  return FLB_OK;
+}
+
+int flb_get_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out, uint64_t* n_samples) {
+  if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  const ReplicaDesc& d = c->L.desc[replica];
+  int sa = -1, sb = -1;
+  for (int s = 0; s < (int)d.n_fields; ++s) { if (d.field_id[s] == fa) sa = s; if (d.field_id[s] == fb) sb = s; }
+  if (sa < 0 || sb < 0) return set_error(FLB_EINVAL, "fields %d, %d are not both sampled", fa, fb);
+  if (c->n_samples == 0) return set_error(FLB_ESTATE, "no samples accumulated");
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  const bool swap = sa > sb;
+  const int lo = swap ? sb : sa, hi = swap ? sa : sb;
+  int pr = -1;
+  for (int k = 0; k < d.n_pairs; ++k) if (d.pair_a[k] == lo && d.pair_b[k] == hi) pr = k;
+  const int nx = d.nx, ny = d.ny, hn = d.half_nx;
+  const bool autoc = lo == hi;
+  std::vector<double> acc((size_t)ny * hn * (autoc ? 1 : 2));
+  rc = cuda_check(cudaMemcpy(acc.data(), c->ws + d.pair_off[pr], acc.size() * 8, cudaMemcpyDeviceToHost), "read sums");
+  if (rc) return rc;
+  std::vector<double> m0(d.n_fields);
+  rc = cuda_check(cudaMemcpy(m0.data(), c->ws + d.off_mean0, 8 * d.n_fields, cudaMemcpyDeviceToHost), "read means");
+  if (rc) return rc;
+  const double ns = (double)c->n_samples;
+  const double V = (double)nx * ny;
+  auto var = [&](int f) { return f < 9 ? d.mu * d.rho0 : d.kT / d.rho0; };
+  const double vv = var(fa) * var(fb);
+  const double norm = vv > 0 ? 1.0 / (V * std::sqrt(vv)) : 1.0 / V;
+  for (int ky = 0; ky < ny; ++ky)
+    for (int kx = 0; kx < nx; ++kx) {
+      double re, im;
+      int hy = ky, hx = kx;
+      bool conj = false;
+      if (kx > nx / 2) { hx = nx - kx; hy = (ny - ky) % ny; conj = true; }
+      const size_t idx = (size_t)hy * hn + hx;
+      if (autoc) { re = acc[idx]; im = 0.0; }
+      else { re = acc[2 * idx]; im = acc[2 * idx + 1]; }
+      if (conj) im = -im;
+      if (swap) im = -im;
+      re /= ns; im /= ns;
+      if (kx == 0 && ky == 0) re -= (m0[sa] / ns) * (m0[sb] / ns);
+      host_out[2 * ((size_t)ky * nx + kx)] = re * norm;
+      host_out[2 * ((size_t)ky * nx + kx) + 1] = im * norm;
+    }
+  if (n_samples) *n_samples = c->n_samples;
+  return FLB_OK;
+}
+
+int flb_get_populations(flb_ctx* c, int replica, double* host_out) {
+  if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  const ReplicaDesc& d = c->L.desc[replica];
+  const int64_t V = (int64_t)d.nx * d.ny;
+  const char* src = c->ws + d.off_pop[c->step & 1];
+  if (c->precision == FLB_FP64)
+    return cuda_check(cudaMemcpy(host_out, src, d.q * V * 8, cudaMemcpyDeviceToHost), "read populations");
+  std::vector<float> tmp((size_t)d.q * V);
+  rc = cuda_check(cudaMemcpy(tmp.data(), src, tmp.size() * 4, cudaMemcpyDeviceToHost), "read populations");
+  if (rc) return rc;
+  for (int i = 0; i < d.q; ++i) {
+    const double wr = (d.q == 9 ? kW9[i] : kW3[i]) * d.rho0;
+    for (int64_t s = 0; s < V; ++s) host_out[i * V + s] = wr + (double)tmp[i * V + s];
+  }
+  return FLB_OK;
+}
+
+int flb_set_populations(flb_ctx* c, int replica, const double* host_in) {
+  if (!c || !host_in) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  const ReplicaDesc& d = c->L.desc[replica];
+  const int64_t V = (int64_t)d.nx * d.ny;
+  char* dst = c->ws + d.off_pop[c->step & 1];
+  if (c->precision == FLB_FP64)
+    return cuda_check(cudaMemcpy(dst, host_in, d.q * V * 8, cudaMemcpyHostToDevice), "write populations");
+  std::vector<float> tmp((size_t)d.q * V);
+  for (int i = 0; i < d.q; ++i) {
+    const double wr = (d.q == 9 ? kW9[i] : kW3[i]) * d.rho0;
+    for (int64_t s = 0; s < V; ++s) tmp[i * V + s] = (float)(host_in[i * V + s] - wr);
+  }
+  return cuda_check(cudaMemcpy(dst, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice), "write populations");
+}
+
+int flb_get_conserved(flb_ctx* c, int replica, double* out3) {
+  if (!c || !out3) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  const ReplicaDesc& d = c->L.desc[replica];
+  double* sums = reinterpret_cast<double*>(c->ws + c->L.off_sums) + 3 * replica;
+  int rc = cuda_check(cudaMemsetAsync(sums, 0, 24, c->stream), "sums");
+  if (rc) return rc;
+  launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, status_dev(c),
+                   (int64_t)d.nx * d.ny, c->stream);
+  rc = cuda_check(cudaGetLastError(), "conserved launch");
+  if (rc) return rc;
+  rc = flb_sync(c);
+  if (rc) return rc;
+  return cuda_check(cudaMemcpy(out3, sums, 24, cudaMemcpyDeviceToHost), "read sums");
+}
+
+int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int enable) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  if (c->lattice != FLB_D2Q9) return set_error(FLB_EINVAL, "the noise-scale network is D2Q9 only");
+  if (enable && (!w_bf16 || !biases)) return set_error(FLB_EINVAL, "NULL weights");
+  if (enable) {
+    const size_t nf = mlp_weights_bytes() / 4;
+    c->mlp_host.assign(nf, 0.f);
+    for (int i = 0; i < kMlpWeights; ++i) {
+      const uint32_t bits = (uint32_t)w_bf16[i] << 16;
+      float v;
+      memcpy(&v, &bits, 4);
+      c->mlp_host[i] = v;
+    }
+    for (int i = 0; i < kMlpBiases; ++i) c->mlp_host[kMlpWeights + i] = biases[i];
+    int rc = cuda_check(cudaMemcpyAsync(c->ws + c->L.off_mlp, c->mlp_host.data(), nf * 4, cudaMemcpyHostToDevice,
+                                        c->stream), "copy mlp");
+    if (rc) return rc;
+    rc = cuda_check(cudaStreamSynchronize(c->stream), "copy mlp");
+    if (rc) return rc;
+  }
+  c->mlp_on = enable != 0;
+  return FLB_OK;
+}
+
+int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
+  if (!c || !bytes_inout) return set_error(FLB_EINVAL, "NULL argument");
+  const int64_t rs = c->precision == FLB_FP64 ? 8 : 4;
+  size_t need = 64;
+  for (int r = 0; r < c->n; ++r) {
+    const ReplicaDesc& d = c->L.desc[r];
+    need += d.q * (size_t)d.nx * d.ny * rs;
+    if (d.n_fields) need += (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
+  }
+  if (!host_buf) { *bytes_inout = need; return FLB_OK; }
+  if (*bytes_inout < need) return set_error(FLB_EINVAL, "buffer of %zu bytes < %zu", *bytes_inout, need);
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  char* p = static_cast<char*>(host_buf);
+  uint64_t hdr[8] = {0x464c4243484b5031ull, (uint64_t)c->precision, (uint64_t)c->n, c->step, c->n_samples,
+                     (uint64_t)need, (uint64_t)c->lattice, 0};
+  memcpy(p, hdr, 64);
+  p += 64;
+  for (int r = 0; r < c->n; ++r) {
+    const ReplicaDesc& d = c->L.desc[r];
+    const size_t pb = d.q * (size_t)d.nx * d.ny * rs;
+    rc = cuda_check(cudaMemcpy(p, c->ws + d.off_pop[c->step & 1], pb, cudaMemcpyDeviceToHost), "save");
+    if (rc) return rc;
+    p += pb;
+    if (d.n_fields) {
+      const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
+      rc = cuda_check(cudaMemcpy(p, c->ws + d.pair_off[0], ab, cudaMemcpyDeviceToHost), "save");
+      if (rc) return rc;
+      p += ab;
+    }
+  }
+  *bytes_inout = need;
+  return FLB_OK;
+}
+
+int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return set_error(FLB_EINVAL, "NULL argument");
+  size_t need = 0;
+  int rc = flb_save(c, nullptr, &need);
+  if (rc) return rc;
+  if (bytes != need) return set_error(FLB_EINVAL, "checkpoint has %zu bytes, context needs %zu", bytes, need);
+  const char* p = static_cast<const char*>(host_buf);
+  uint64_t hdr[8];
+  memcpy(hdr, p, 64);
+  if (hdr[0] != 0x464c4243484b5031ull || hdr[1] != (uint64_t)c->precision || hdr[2] != (uint64_t)c->n ||
+      hdr[6] != (uint64_t)c->lattice)
+    return set_error(FLB_EINVAL, "checkpoint does not match this context");
+  rc = cuda_check(cudaStreamSynchronize(c->stream), "load");
+  if (rc) return rc;
+  p += 64;
+  const uint64_t step = hdr[3];
+  const int64_t rs = c->precision == FLB_FP64 ? 8 : 4;
+  for (int r = 0; r < c->n; ++r) {
+    const ReplicaDesc& d = c->L.desc[r];
+    const size_t pb = d.q * (size_t)d.nx * d.ny * rs;
+    rc = cuda_check(cudaMemcpy(c->ws + d.off_pop[step & 1], p, pb, cudaMemcpyHostToDevice), "load");
+    if (rc) return rc;
+    p += pb;
+    if (d.n_fields) {
+      const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
+      rc = cuda_check(cudaMemcpy(c->ws + d.pair_off[0], p, ab, cudaMemcpyHostToDevice), "load");
+      if (rc) return rc;
+      p += ab;
+    }
+  }
+  c->step = step;
+  c->n_samples = hdr[4];
+  return FLB_OK;
+}
+
+void flb_destroy(flb_ctx* c) { delete c; }
+
+int flb_philox(const uint32_t* site_dev, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,
+               uint64_t seed, int fp32, uint32_t* words_out_dev, double* normals_out_dev, void* cuda_stream) {
+  if (n < 0 || (n > 0 && !site_dev)) return set_error(FLB_EINVAL, "bad site array");
+  if (call > 255 || tag > 0xFFFFFF) return set_error(FLB_EINVAL, "call must be < 256");
+  launch_philox(site_dev, n, step, call, tag, stream, seed, fp32, words_out_dev, normals_out_dev,
+                static_cast<cudaStream_t>(cuda_stream));
+  return cuda_check(cudaGetLastError(), "flb_philox launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal definitions shared by the CUDA translation units of libflb.
+// Device code for sm_103a; host code plain C++17.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "../../include/flb.h"
+
+namespace flb {
+
+constexpr int kMaxFields = FLB_MAX_FIELDS;
+constexpr int kMaxPairs = kMaxFields * (kMaxFields + 1) / 2;
+constexpr int kMlpHidden = 32;
+constexpr int kMlpOut = 6;
+constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden;  // 1312
+constexpr int kMlpBiases = kMlpHidden + kMlpHidden + kMlpOut;                               // 70
+
+// Per-replica description, resident in device memory (one array per context).
+// Offsets are byte offsets from the workspace base.
+struct ReplicaDesc {
+  int32_t nx, ny, log2nx, log2ny;
+  int32_t q;
+  int32_t units_per_row;        // nx / VEC of the step launch
+  int64_t n_units;              // units_per_row * ny
+  int64_t block_begin;          // first virtual block of this replica in the step launch
+  uint32_t seed_lo, seed_hi, stream, noise_mask;
+  uint32_t field_mask, n_fields;
+  int32_t field_id[kMaxFields];     // slot -> field id
+  int32_t n_pairs;
+  int32_t pair_a[kMaxPairs], pair_b[kMaxPairs];   // slot indices, a <= b
+  int64_t pair_off[kMaxPairs];      // byte offset of the pair's accumulator plane
+  double rho0, kT, mu, u0x, u0y;
+  double inv_tau[9];
+  double amp[9];                    // (1/tau) sqrt(mu rho0 (2 tau - 1)), 0 when masked
+  double mref[kMaxFields];          // reference value subtracted from each field id
+  int64_t off_pop[2];               // population buffers (ping-pong)
+  int64_t off_fields;               // [n_fields][ny][nx] Real
+  int64_t off_spec;                 // [n_fields][ny][wpitch] complex Real (row-transformed)
+  int64_t off_mean0;                // [n_fields] double: sum over samples of X(k=0)
+  int64_t off_tw_x, off_tw_y;       // twiddles exp(-2 pi i m / n), m < n/2, complex Real
+  int32_t half_nx;                  // nx / 2 + 1
+  int32_t wpitch;                   // pitch (complex elements) of spec rows
+};
+
+struct DevStatus {
+  int32_t error;        // 0 ok; FLB_EUNSTABLE / FLB_ETIMEOUT set by kernels
+  int32_t replica;      // first replica that raised it
+  uint64_t n_samples;   // samples accumulated
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 128-bit counter, 64-bit key.
+__host__ __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                                      uint32_t& c3, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#ifdef __CUDA_ARCH__
+  const uint32_t hi0 = __umulhi(M0, c0), hi1 = __umulhi(M1, c2);
+#else
+  const uint32_t hi0 = (uint32_t)(((uint64_t)M0 * c0) >> 32), hi1 = (uint32_t)(((uint64_t)M1 * c2) >> 32);
+#endif
+  const uint32_t lo0 = M0 * c0, lo1 = M1 * c2;
+  const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+  c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                        uint32_t c3, uint32_t k0, uint32_t k1) {
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c0, c1, c2, c3, k0, k1);
+    k0 += W0; k1 += W1;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Box-Muller on a word pair.  FP64: u = (w + 1/2) 2^-32.  FP32: u = ((w >> 9) + 1/2) 2^-23,
+// the top 23 bits, so that u is exact in FP32 and strictly inside (0, 1).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
+  const double ua = ((double)wa + 0.5) * 0x1p-32;
+  const double ub = ((double)wb + 0.5) * 0x1p-32;
+  const double r = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  n0 = r * c; n1 = r * s;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+  const float ua = ((float)(wa >> 9) + 0.5f) * 0x1p-23f;
+  const float ub = ((float)(wb >> 9) + 0.5f) * 0x1p-23f;
+  const float r = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  n0 = r * c; n1 = r * s;
+}
+
+template <typename T> struct cplx { T x, y; };
+template <typename T> struct vec2_of;
+template <> struct vec2_of<float> { using type = float2; };
+template <> struct vec2_of<double> { using type = double2; };
+
+// Arguments of one step launch (lb_step.cu).
+struct StepLaunch {
+  const ReplicaDesc* descs; const int64_t* vb_begin; int n_reps; int64_t n_vblocks;
+  char* ws; int parity; uint32_t step; const void* mlp; int grid; int block;
+};
+
+// host-side helpers (api.cu)
+int set_error(int code, const char* fmt, ...);
+
+}  // namespace flb

@@ -1,0 +1,167 @@
+"""Python front end of libflb: a context over one or more replicas.
+
+PyTorch provides the device workspace and the CUDA stream; every step of the
+method runs in the library's kernels through the C ABI.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_NONCONSERVED = {"D2Q9": (3, 4, 5, 6, 7, 8), "D1Q3": (2,)}
+_LATTICE = {"D2Q9": L.FLB_D2Q9, "D1Q3": L.FLB_D1Q3}
+_PREC = {"fp64": L.FLB_FP64, "fp32": L.FLB_FP32_DEV}
+
+
+def replica_struct(p):
+    """flb_replica from a parameter dict (paper_1010_1233_gb300.workloads.replica)."""
+    s = L.flb_replica()
+    s.lattice = _LATTICE[p["lattice"]]
+    s.nx = int(p["nx"])
+    s.ny = int(p["ny"]) if p["lattice"] == "D2Q9" else 1
+    tau = list(p["tau"]) + [1.0] * (9 - len(p["tau"]))
+    for a in range(9):
+        s.tau[a] = float(tau[a])
+    s.rho0 = float(p["rho0"])
+    s.kT = float(p["kT"])
+    s.u0[0], s.u0[1] = float(p["u0"][0]), float(p["u0"][1])
+    s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
+    s.stream = int(p.get("stream", 0))
+    nm = p.get("noise_mask")
+    s.noise_mask = sum(1 << a for a in _NONCONSERVED[p["lattice"]]) if nm is None else int(nm)
+    s.init_mode = int(p.get("init_mode", 0))
+    s.field_mask = sum(1 << f for f in p.get("fields", ()))
+    return s
+
+
+def bf16_bits(x):
+    """bfloat16 bit patterns (round to nearest even) of an FP32 array, via torch."""
+    t = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16)
+    return t.view(torch.int16).numpy().view(np.uint16)
+
+
+class Sim:
+    """A batch of replicas sharing one lattice type and storage precision."""
+
+    def __init__(self, replicas, precision="fp32", device=None, stream=None):
+        if isinstance(replicas, dict):
+            replicas = [replicas]
+        self.params = [dict(p) for p in replicas]
+        self.precision = precision
+        n = len(self.params)
+        arr = (L.flb_replica * n)(*[replica_struct(p) for p in self.params])
+        self._reps = arr
+        lib = L.lib()
+        nbytes = ctypes.c_size_t()
+        L.check(lib.flb_workspace_bytes(_PREC[precision], arr, n, ctypes.byref(nbytes)))
+        self.device = torch.device(device or "cuda")
+        self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        ctx = ctypes.c_void_p()
+        L.check(lib.flb_create(_PREC[precision], arr, n, ctypes.c_void_p(self.workspace.data_ptr()),
+                               self.workspace.numel(), ctypes.c_void_p(self.stream.cuda_stream),
+                               ctypes.byref(ctx)))
+        self._ctx = ctx
+        self.workspace_bytes = int(nbytes.value)
+
+    # -- stepping ---------------------------------------------------------
+    def run(self, n_steps, sample_every=0):
+        L.check(L.lib().flb_run(self._ctx, int(n_steps), int(sample_every)))
+        return self
+
+    def sync(self):
+        L.check(L.lib().flb_sync(self._ctx))
+
+    def reset_stats(self):
+        L.check(L.lib().flb_reset_stats(self._ctx))
+
+    @property
+    def step(self):
+        v = ctypes.c_uint64()
+        L.check(L.lib().flb_get_step(self._ctx, ctypes.byref(v)))
+        return int(v.value)
+
+    # -- results ----------------------------------------------------------
+    def _shape(self, r):
+        p = self.params[r]
+        return (p["ny"] if p["lattice"] == "D2Q9" else 1, p["nx"])
+
+    def correlator(self, r, a, b, with_count=False):
+        ny, nx = self._shape(r)
+        out = np.empty(ny * nx * 2)
+        n = ctypes.c_uint64()
+        L.check(L.lib().flb_get_correlator(self._ctx, r, a, b,
+                                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(n)))
+        c = out[0::2] + 1j * out[1::2]
+        c = c.reshape(ny, nx)
+        return (c, int(n.value)) if with_count else c
+
+    def populations(self, r=0):
+        ny, nx = self._shape(r)
+        q = 9 if self.params[r]["lattice"] == "D2Q9" else 3
+        out = np.empty((q, ny, nx))
+        L.check(L.lib().flb_get_populations(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def set_populations(self, f, r=0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        L.check(L.lib().flb_set_populations(self._ctx, r, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def conserved(self, r=0):
+        out = np.empty(3)
+        L.check(L.lib().flb_get_conserved(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    # -- learned noise scale ----------------------------------------------
+    def set_mlp(self, weights=None):
+        """weights: dict W1 (32,3), b1, W2 (32,32), b2, W3 (6,32), b3 (FP32); None disables."""
+        lib = L.lib()
+        if weights is None:
+            L.check(lib.flb_set_mlp(self._ctx, None, None, 0))
+            return
+        w = np.concatenate([bf16_bits(weights[k]).ravel() for k in ("W1", "W2", "W3")])
+        b = np.concatenate([np.asarray(weights[k], np.float32).ravel() for k in ("b1", "b2", "b3")])
+        w = np.ascontiguousarray(w, dtype=np.uint16)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        L.check(lib.flb_set_mlp(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
+                                b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    # -- checkpoint -------------------------------------------------------
+    def save(self):
+        lib = L.lib()
+        n = ctypes.c_size_t()
+        L.check(lib.flb_save(self._ctx, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(lib.flb_save(self._ctx, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        L.check(L.lib().flb_load(self._ctx, buf, len(blob)))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            L.lib().flb_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def philox(sites, step, call, tag, stream, seed, fp32=False, device="cuda"):
+    """Philox words (n, 4) and normals (n, 4) exactly as the step kernels draw them."""
+    s = torch.as_tensor(np.asarray(sites, dtype=np.uint32).view(np.int32), device=device)
+    n = s.numel()
+    words = torch.empty(4 * n, dtype=torch.int32, device=device)
+    normals = torch.empty(4 * n, dtype=torch.float64, device=device)
+    st = torch.cuda.current_stream()
+    L.check(L.lib().flb_philox(ctypes.c_void_p(s.data_ptr()), n, step, call, tag, stream, seed, int(fp32),
+                               ctypes.c_void_p(words.data_ptr()), ctypes.c_void_p(normals.data_ptr()),
+                               ctypes.c_void_p(st.cuda_stream)))
+    torch.cuda.synchronize()
+    return (words.cpu().numpy().view(np.uint32).reshape(n, 4), normals.cpu().numpy().reshape(n, 4))

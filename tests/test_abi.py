@@ -1,0 +1,82 @@
+"""The C-ABI library loads, exports every declared symbol and validates its input (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1010_1233_gb300 import _lib as L, build, workloads as W
+from paper_1010_1233_gb300.sim import replica_struct
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return L.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(flb_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "flb_run" in names and "flb_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(L.exported_symbols()) | set(names)
+
+
+def _ws(reps, precision=L.FLB_FP32_DEV):
+    arr = (L.flb_replica * len(reps))(*[replica_struct(p) for p in reps])
+    n = ctypes.c_size_t()
+    rc = L.lib().flb_workspace_bytes(precision, arr, len(reps), ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_size_grows_with_lattice(lib):
+    rc1, a = _ws([W.replica(nx=64, ny=64)])
+    rc2, b = _ws([W.replica(nx=128, ny=64)])
+    assert rc1 == rc2 == 0 and b > a >= 2 * 9 * 64 * 64 * 4
+    rc3, c = _ws([W.replica(nx=64, ny=64, fields=(0, 9, 10))])
+    assert rc3 == 0 and c > a
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau=W.taus_d2q9(0.5)),                     # tau must exceed 1/2
+    dict(nx=7),                                     # odd nx
+    dict(rho0=0.0),
+    dict(noise_mask=1),                             # noise on density
+    dict(fields=(0,), nx=24),                       # sampling needs powers of two
+    dict(fields=(11,)),                             # unknown field
+    dict(init_mode=3),
+])
+def test_invalid_parameters_rejected(lib, bad):
+    p = W.replica(nx=16, ny=16)
+    p.update(bad)
+    rc, _ = _ws([p])
+    assert rc == L.FLB_EINVAL
+    assert len(lib.flb_last_error()) > 0
+
+
+def test_mixed_lattices_rejected(lib):
+    rc, _ = _ws([W.replica(nx=16, ny=16), W.replica("D1Q3", 16, 1, W.taus_d1q3(0.8))])
+    assert rc == L.FLB_EINVAL
+
+
+def test_d1q3_needs_single_row(lib):
+    p = W.replica("D1Q3", 16, 1, W.taus_d1q3(0.8))
+    p["ny"] = 4
+    s = replica_struct(p)
+    s.ny = 4
+    arr = (L.flb_replica * 1)(s)
+    n = ctypes.c_size_t()
+    assert lib.flb_workspace_bytes(L.FLB_FP64, arr, 1, ctypes.byref(n)) == L.FLB_EINVAL

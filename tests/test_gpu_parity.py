@@ -1,0 +1,211 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lb, mlp as omlp, philox as ophilox, spectra
+from paper_1010_1233_gb300 import Sim, philox, workloads as W
+from paper_1010_1233_gb300 import _lib as L
+
+pytestmark = pytest.mark.gpu
+
+LADD = (1 << 3) | (1 << 4) | (1 << 5)
+FP64_TOL = 1e-12        # per step, relative to max |f - w rho0|
+FP32_TOL = 2e-5         # after the run, relative to max |f - w rho0|
+
+
+def _oracle(p, **kw):
+    d = dict(p)
+    d.update(kw)
+    return lb.Run(lb.Params(**d))
+
+
+def _rel(a, b, ref):
+    return np.abs(a - b).max() / max(np.abs(ref).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------- generator
+def test_philox_words_bit_exact_and_normals():
+    rng = np.random.default_rng(1)
+    sites = np.concatenate([np.arange(1000), rng.integers(0, 2**32, 3000)]).astype(np.uint32)
+    for step, call, tag, stream, seed in [(0, 0, 0, 0, 0), (123456, 1, 0, 5, 7), (2**32 - 1, 2, 1, 63, 2**64 - 3)]:
+        words, nrm = philox(sites, step, call, tag, stream, seed)
+        want = ophilox.philox4x32_10(sites.astype(np.uint64), step, call | (tag << 8), stream, seed)
+        for k in range(4):
+            assert np.array_equal(words[:, k], want[k])
+        a0, a1 = ophilox.box_muller(ophilox.uniform_fp64(want[0]), ophilox.uniform_fp64(want[1]))
+        a2, a3 = ophilox.box_muller(ophilox.uniform_fp64(want[2]), ophilox.uniform_fp64(want[3]))
+        ref = np.stack([a0, a1, a2, a3], 1)
+        assert np.abs(nrm - ref).max() < 1e-13
+        # FP32 recipe: 23-bit uniforms, single-precision log/sincos
+        _, n32 = philox(sites, step, call, tag, stream, seed, fp32=True)
+        assert np.abs(n32 - ref).max() < 1e-4
+        assert np.median(np.abs(n32 - ref)) < 2e-6
+
+
+# ---------------------------------------------------------------------------- FP64 step
+CASES = [
+    ("D2Q9", 64, 64, dict(tau=W.taus_d2q9(0.8, 0.8, 1.0), u0=(0.0, 0.0), init_mode=1)),
+    ("D2Q9", 128, 32, dict(tau=W.taus_d2q9(0.6, 0.9, 1.3), u0=(0.1, 0.05), init_mode=1)),
+    ("D2Q9", 24, 10, dict(tau=W.taus_d2q9(0.7, 0.7, 1.0), u0=(-0.05, 0.1), noise_mask=LADD)),
+    ("D1Q3", 64, 1, dict(tau=W.taus_d1q3(0.8), init_mode=1)),
+    ("D1Q3", 22, 1, dict(tau=W.taus_d1q3(0.55), u0=(0.2, 0.0))),
+]
+
+
+@pytest.mark.parametrize("lat,nx,ny,kw", CASES, ids=[f"{c[0]}-{c[1]}x{c[2]}" for c in CASES])
+def test_fp64_step_matches_oracle_every_step(lat, nx, ny, kw):
+    p = W.replica(lat, nx, ny, kT=1e-3, seed=11, stream=3, **kw)
+    sim = Sim(p, precision="fp64")
+    ref = _oracle(p)
+    feq = lb.uniform_state(ref.p)
+    assert _rel(sim.populations(), ref.f, ref.f - feq) < 1e-14
+    worst = 0.0
+    for _ in range(100):
+        sim.run(1)
+        ref.run(1)
+        worst = max(worst, _rel(sim.populations(), ref.f, ref.f - feq))
+    assert worst < FP64_TOL, worst
+    c = sim.conserved()
+    assert abs(c[0] - ref.conserved()[0]) < 1e-12 * nx * ny
+
+
+def test_fp64_from_arbitrary_state():
+    p = W.replica("D2Q9", 32, 16, W.taus_d2q9(0.9, 0.7, 1.5), kT=1e-2, u0=(0.03, -0.02), seed=3)
+    ref = _oracle(p)
+    f = ref.f * (1 + W.random_perturbation(ref.f.shape, 8, 0.02))
+    ref = _oracle(p)
+    ref.f = f.copy()
+    sim = Sim(p, precision="fp64")
+    sim.set_populations(f)
+    sim.run(30)
+    ref.run(30)
+    assert _rel(sim.populations(), ref.f, ref.f - lb.uniform_state(ref.p)) < FP64_TOL
+
+
+# ---------------------------------------------------------------------------- FP32 deviation storage
+@pytest.mark.parametrize("nx,ny", [(64, 64), (36, 20), (30, 8)])
+def test_fp32_dev_close_to_oracle(nx, ny):
+    p = W.replica("D2Q9", nx, ny, W.taus_d2q9(0.8, 0.8, 1.0), kT=1e-4, u0=(0.1, 0.05), seed=4,
+                  init_mode=1)
+    sim = Sim(p, precision="fp32")
+    ref = _oracle(p)
+    feq = lb.uniform_state(ref.p)
+    errs = []
+    for _ in range(10):
+        sim.run(10)
+        ref.run(10)
+        errs.append(_rel(sim.populations(), ref.f, ref.f - feq))
+    print("FP32-dev relative population error every 10 steps:", ["%.1e" % e for e in errs])
+    assert max(errs) < FP32_TOL
+
+
+# ---------------------------------------------------------------------------- correlators
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_correlators_match_oracle(precision, tol):
+    fields = (0, 1, 2, 3, 5, 8, W.FIELD_UX, W.FIELD_UY)
+    p = W.replica("D2Q9", 16, 32, W.taus_d2q9(0.8, 0.9, 1.1), kT=1e-3, u0=(0.08, -0.04), seed=21,
+                  init_mode=1, fields=fields)
+    sim = Sim(p, precision=precision)
+    ref = _oracle(p)
+    sim.run(40, sample_every=3)
+    ref.run(40, sample_every=3)
+    for a, b in spectra.pairs(fields):
+        g, n = sim.correlator(0, a, b, with_count=True)
+        o = ref.acc.correlator(a, b)
+        assert n == ref.acc.n
+        err = np.abs(g - o).max() / max(1.0, np.abs(o).max())
+        assert err < tol, (a, b, err)
+
+
+def test_d1q3_correlators_match_oracle():
+    p = W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1, 2, 9))
+    sim = Sim(p, precision="fp64")
+    ref = _oracle(p)
+    sim.run(50, 1)
+    ref.run(50, 1)
+    for a, b in spectra.pairs(p["fields"]):
+        assert np.abs(sim.correlator(0, a, b) - ref.acc.correlator(a, b)).max() < 1e-9
+
+
+# ---------------------------------------------------------------------------- batching, checkpoint
+def test_batched_replicas_bitwise_equal_single():
+    reps = [W.replica("D2Q9", 32, 32, W.taus_d2q9(0.7 + 0.1 * i), kT=1e-4, u0=(0.02 * i, 0), seed=i,
+                      stream=i, init_mode=1, fields=(0, 9, 10)) for i in range(3)]
+    reps.append(W.replica("D2Q9", 64, 16, W.taus_d2q9(0.9), kT=1e-4, seed=9, stream=9, fields=(0, 9, 10)))
+    for prec in ("fp64", "fp32"):
+        batch = Sim(reps, precision=prec)
+        batch.run(25, 5)
+        for i, p in enumerate(reps):
+            one = Sim(p, precision=prec)
+            one.run(25, 5)
+            assert np.array_equal(batch.populations(i), one.populations())
+            assert np.array_equal(batch.correlator(i, 0, 9), one.correlator(0, 0, 9))
+
+
+def test_checkpoint_resume_bitwise():
+    p = W.replica("D2Q9", 32, 32, W.taus_d2q9(0.8), kT=1e-4, seed=2, init_mode=1, fields=(0, 9))
+    a = Sim(p, precision="fp32")
+    a.run(20, 4)
+    blob = a.save()
+    a.run(20, 4)
+    b = Sim(p, precision="fp32")
+    b.load(blob)
+    assert b.step == 20
+    b.run(20, 4)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.correlator(0, 0, 9), b.correlator(0, 0, 9))
+
+
+def test_conservation_fp64_long_run():
+    p = W.replica("D2Q9", 64, 64, W.taus_d2q9(0.55, 0.6, 1.9), kT=1e-3, u0=(0.1, 0.1), seed=5, init_mode=1)
+    sim = Sim(p, precision="fp64")
+    c0 = sim.conserved()
+    sim.run(2000)
+    assert np.abs(sim.conserved() - c0).max() < 1e-13 * 64 * 64
+
+
+# ---------------------------------------------------------------------------- noise-scale network
+def test_mlp_scaled_noise_matches_oracle():
+    wts = W.mlp_weights(3, out_scale=0.5)
+    p = W.replica("D2Q9", 32, 16, W.taus_d2q9(0.8, 0.8, 1.0), kT=1e-4, u0=(0.15, -0.05), seed=6,
+                  init_mode=1)
+    sim = Sim(p, precision="fp32")
+    sim.set_mlp(wts)
+    w64 = {k: (omlp.to_bf16(v) if k.startswith("W") else v.astype(np.float64)) for k, v in wts.items()}
+    ref = _oracle(p)
+    ref.p.mlp = w64
+    ref.p.mlp_bf16 = True
+    sim.run(10)
+    ref.run(10)
+    feq = lb.uniform_state(ref.p)
+    err = _rel(sim.populations(), ref.f, ref.f - feq)
+    assert err < FP32_TOL, err
+    # the network really changes the dynamics
+    plain = _oracle(p)
+    plain.run(10)
+    assert _rel(plain.f, ref.f, ref.f - feq) > 20 * err
+
+
+def test_mlp_zero_output_is_plain_method_bitwise():
+    wts = W.mlp_weights(4)
+    wts["W3"][:] = 0
+    wts["b3"][:] = 0
+    p = W.replica("D2Q9", 32, 32, W.taus_d2q9(0.8), kT=1e-4, u0=(0.1, 0), seed=7, init_mode=1)
+    a = Sim(p, precision="fp32")
+    a.set_mlp(wts)
+    b = Sim(p, precision="fp32")
+    a.run(15)
+    b.run(15)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_errors_surface_without_fault():
+    p = W.replica("D2Q9", 16, 16, fields=(0,))
+    sim = Sim(p, precision="fp32")
+    with pytest.raises(L.FlbError):
+        sim.correlator(0, 0, 0)         # no samples yet
+    with pytest.raises(L.FlbError):
+        sim.correlator(0, 0, 9)         # field 9 not sampled
+    with pytest.raises(L.FlbError):
+        sim.populations(3)              # replica out of range
