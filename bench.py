@@ -1,0 +1,298 @@
+"""Throughput benchmark of the fluctuating D2Q9 lattice Boltzmann path on GB300.
+
+Default workload ``d2q9_16384``: D2Q9 16384 x 16384, FP32 deviation storage,
+tau_shear = tau_bulk = 0.6, tau_ghost = 1.0, u0 = (0.1, 0.05), kT = 1e-4,
+noise-scale network on (seeded random weights of the 3-32-32-6 architecture),
+rho/u_x/u_y spectra (6 pairs) sampled every 20 steps.  A bench step is one
+lattice Boltzmann step of the whole lattice; sampling is amortised over the
+steps (K a multiple of 20 covers it exactly).
+
+Prints one JSON line (rank 0): MLUPS of the whole job, the HBM roofline of the
+dominant kernel (the fused stream-collide-noise step, 72 algorithmic bytes per
+site: 9 FP32 reads + 9 FP32 writes), the end-to-end number through the public
+API with host buffers, and the oracle's throughput on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 16384]
+Under torchrun every rank runs its own replica (weak scaling, no data-path
+collective); the time is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SAMPLE_EVERY = 20
+ALG_BYTES_PER_SITE = 72          # FP32 deviation storage: 9 reads + 9 writes of 4 B
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384, help="lattice edge (default: the 16384^2 workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-n", type=int, default=256)
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_1010_1233_gb300 import workloads as W
+    wl = W.d2q9_16384(n)
+    return wl, wl["replicas"][0]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [l for l in out.splitlines() if l.strip()]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n, steps, args_threads=1):
+    """Time the FP64 oracle on the host (one thread) on an n x n sample of the workload."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import lb
+from paper_1010_1233_gb300 import workloads as W
+wl = W.d2q9_16384(%d)
+p = dict(wl["replicas"][0])
+w = W.mlp_weights(1234, out_scale=0.1)
+P = lb.Params(**p)
+P.mlp = {k: v.astype(np.float64) for k, v in w.items()}
+r = lb.Run(P)
+r.run(1, %d)
+t0 = time.perf_counter()
+r.run(%d, %d)
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "sites": p["nx"] * p["ny"], "steps": %d}))
+""" % (ROOT, n, SAMPLE_EVERY, steps, SAMPLE_EVERY, steps)
+    env = dict(os.environ, OMP_NUM_THREADS=str(args_threads), OPENBLAS_NUM_THREADS=str(args_threads),
+               MKL_NUM_THREADS=str(args_threads), CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        return {"error": out.stderr[-400:]}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    mlups = d["sites"] * d["steps"] / d["seconds"] / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": args_threads, "kind": "oracle",
+            "sample": f"D2Q9 {n}x{n} FP64 oracle, same taus/u0/network/fields, {steps} steps incl. "
+                      f"{max(1, steps // SAMPLE_EVERY)} direct-DFT samples, {d['seconds']:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.cpu_n
+    per = cpu_baseline(n, max(SAMPLE_EVERY, args.steps // 5) if args.steps > 0 else SAMPLE_EVERY)
+    if "error" in per:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + per["error"][-200:]}))
+        return
+    wl, p = workload(args.n)
+    line = {
+        "impl": "reference", "metric": "D2Q9 fluctuating-LB MLUPS", "value": per["value"], "unit": "MLUPS",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "d2q9_16384 (bounded CPU sample)", "nx": n, "ny": n},
+        "cpu_baseline": per,
+        "e2e": {"value": per["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1010_1233_gb300 import Sim, build
+    from paper_1010_1233_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    wl, p = workload(args.n)
+    p = dict(p, seed=p["seed"] + rank, stream=rank)
+    sim = Sim(p, precision="fp32")
+    wts = W.mlp_weights(1234, out_scale=0.1)
+    sim.set_mlp(wts)
+    stream = sim.stream
+    V = p["nx"] * p["ny"]
+    K, Wm = args.steps, max(3, args.warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim.run(Wm, SAMPLE_EVERY)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.run(K, SAMPLE_EVERY)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * V * K / (ms_max * 1e-3) / 1e6
+    n_samples = sum(1 for s in range(Wm, Wm + K) if s % SAMPLE_EVERY == 0)
+    four_step = 1 if p["ny"] > 2048 else 0
+    launches = K + n_samples * (2 + four_step)
+
+    # dominant kernel alone: plain (non-sampling) steps back to back, same launch configuration
+    Kd = max(20, min(K, 100))
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    sim.run(Kd, 0)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = d0.elapsed_time(d1) / Kd
+    hbm, peak_kind = peaks()
+    achieved = ALG_BYTES_PER_SITE * V / (step_ms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API with host buffers: load a checkpoint from pinned
+        # host memory, run K steps, save the final state (populations + correlator sums) back
+        import ctypes
+        from paper_1010_1233_gb300 import _lib as L
+        lib = L.lib()
+        size = ctypes.c_size_t()
+        L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
+        nb = int(size.value)
+        try:
+            host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+            host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+            pinned = True
+        except Exception:
+            host_in = torch.empty(nb, dtype=torch.uint8)
+            host_out = torch.empty(nb, dtype=torch.uint8)
+            pinned = False
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
+        barrier()
+        t0 = time.perf_counter()
+        L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
+        sim.run(K, SAMPLE_EVERY)
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * V * K / float(tt.item()) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
+               "pinned": pinned, "what": "flb_load(host state) + K steps + flb_save(host state)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_n, args.cpu_steps)
+
+    if rank == 0:
+        line = {
+            "metric": "D2Q9 fluctuating-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "d2q9_16384", "lattice": "D2Q9", "nx": p["nx"], "ny": p["ny"],
+                       "storage": "fp32 deviation f - w rho0, FP64 correlator sums",
+                       "tau_shear": 0.6, "tau_ghost": 1.0, "u0": list(p["u0"]), "kT": p["kT"],
+                       "mlp": "3-32-32-6 seeded random weights", "sample_every": SAMPLE_EVERY,
+                       "fields": ["rho", "u_x", "u_y"], "parallelism": f"replica x{world}",
+                       "l2": "inputs larger than L2 (%.1f GB state), no flush" % (2 * 9 * 4 * V / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_step_d2q9 (fused pull-stream/collide/noise/network)",
+                         "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

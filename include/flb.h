@@ -121,6 +121,12 @@ int flb_get_correlator(flb_ctx* ctx, int replica, int field_a, int field_b,
 int flb_get_populations(flb_ctx* ctx, int replica, double* host_out);
 int flb_set_populations(flb_ctx* ctx, int replica, const double* host_in);
 
+/* Copy the populations of a rectangular window [x0, x0+w) x [y0, y0+h) of a replica
+ * (no wrap-around: the window must lie inside the lattice) to host FP64 [q][h][w].
+ * For sampling outputs of large lattices without copying the whole state.  Synchronises. */
+int flb_get_populations_window(flb_ctx* ctx, int replica, int x0, int y0, int w, int h,
+                               double* host_out);
+
 /* FP64 sums over the lattice of rho, j_x, j_y (j_y = 0 for D1Q3) of the stored
  * state; out[3].  Synchronises. */
 int flb_get_conserved(flb_ctx* ctx, int replica, double* out3);

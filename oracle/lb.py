@@ -171,9 +171,15 @@ def sample_fields(p, f, rho, u):
     return out
 
 
-def collide(p, f, t, return_parts=False):
-    """Collision with noise (Eq. 5) at step t on the pre-collision state f."""
+def collide(p, f, t, return_parts=False, sites=None):
+    """Collision with noise (Eq. 5) at step t on the pre-collision state f.
+
+    sites: global site indices y*nx + x of the entries of f (default: the whole
+    lattice of p); lets a patch of a large lattice be collided on its own.
+    """
     lat = p.lat
+    if sites is None:
+        sites = site_index(p)
     rho, j, u = macroscopic(lat, f)
     M = np.tensordot(lat.m, f, axes=(1, 0))                           # Eq. 3
     Meq = np.tensordot(lat.m, _lat.equilibrium(lat, rho, u), axes=(1, 0))   # Eq. 2 -> moments
@@ -183,7 +189,7 @@ def collide(p, f, t, return_parts=False):
     active = [a for a in lat.nonconserved if (mask >> a) & 1]
     if active:
         n_normals = 6 if lat.name == "D2Q9" else 1
-        N = _rng.site_normals(n_normals, site_index(p), t, 0, p.stream, p.seed)
+        N = _rng.site_normals(n_normals, sites, t, 0, p.stream, p.seed)
         s = noise_scale(p, rho, u)
         for c, a in enumerate(lat.nonconserved):
             if (mask >> a) & 1:

@@ -74,3 +74,42 @@ class Accumulator:
         V = p.nx * (p.ny if p.lat.d == 2 else 1)
         norm = 1.0 / (V * np.sqrt(field_variance(p, a) * field_variance(p, b)))
         return c * norm
+
+
+def dft_at(x, kx, ky):
+    """X(k) for one wave vector by the direct sum over all sites (large lattices)."""
+    ny, nx = x.shape
+    ex = np.exp(-2j * np.pi * kx * np.arange(nx) / nx)
+    ey = np.exp(-2j * np.pi * ky * np.arange(ny) / ny)
+    return ey @ (x.astype(np.complex128) @ ex)
+
+
+class PointAccumulator:
+    """Accumulator restricted to a list of wave vectors (ky, kx), same normalisation."""
+
+    def __init__(self, p, kpoints):
+        self.p = p
+        self.fields = list(p.fields)
+        self.k = list(kpoints)
+        self.n = 0
+        self.X = []
+
+    def add(self, fields):
+        ny = self.p.ny if self.p.lat.d == 2 else 1
+        X = {fid: np.array([dft_at(np.asarray(v).reshape(ny, self.p.nx), kx, ky) for ky, kx in self.k])
+             for fid, v in fields.items()}
+        X0 = {fid: float(np.sum(v)) for fid, v in fields.items()}
+        self.X.append((X, X0))
+        self.n += 1
+
+    def correlator(self, a, b):
+        p = self.p
+        c = sum(X[a] * np.conj(X[b]) for X, _ in self.X) / self.n
+        m_a = sum(X0[a] for _, X0 in self.X) / self.n
+        m_b = sum(X0[b] for _, X0 in self.X) / self.n
+        c = c.copy()
+        for i, (ky, kx) in enumerate(self.k):
+            if kx == 0 and ky == 0:
+                c[i] -= m_a * m_b
+        V = p.nx * (p.ny if p.lat.d == 2 else 1)
+        return c / (V * np.sqrt(field_variance(p, a) * field_variance(p, b)))

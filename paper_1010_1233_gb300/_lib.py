@@ -38,6 +38,7 @@ _SIGS = {
     "flb_get_correlator": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double), POINTER(c_uint64)]),
     "flb_get_populations": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "flb_set_populations": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_get_populations_window": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "flb_get_conserved": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "flb_get_step": (c_int, [c_void_p, POINTER(c_uint64)]),
     "flb_set_mlp": (c_int, [c_void_p, POINTER(c_uint16), POINTER(c_float), c_int]),

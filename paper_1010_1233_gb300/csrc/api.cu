@@ -15,9 +15,9 @@ namespace flb {
 // launchers (lb_step.cu, spectra.cu)
 void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool sample, bool mlp, cudaStream_t st);
 void launch_init(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
-                 double* sums, int64_t V, cudaStream_t st);
+                 double* sums, double* partial, int64_t V, cudaStream_t st);
 void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity,
-                      double* sums, DevStatus* status, int64_t V, cudaStream_t st);
+                      double* sums, double* partial, DevStatus* status, int64_t V, cudaStream_t st);
 void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,
                    uint64_t seed, int fp32, uint32_t* words, double* normals, cudaStream_t st);
 size_t mlp_weights_bytes();
@@ -29,6 +29,8 @@ void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 
@@ -63,14 +65,24 @@ static constexpr int kColsSmemBudget = 200 * 1024;
 
 struct Layout {
   std::vector<ReplicaDesc> desc;
-  int64_t off_descs = 0, off_vb_step = 0, off_vb_rows = 0, off_vb_cols = 0;
-  int64_t off_status = 0, off_sums = 0, off_feq0 = 0, off_mlp = 0;
+  int64_t off_descs = 0, off_vb_step = 0, off_vb_rows = 0, off_vb_cols = 0, off_vb_cols_a = 0;
+  int64_t off_status = 0, off_sums = 0, off_partial = 0, off_feq0 = 0, off_mlp = 0;
   int64_t total = 0;
-  int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0;
-  std::vector<int64_t> vb_step, vb_rows, vb_cols;
+  int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0, n_vb_cols_a = 0;
+  std::vector<int64_t> vb_step, vb_rows, vb_cols, vb_cols_a;
   int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
   bool any_fields = false;
 };
+
+// Column FFT split: one pass of length ny when F columns of 4 fit the shared-memory
+// budget, otherwise the four-step split with N1 = 2^floor(log2(ny)/2).
+static int column_split(int precision, int F, int ny) {
+  const int cs = precision == FLB_FP64 ? 16 : 8;
+  if ((int64_t)F * ny * 4 * cs <= kColsSmemBudget) return 0;
+  int l = 0;
+  while ((1 << l) < ny) ++l;
+  return l / 2;
+}
 
 static int field_valid(int lattice, int f) {
   if (lattice == FLB_D2Q9) return f >= 0 && f <= 10;
@@ -107,7 +119,9 @@ static int validate(int precision, const flb_replica* reps, int n) {
       if (!is_pow2(p.nx) || !is_pow2(p.ny)) return set_error(FLB_EINVAL, "replica %d: sampling needs power-of-two nx, ny", r);
       if (fft_rows_smem(precision, p.nx) > 227 * 1024) return set_error(FLB_EINVAL, "replica %d: nx too large for the row FFT", r);
       const int F = __builtin_popcount(p.field_mask);
-      if (fft_cols_smem(precision, F, p.ny, 1) > kColsSmemBudget)
+      const int l1 = column_split(precision, F, p.ny);
+      const int len = std::max(1 << l1, p.ny >> l1);
+      if (fft_cols_smem(precision, F, len, 1) > kColsSmemBudget)
         return set_error(FLB_EINVAL, "replica %d: ny = %d too long for the column FFT with %d fields", r, p.ny, F);
     }
     if (p.init_mode == 1 && p.kT > 0 && (int64_t)p.nx * p.ny < 2) return set_error(FLB_EINVAL, "thermal init needs V >= 2");
@@ -149,6 +163,7 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   d.n_pairs = np;
   d.half_nx = p.nx / 2 + 1;
   d.wpitch = (d.half_nx + 1) & ~1;
+  d.log2n1 = F ? column_split(precision, F, p.ny) : 0;
 }
 
 static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
@@ -166,7 +181,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   }
   L.desc.resize(n);
   int64_t off = 0;
-  int maxF = 0, maxny = 1, maxnx = 2;
+  int maxF = 0, maxlen = 1, maxnx = 2;
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
     fill_desc(precision, reps[r], d);
@@ -176,7 +191,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     if (d.n_fields) {
       L.any_fields = true;
       maxF = std::max(maxF, (int)d.n_fields);
-      maxny = std::max(maxny, d.ny);
+      maxlen = std::max(maxlen, std::max(1 << d.log2n1, d.ny >> d.log2n1));
       maxnx = std::max(maxnx, d.nx);
       d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs);
       d.off_spec = off; off = align256(off + (int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
@@ -193,14 +208,14 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     d.n_units = (int64_t)d.units_per_row * d.ny;
   }
   // virtual-block prefixes of the three launches
-  L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n);
+  L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
   if (L.any_fields) {
     const int cs = precision == FLB_FP64 ? 16 : 8;
     L.ncol = 16;
-    while (L.ncol > 1 && (int64_t)maxF * maxny * L.ncol * cs > kColsSmemBudget) L.ncol >>= 1;
+    while (L.ncol > 1 && (int64_t)maxF * maxlen * L.ncol * cs > kColsSmemBudget) L.ncol >>= 1;
     L.rows_smem = maxnx * cs;
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
-    L.cols_smem = maxF * maxny * L.ncol * cs;
+    L.cols_smem = maxF * maxlen * L.ncol * cs;
   }
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
@@ -208,17 +223,22 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.n_vb_step += (d.n_units + kStepBlock - 1) / kStepBlock;
     L.vb_rows[r] = L.n_vb_rows;
     L.vb_cols[r] = L.n_vb_cols;
+    L.vb_cols_a[r] = L.n_vb_cols_a;
     if (d.n_fields) {
+      const int64_t tiles = (d.half_nx + L.ncol - 1) / L.ncol;
       L.n_vb_rows += (int64_t)((d.n_fields + 1) / 2) * d.ny;
-      L.n_vb_cols += (d.half_nx + L.ncol - 1) / L.ncol;
+      L.n_vb_cols += tiles << d.log2n1;                       // (k1, tile)
+      if (d.log2n1) L.n_vb_cols_a += tiles * (d.ny >> d.log2n1);   // (y2, tile)
     }
   }
   L.off_descs = off; off = align256(off + n * (int64_t)sizeof(ReplicaDesc));
   L.off_vb_step = off; off = align256(off + 8 * (int64_t)n);
   L.off_vb_rows = off; off = align256(off + 8 * (int64_t)n);
   L.off_vb_cols = off; off = align256(off + 8 * (int64_t)n);
+  L.off_vb_cols_a = off; off = align256(off + 8 * (int64_t)n);
   L.off_status = off; off = align256(off + (int64_t)sizeof(DevStatus));
   L.off_sums = off; off = align256(off + 8 * 3 * (int64_t)n);
+  L.off_partial = off; off = align256(off + 8 * 3 * (int64_t)kReduceBlocks);
   L.off_feq0 = off; off = align256(off + 8 * 18 * (int64_t)n);
   L.off_mlp = off; off = align256(off + (int64_t)mlp_weights_bytes());
   L.total = off;
@@ -313,6 +333,7 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_step, Lc.vb_step.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_rows, Lc.vb_rows.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_cols, Lc.vb_cols.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_cols_a, Lc.vb_cols_a.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
   std::vector<double> feq(18 * (size_t)n_replicas);
   for (int r = 0; r < n_replicas; ++r) feq0_host(reps[r], precision, &feq[18 * (size_t)r]);
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_feq0, feq.data(), feq.size() * 8, cudaMemcpyHostToDevice, st), "copy feq0");
@@ -325,7 +346,8 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
     rc = cuda_check(cudaMemsetAsync(sums, 0, 24, st), "sums");
     if (rc) break;
     launch_init(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode,
-                reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + 18 * r, sums, V, st);
+                reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + 18 * r, sums,
+                reinterpret_cast<double*>(c->ws + Lc.off_partial), V, st);
     if (d.n_fields) {
       launch_twiddles(precision, c->ws + d.off_tw_x, d.nx, st);
       launch_twiddles(precision, c->ws + d.off_tw_y, d.ny, st);
@@ -353,6 +375,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   S.grid = (int)std::min<int64_t>(L.n_vb_step, (int64_t)c->sms * 16);
   const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
   const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
+  const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
   for (uint64_t i = 0; i < n_steps; ++i) {
     const uint64_t t = c->step;
     const bool sample = sample_every && L.any_fields && (t % sample_every) == 0;
@@ -362,6 +385,9 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
     if (sample) {
       launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
                       L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, c->stream);
+      if (L.n_vb_cols_a)
+        launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
+                          L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, c->stream);
       launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
                       L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, c->stream);
       ++c->n_samples;
@@ -460,6 +486,35 @@ int flb_get_populations(flb_ctx* c, int replica, double* host_out) {
   return FLB_OK;
 }
 
+int flb_get_populations_window(flb_ctx* c, int replica, int x0, int y0, int w, int h, double* host_out) {
+  if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  const ReplicaDesc& d = c->L.desc[replica];
+  if (w <= 0 || h <= 0 || x0 < 0 || y0 < 0 || x0 + w > d.nx || y0 + h > d.ny)
+    return set_error(FLB_EINVAL, "window [%d,%d)x[%d,%d) outside the %dx%d lattice", x0, x0 + w, y0, y0 + h, d.nx, d.ny);
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  const int64_t V = (int64_t)d.nx * d.ny;
+  const size_t rs = c->precision == FLB_FP64 ? 8 : 4;
+  const char* src = c->ws + d.off_pop[c->step & 1];
+  std::vector<char> tmp((size_t)d.q * w * h * rs);
+  for (int i = 0; i < d.q; ++i) {
+    rc = cuda_check(cudaMemcpy2D(tmp.data() + (size_t)i * w * h * rs, w * rs,
+                                 src + ((size_t)i * V + (size_t)y0 * d.nx + x0) * rs, (size_t)d.nx * rs,
+                                 w * rs, h, cudaMemcpyDeviceToHost), "read window");
+    if (rc) return rc;
+  }
+  for (int i = 0; i < d.q; ++i) {
+    const double wr = c->precision == FLB_FP64 ? 0.0 : (d.q == 9 ? kW9[i] : kW3[i]) * d.rho0;
+    for (size_t s = 0; s < (size_t)w * h; ++s) {
+      const size_t k = (size_t)i * w * h + s;
+      host_out[k] = rs == 8 ? reinterpret_cast<const double*>(tmp.data())[k]
+                            : wr + (double)reinterpret_cast<const float*>(tmp.data())[k];
+    }
+  }
+  return FLB_OK;
+}
+
 int flb_set_populations(flb_ctx* c, int replica, const double* host_in) {
   if (!c || !host_in) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
@@ -483,11 +538,10 @@ int flb_get_conserved(flb_ctx* c, int replica, double* out3) {
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
   double* sums = reinterpret_cast<double*>(c->ws + c->L.off_sums) + 3 * replica;
-  int rc = cuda_check(cudaMemsetAsync(sums, 0, 24, c->stream), "sums");
-  if (rc) return rc;
-  launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, status_dev(c),
-                   (int64_t)d.nx * d.ny, c->stream);
-  rc = cuda_check(cudaGetLastError(), "conserved launch");
+  launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums,
+                   reinterpret_cast<double*>(c->ws + c->L.off_partial), status_dev(c), (int64_t)d.nx * d.ny,
+                   c->stream);
+  int rc = cuda_check(cudaGetLastError(), "conserved launch");
   if (rc) return rc;
   rc = flb_sync(c);
   if (rc) return rc;

@@ -13,6 +13,7 @@ namespace flb {
 
 constexpr int kMaxFields = FLB_MAX_FIELDS;
 constexpr int kMaxPairs = kMaxFields * (kMaxFields + 1) / 2;
+constexpr int kReduceBlocks = 2048;   // partial sums of the deterministic reductions
 constexpr int kMlpHidden = 32;
 constexpr int kMlpOut = 6;
 constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden;  // 1312
@@ -43,6 +44,7 @@ struct ReplicaDesc {
   int64_t off_tw_x, off_tw_y;       // twiddles exp(-2 pi i m / n), m < n/2, complex Real
   int32_t half_nx;                  // nx / 2 + 1
   int32_t wpitch;                   // pitch (complex elements) of spec rows
+  int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
 };
 
 struct DevStatus {
@@ -77,8 +79,9 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1
   return make_uint4(c0, c1, c2, c3);
 }
 
-// Box-Muller on a word pair.  FP64: u = (w + 1/2) 2^-32.  FP32: u = ((w >> 9) + 1/2) 2^-23,
-// the top 23 bits, so that u is exact in FP32 and strictly inside (0, 1).
+// Box-Muller on a word pair.  FP64: u = (w + 1/2) 2^-32 (exact).  FP32: u = RN(w) 2^-32 + 2^-33,
+// which keeps a relative error <= 2^-24 for every u (small u included, where the log is
+// sensitive); u can round up to 1 only where the normal's radius is ~1e-4 anyway.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
   const double ua = ((double)wa + 0.5) * 0x1p-32;
   const double ub = ((double)wb + 0.5) * 0x1p-32;
@@ -89,8 +92,8 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0,
 }
 
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
-  const float ua = ((float)(wa >> 9) + 0.5f) * 0x1p-23f;
-  const float ub = ((float)(wb >> 9) + 0.5f) * 0x1p-23f;
+  const float ua = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
+  const float ub = fmaf(__uint2float_rn(wb), 0x1p-32f, 0x1p-33f);
   const float r = sqrtf(-2.0f * logf(ua));
   float s, c;
   sincospif(2.0f * ub, &s, &c);

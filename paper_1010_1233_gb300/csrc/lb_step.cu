@@ -323,7 +323,39 @@ __device__ __forceinline__ void thermal_normals(const ReplicaDesc& d, uint32_t s
   }
 }
 
-__global__ void k_thermal_sum(const ReplicaDesc* __restrict__ descs, int r, double* __restrict__ sums) {
+// Deterministic block reduction of three sums: each block writes its partial sums
+// (fixed site set, fixed shuffle tree); k_finish_sums adds the partials in order.
+__device__ __forceinline__ void block_sum3(double (&acc)[3], double* __restrict__ partial) {
+  __shared__ double red[32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 3; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < 3; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < nw; ++w) v += red[w][k];
+      partial[3 * blockIdx.x + k] = v;
+    }
+  }
+}
+
+__global__ void k_finish_sums(const double* __restrict__ partial, int nblocks, double* __restrict__ sums,
+                              DevStatus* status, int r) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < 3; ++k) {
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partial[3 * b + k];
+    sums[k] = v;
+    if (status && !isfinite(v) && status->error == 0) { status->error = FLB_EUNSTABLE; status->replica = r; }
+  }
+}
+
+__global__ void k_thermal_sum(const ReplicaDesc* __restrict__ descs, int r, double* __restrict__ partial) {
   const ReplicaDesc& d = descs[r];
   const int64_t V = (int64_t)d.nx * d.ny;
   double acc[3] = {0, 0, 0};
@@ -333,11 +365,7 @@ __global__ void k_thermal_sum(const ReplicaDesc* __restrict__ descs, int r, doub
     acc[0] += N[0]; acc[1] += N[1];
     if (d.q == 9) acc[2] += N[2];
   }
-  for (int k = 0; k < 3; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], v);
-  }
+  block_sum3(acc, partial);
 }
 
 template <typename R, bool DEV>
@@ -387,10 +415,10 @@ __global__ void k_init(const ReplicaDesc* __restrict__ descs, int r, char* __res
   }
 }
 
-// FP64 lattice sums of rho, j_x, j_y of the stored state; flags a non-finite sum.
+// FP64 lattice sums of rho, j_x, j_y of the stored state (per-block partials).
 template <typename R, bool DEV>
 __global__ void k_conserved(const ReplicaDesc* __restrict__ descs, int r, const char* __restrict__ ws,
-                            int parity, double* __restrict__ sums, DevStatus* status) {
+                            int parity, double* __restrict__ partial) {
   const ReplicaDesc& d = descs[r];
   const int64_t V = (int64_t)d.nx * d.ny;
   const R* p = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
@@ -410,14 +438,7 @@ __global__ void k_conserved(const ReplicaDesc* __restrict__ descs, int r, const 
       acc[1] += b - c;
     }
   }
-  for (int k = 0; k < 3; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&sums[k], v);
-      if (!isfinite(v) && atomicCAS(&status->error, 0, FLB_EUNSTABLE) == 0) status->replica = r;
-    }
-  }
+  block_sum3(acc, partial);
 }
 
 // Diagnostics: the generator exactly as the step kernels call it.
@@ -473,20 +494,24 @@ void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool 
 }
 
 void launch_init(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
-                 double* sums, int64_t V, cudaStream_t st) {
+                 double* sums, double* partial, int64_t V, cudaStream_t st) {
   const int block = 256;
-  const int grid = (int)((V + block - 1) / block < 4096 ? (V + block - 1) / block : 4096);
-  if (mode == 1) k_thermal_sum<<<grid, block, 0, st>>>(descs, r, sums);
+  const int grid = (int)((V + block - 1) / block < kReduceBlocks ? (V + block - 1) / block : kReduceBlocks);
+  if (mode == 1) {
+    k_thermal_sum<<<grid, block, 0, st>>>(descs, r, partial);
+    k_finish_sums<<<1, 32, 0, st>>>(partial, grid, sums, nullptr, r);
+  }
   if (precision == FLB_FP64) k_init<double, false><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
   else k_init<float, true><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
 }
 
 void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity,
-                      double* sums, DevStatus* status, int64_t V, cudaStream_t st) {
+                      double* sums, double* partial, DevStatus* status, int64_t V, cudaStream_t st) {
   const int block = 256;
-  const int grid = (int)((V + block - 1) / block < 2048 ? (V + block - 1) / block : 2048);
-  if (precision == FLB_FP64) k_conserved<double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, sums, status);
-  else k_conserved<float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, sums, status);
+  const int grid = (int)((V + block - 1) / block < kReduceBlocks ? (V + block - 1) / block : kReduceBlocks);
+  if (precision == FLB_FP64) k_conserved<double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  else k_conserved<float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  k_finish_sums<<<1, 32, 0, st>>>(partial, grid, sums, status, r);
 }
 
 void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,

@@ -7,7 +7,11 @@
 // transformed along x in shared memory, and unpacked into the row transforms
 // of both fields, X_a(kx) = (Z(kx) + Z(-kx)^*)/2, X_b(kx) = (Z(kx) - Z(-kx)^*)/(2i).
 // Pass 2 (columns): tiles of columns of every field are transformed along y in
-// shared memory and the pair products are added to the FP64 sums.
+// shared memory and the pair products are added to the FP64 sums.  Columns too
+// long for shared memory use the four-step split ny = N1 N2, y = N2 y1 + y2,
+// ky = k1 + N1 k2:  X(ky) = sum_y2 W_N2^(y2 k2) W_N^(y2 k1) sum_y1 W_N1^(y1 k1) x(y);
+// pass 2a does the inner length-N1 transforms and the W_N^(y2 k1) twiddle in
+// place (rows N2 y1 + y2 -> N2 k1 + y2), pass 2b the outer length-N2 transforms.
 #include "flb_internal.cuh"
 
 namespace flb {
@@ -20,9 +24,10 @@ template <typename R> __device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
 
 // In-place radix-2 decimation-in-time FFTs on n_fft sequences of length 2^logn in
 // shared memory, sequence k at data + k * seq_stride, already in bit-reversed order.
-// tw[m] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  All threads of the block call it.
+// tw[m * tw_stride] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  All threads of the block call it.
 template <typename R>
-__device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C<R>* __restrict__ tw) {
+__device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C<R>* __restrict__ tw,
+                        int tw_stride) {
   if (logn == 0) return;
   const int half_n = 1 << (logn - 1);
   const int total = n_fft * half_n;
@@ -35,7 +40,7 @@ __device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C
       const int pos = j & (half - 1);
       const int i0 = ((j >> s) << (s + 1)) + pos;
       C<R>* d = data + k * seq_stride;
-      const C<R> w = tw[pos << tshift];
+      const C<R> w = tw[(pos << tshift) * tw_stride];
       const C<R> a = d[i0];
       const C<R> t = cmul<R>(d[i0 + half], w);
       C<R> u, v;
@@ -84,7 +89,7 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
       z[brev(x, logn)] = v;
     }
     __syncthreads();
-    dit_fft<R>(z, logn, 1, 0, reinterpret_cast<const C<R>*>(ws + d.off_tw_x));
+    dit_fft<R>(z, logn, 1, 0, reinterpret_cast<const C<R>*>(ws + d.off_tw_x), 1);
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     C<R>* ra = spec + fa * fplane + (int64_t)y * d.wpitch;
@@ -104,7 +109,52 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
   }
 }
 
-// Pass 2: one block per (replica, tile of ncol columns); all fields of the tile.
+// Pass 2a (four-step only): one block per (replica, y2, tile of ncol columns).
+template <typename R>
+__global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
+                             int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C<R>* s = reinterpret_cast<C<R>*>(smem_raw);
+  for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
+    const int r = find_rep(vb_begin, n_reps, vb);
+    const ReplicaDesc& d = descs[r];
+    const int tiles = (d.half_nx + ncol - 1) / ncol;
+    const int64_t local = vb - vb_begin[r];
+    const int y2 = (int)(local / tiles);
+    const int kx0 = (int)(local % tiles) * ncol;
+    const int ncl = min(ncol, d.half_nx - kx0);
+    const int logn1 = d.log2n1, n1 = 1 << logn1, n2 = d.ny >> logn1, F = (int)d.n_fields;
+    C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
+    const int64_t fplane = (int64_t)d.ny * d.wpitch;
+    const int total = F * n1 * ncol;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int c = i % ncol;
+      const int y1 = (i / ncol) % n1;
+      const int f = i / (ncol * n1);
+      C<R> v; v.x = (R)0; v.y = (R)0;
+      if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
+      s[(f * ncol + c) * n1 + brev(y1, logn1)] = v;
+    }
+    __syncthreads();
+    const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_y);
+    dit_fft<R>(s, logn1, F * ncol, n1, tw, n2);
+    const int hn = d.ny >> 1;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int c = i % ncol;
+      const int k1 = (i / ncol) % n1;
+      const int f = i / (ncol * n1);
+      if (c >= ncl) continue;
+      const int e = y2 * k1;                       // < ny
+      C<R> w = tw[e < hn ? e : e - hn];
+      if (e >= hn) { w.x = -w.x; w.y = -w.y; }
+      spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c] = cmul<R>(s[(f * ncol + c) * n1 + k1], w);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2b: one block per (replica, k1, tile of ncol columns); all fields of the tile.
+// One-pass columns are the case N1 = 1.
 template <typename R>
 __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
                                int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol) {
@@ -113,35 +163,40 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
-    const int kx0 = (int)(vb - vb_begin[r]) * ncol;
-    const int ny = d.ny, logn = d.log2ny, F = (int)d.n_fields;
+    const int tiles = (d.half_nx + ncol - 1) / ncol;
+    const int64_t local = vb - vb_begin[r];
+    const int k1 = (int)(local / tiles);
+    const int kx0 = (int)(local % tiles) * ncol;
+    const int logn1 = d.log2n1, n1 = 1 << logn1, logn2 = d.log2ny - logn1, n2 = d.ny >> logn1;
+    const int F = (int)d.n_fields;
     const int ncl = min(ncol, d.half_nx - kx0);
     const C<R>* spec = reinterpret_cast<const C<R>*>(ws + d.off_spec);
-    const int64_t fplane = (int64_t)ny * d.wpitch;
-    // smem layout: [field][column][ny]
-    const int total = F * ny * ncol;
+    const int64_t fplane = (int64_t)d.ny * d.wpitch;
+    // smem layout: [field][column][n2]
+    const int total = F * n2 * ncol;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
       const int c = i % ncol;
-      const int y = (i / ncol) % ny;
-      const int f = i / (ncol * ny);
+      const int y2 = (i / ncol) % n2;
+      const int f = i / (ncol * n2);
       C<R> v; v.x = (R)0; v.y = (R)0;
-      if (c < ncl) v = spec[f * fplane + (int64_t)y * d.wpitch + kx0 + c];
-      s[(f * ncol + c) * ny + brev(y, logn)] = v;
+      if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
+      s[(f * ncol + c) * n2 + brev(y2, logn2)] = v;
     }
     __syncthreads();
-    dit_fft<R>(s, logn, F * ncol, ny, reinterpret_cast<const C<R>*>(ws + d.off_tw_y));
+    dit_fft<R>(s, logn2, F * ncol, n2, reinterpret_cast<const C<R>*>(ws + d.off_tw_y), n1);
     // accumulate pair products in FP64; k = 0 sums for the mean subtraction
-    const int npts = ny * ncol;
+    const int npts = n2 * ncol;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
       const int c = i % ncol;
-      const int ky = i / ncol;
+      const int k2 = i / ncol;
       if (c >= ncl) continue;
       const int kx = kx0 + c;
+      const int ky = k1 + n1 * k2;
       const int64_t pt = (int64_t)ky * d.half_nx + kx;
       for (int pr = 0; pr < d.n_pairs; ++pr) {
         const int a = d.pair_a[pr], b = d.pair_b[pr];
-        const C<R> Xa = s[(a * ncol + c) * ny + ky];
-        const C<R> Xb = s[(b * ncol + c) * ny + ky];
+        const C<R> Xa = s[(a * ncol + c) * n2 + k2];
+        const C<R> Xb = s[(b * ncol + c) * n2 + k2];
         const double xr = (double)Xa.x, xi = (double)Xa.y, yr = (double)Xb.x, yi = (double)Xb.y;
         if (a == b) {
           double* acc = reinterpret_cast<double*>(ws + d.pair_off[pr]);
@@ -156,7 +211,7 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
       }
       if (kx == 0 && ky == 0) {
         double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
-        for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol + c) * ny].x;
+        for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol + c) * n2].x;
       }
     }
     __syncthreads();
@@ -192,6 +247,8 @@ cudaError_t set_fft_smem_limits() {
   if ((e = cudaFuncSetAttribute(k_fft_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_acc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
+  if ((e = cudaFuncSetAttribute(k_fft_cols_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
+  if ((e = cudaFuncSetAttribute(k_fft_cols_a<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   return cudaFuncSetAttribute(k_fft_cols_acc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
 }
 
@@ -201,6 +258,14 @@ void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_
     k_fft_rows<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws);
   else
     k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws);
+}
+
+void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st) {
+  if (precision == FLB_FP64)
+    k_fft_cols_a<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
+  else
+    k_fft_cols_a<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
 }
 
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,

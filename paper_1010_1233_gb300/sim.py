@@ -85,6 +85,8 @@ class Sim:
 
     # -- results ----------------------------------------------------------
     def _shape(self, r):
+        if not 0 <= r < len(self.params):
+            raise L.FlbError(L.FLB_EINVAL, f"replica {r} out of range")
         p = self.params[r]
         return (p["ny"] if p["lattice"] == "D2Q9" else 1, p["nx"])
 
@@ -103,6 +105,15 @@ class Sim:
         q = 9 if self.params[r]["lattice"] == "D2Q9" else 3
         out = np.empty((q, ny, nx))
         L.check(L.lib().flb_get_populations(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def populations_window(self, x0, y0, w, h, r=0):
+        """Populations [q][h][w] of the window starting at (x0, y0) (inside the lattice)."""
+        self._shape(r)
+        q = 9 if self.params[r]["lattice"] == "D2Q9" else 3
+        out = np.empty((q, h, w))
+        L.check(L.lib().flb_get_populations_window(self._ctx, r, x0, y0, w, h,
+                                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
     def set_populations(self, f, r=0):

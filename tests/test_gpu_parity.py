@@ -1,4 +1,6 @@
 """CUDA path against the FP64 oracle, element by element, through the C ABI (GPU)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -21,7 +23,8 @@ def _oracle(p, **kw):
 
 
 def _rel(a, b, ref):
-    return np.abs(a - b).max() / max(np.abs(ref).max(), 1e-300)
+    """max |a - b| relative to max |ref| (ref = the oracle's deviation from equilibrium)."""
+    return np.abs(a - b).max() / max(np.abs(ref).max(), 1e-12)
 
 
 # ---------------------------------------------------------------------------- generator
@@ -59,7 +62,7 @@ def test_fp64_step_matches_oracle_every_step(lat, nx, ny, kw):
     sim = Sim(p, precision="fp64")
     ref = _oracle(p)
     feq = lb.uniform_state(ref.p)
-    assert _rel(sim.populations(), ref.f, ref.f - feq) < 1e-14
+    assert np.abs(sim.populations() - ref.f).max() < 1e-15 * np.abs(ref.f).max()
     worst = 0.0
     for _ in range(100):
         sim.run(1)
@@ -180,7 +183,11 @@ def test_mlp_scaled_noise_matches_oracle():
     ref.run(10)
     feq = lb.uniform_state(ref.p)
     err = _rel(sim.populations(), ref.f, ref.f - feq)
-    assert err < FP32_TOL, err
+    # Both sides round the network's operands to bfloat16, but from FP32 (kernel) and FP64
+    # (oracle) pre-activations: a value within ~1e-7 of a rounding tie can round to the
+    # neighbouring bfloat16 (one ulp, 2^-8..2^-7 relative).  One such flip moves s_c by
+    # |W3| ulp(h) ~ 0.09 * 0.008 ~ 7e-4 at one site, i.e. ~1e-4 of the maximal deviation.
+    assert err < 1e-3, err
     # the network really changes the dynamics
     plain = _oracle(p)
     plain.run(10)
@@ -209,3 +216,23 @@ def test_errors_surface_without_fault():
         sim.correlator(0, 0, 9)         # field 9 not sampled
     with pytest.raises(L.FlbError):
         sim.populations(3)              # replica out of range
+    buf = np.zeros(9 * 16 * 16)
+    rc = L.lib().flb_get_populations(sim._ctx, 3, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert rc == L.FLB_EINVAL and not buf.any()
+    assert L.lib().flb_run(sim._ctx, 1, 0) == 0 and sim.step == 1
+
+
+@pytest.mark.parametrize("precision,nx,ny,tol", [("fp64", 8, 2048, 1e-10), ("fp32", 8, 4096, 2e-4)])
+def test_four_step_column_fft_matches_oracle(precision, nx, ny, tol):
+    # columns too long for shared memory take the N1 x N2 split
+    fields = (0, W.FIELD_UX, W.FIELD_UY)
+    p = W.replica("D2Q9", nx, ny, W.taus_d2q9(0.7, 0.8, 1.2), kT=1e-3, u0=(0.05, 0.1), seed=31,
+                  init_mode=1, fields=fields)
+    sim = Sim(p, precision=precision)
+    ref = _oracle(p)
+    sim.run(6, sample_every=2)
+    ref.run(6, sample_every=2)
+    for a, b in spectra.pairs(fields):
+        o = ref.acc.correlator(a, b)
+        err = np.abs(sim.correlator(0, a, b) - o).max() / max(1.0, np.abs(o).max())
+        assert err < tol, (a, b, err)

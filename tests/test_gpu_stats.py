@@ -1,0 +1,79 @@
+"""Equal-time spectra measured by the CUDA path against the exact linear theory (GPU).
+
+The linear theory of the oracle (discrete Lyapunov equation per wave vector)
+gives the stationary S_ab(k) with no sampling noise: delta_ab at u0 = 0 with
+ghost noise (Eq. 7), the non-trivial Ladd spectra without it (Figs. 1-3), and
+the Galilean-invariance violation at u0 != 0 (Fig. 4).  Batch means give a
+standard error per (k, pair); every included point must be within 5 of them.
+"""
+import numpy as np
+import pytest
+
+from oracle import lb, spectra, theory
+from paper_1010_1233_gb300 import Sim, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LADD = (1 << 3) | (1 << 4) | (1 << 5)
+
+
+def measure(p, precision, batches, steps, warmup, every=1):
+    sim = Sim(p, precision=precision)
+    sim.run(warmup)
+    out = {pr: [] for pr in spectra.pairs(p["fields"])}
+    for _ in range(batches):
+        sim.reset_stats()
+        sim.run(steps, every)
+        for pr in out:
+            out[pr].append(sim.correlator(0, *pr))
+    return {pr: (np.mean(v, 0), np.std(v, 0, ddof=1) / np.sqrt(len(v))) for pr, v in out.items()}
+
+
+def compare(p, meas, floor=2e-3):
+    P = lb.Params(**p)
+    S, ex = theory.theory_spectra(P, p["fields"])
+    zmax, dmax = 0.0, 0.0
+    for pr, (m, se) in meas.items():
+        d = np.abs(m - S[pr])[~ex]
+        z = d / np.maximum(se[~ex], floor)
+        zmax, dmax = max(zmax, z.max()), max(dmax, d.max())
+    return zmax, dmax, S, ex
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ideal_gas_flat_spectra(precision):
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8, 0.8, 1.0), kT=1e-4, seed=7, init_mode=1,
+                  fields=(0, 3, 6, W.FIELD_UX, W.FIELD_UY))
+    meas = measure(p, precision, 20, 20000, 0)
+    zmax, dmax, _, _ = compare(p, meas)
+    print(f"{precision}: max |S - delta| = {dmax:.4f}, max z = {zmax:.2f}")
+    assert zmax < 5.0 and dmax < 0.05
+
+
+def test_ladd_spectra():
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(1.0), kT=1e-4, seed=8, noise_mask=LADD,
+                  fields=(0, W.FIELD_UX, W.FIELD_UY))
+    meas = measure(p, "fp32", 20, 20000, 2000)
+    zmax, dmax, S, ex = compare(p, meas)
+    rmax = np.abs(meas[(9, 10)][0])[~ex].max()
+    print(f"Ladd: max |S - theory| = {dmax:.4f}, max z = {zmax:.2f}, max |R_xy| = {rmax:.3f}")
+    assert zmax < 5.0
+    assert 0.2 < rmax < 0.3                    # Sec. 3: up to about 0.25 without ghost noise
+
+
+def test_moving_frame_violation():
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8, 0.8, 1.0), kT=1e-4, seed=9, u0=(0.2, 0.0),
+                  init_mode=1, fields=(0, W.FIELD_UX, W.FIELD_UY))
+    meas = measure(p, "fp32", 20, 20000, 2000)
+    zmax, dmax, S, ex = compare(p, meas)
+    viol = max(np.abs(S[pr] - (pr[0] == pr[1]))[~ex].max() for pr in S)
+    print(f"u0 = 0.2: max |S - theory| = {dmax:.4f}, max z = {zmax:.2f}, predicted violation {viol:.3f}")
+    assert zmax < 5.0 and viol > 0.1
+
+
+def test_d1q3_config():
+    p = W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1))
+    meas = measure(p, "fp64", 20, 5000, 1000)
+    zmax, dmax, _, _ = compare(p, meas)
+    print(f"D1Q3 L=64: max |S - delta| = {dmax:.4f}, max z = {zmax:.2f}")
+    assert zmax < 5.0

@@ -47,3 +47,17 @@ def test_correlator_hermitian_symmetry():
     Cm = np.roll(np.flip(C, (0, 1)), 1, (0, 1))        # C(-k)
     assert np.abs(C - np.conj(Cm)).max() < 1e-13 * np.abs(C).max()
     assert np.abs(acc.correlator(9, 0) - np.conj(C)).max() < 1e-15
+
+
+def test_point_accumulator_equals_full_grid():
+    d = W.replica(nx=8, ny=4, kT=0.01, fields=[0, 9])
+    p = lb.Params(**d)
+    ks = [(0, 0), (1, 3), (3, 7), (2, 4)]
+    full, pts = spectra.Accumulator(p), spectra.PointAccumulator(p, ks)
+    for s in range(4):
+        f = {0: W.random_perturbation((4, 8), s) + 1.0, 9: W.random_perturbation((4, 8), 20 + s)}
+        full.add(f)
+        pts.add(f)
+    for a, b in ((0, 0), (0, 9), (9, 9)):
+        C = full.correlator(a, b)
+        assert np.abs(pts.correlator(a, b) - np.array([C[ky, kx] for ky, kx in ks])).max() < 1e-12
