@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--n", type=int, default=16384, help="lattice edge (default: the 16384^2 workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-steps", type=int, default=400)
     ap.add_argument("--cpu-n", type=int, default=256)
     return ap.parse_args()
 

@@ -73,7 +73,7 @@ def test_moving_frame_violation():
 
 def test_d1q3_config():
     p = W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1))
-    meas = measure(p, "fp64", 20, 5000, 1000)
+    meas = measure(p, "fp64", 20, 20000, 2000)
     zmax, dmax, _, _ = compare(p, meas)
     print(f"D1Q3 L=64: max |S - delta| = {dmax:.4f}, max z = {zmax:.2f}")
     assert zmax < 5.0
