@@ -184,6 +184,7 @@ def run_ours(args):
     sim = Sim(p, precision="fp32")
     wts = W.mlp_weights(1234, out_scale=0.1)
     sim.set_mlp(wts)
+    tuned = sim.autotune(trials=5)
     stream = sim.stream
     V = p["nx"] * p["ny"]
     K, Wm = args.steps, max(3, args.warmup)
@@ -274,7 +275,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
                          "kernel": "k_step_d2q9 (fused pull-stream/collide/noise/network)",
-                         "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms},
+                         "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms,
+                         "launch": {"vec": tuned[0], "grid": tuned[1], "block": 256}},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,

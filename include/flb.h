@@ -127,6 +127,11 @@ int flb_set_populations(flb_ctx* ctx, int replica, const double* host_in);
 int flb_get_populations_window(flb_ctx* ctx, int replica, int x0, int y0, int w, int h,
                                double* host_out);
 
+/* The fields of the most recent sample of a replica (Eq. 11 inputs, before the
+ * transform): host FP64 [n_fields][ny][nx], fields in increasing id order.
+ * FLB_ESTATE before the first sample.  Synchronises. */
+int flb_get_fields(flb_ctx* ctx, int replica, double* host_out);
+
 /* FP64 sums over the lattice of rho, j_x, j_y (j_y = 0 for D1Q3) of the stored
  * state; out[3].  Synchronises. */
 int flb_get_conserved(flb_ctx* ctx, int replica, double* out3);
@@ -147,6 +152,20 @@ int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int e
 int flb_save(flb_ctx* ctx, void* host_buf, size_t* bytes_inout);
 int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 
+/* Launch configuration of the step kernel: vec consecutive sites per thread
+ * (1, 2 or 4; > 1 only on the FP32 D2Q9 path, every nx a multiple of vec) and
+ * the number of persistent blocks (0 = 16 per SM).  Results do not depend on it.
+ * Synchronises. */
+int flb_set_step_config(flb_ctx* ctx, int vec, int grid_blocks);
+int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks);
+
+/* Autotuner: times `trials` launches of the step kernel (current network
+ * setting, no sampling) for every valid vec and grid size in {2,4,8,16} x SMs
+ * and all-blocks, keeps the fastest and reports it (ms_out: time per launch).
+ * The timing launches recompute the next step from the current state without
+ * advancing it, so the simulation is unchanged.  Synchronises. */
+int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, double* ms_out);
+
 /* Destroy the context (does not free the caller's workspace). */
 void flb_destroy(flb_ctx* ctx);
 
@@ -164,6 +183,59 @@ const char* flb_last_error(void);
 int flb_philox(const uint32_t* site_dev, int n, uint32_t step, uint32_t call, uint32_t tag,
                uint32_t stream, uint64_t seed, int fp32, uint32_t* words_out_dev,
                double* normals_out_dev, void* cuda_stream);
+
+/* ---- correlator sampling of caller-provided fields (Eqs. 11-12) ------- */
+
+/* Scratch bytes and output length for flb_spectra_accumulate on n_fields real
+ * fields of nx x ny (powers of two, nx <= 16384 FP32 / 8192 FP64, n_fields <= 11).
+ * n_sums_out receives the number of doubles of the pair-sum array (see below).
+ * Either output pointer may be NULL.  Pure host call. */
+int flb_spectra_scratch_bytes(int precision, int nx, int ny, int n_fields,
+                              size_t* bytes_out, size_t* n_sums_out);
+
+/* Add, for every field pair a <= b in the order (0,0),(0,1),..,(0,F-1),(1,1),..,
+ * the products X_a(k) X_b(k)^* of the discrete Fourier transforms
+ * X(k) = sum_x X(x) exp(-i k.x) (Eq. 11) to FP64 sums on the half spectrum
+ * kx in [0, nx/2], all ky: an auto pair occupies ny*(nx/2+1) doubles
+ * [ky][kx], a cross pair ny*(nx/2+1) complex values (re, im interleaved).
+ * mean0_dev[a] += X_a(0).  fields_dev: device [n_fields][ny][nx], float for
+ * FLB_FP32_DEV (FP32 transforms) or double for FLB_FP64.  pair_sums_dev,
+ * mean0_dev: device FP64, accumulated in place (zero them to start).
+ * scratch_dev: caller-owned device memory of flb_spectra_scratch_bytes bytes,
+ * 256-B aligned; its contents are overwritten.  Asynchronous on cuda_stream. */
+int flb_spectra_accumulate(int precision, int nx, int ny, int n_fields, const void* fields_dev,
+                           double* pair_sums_dev, double* mean0_dev, void* scratch_dev,
+                           size_t scratch_bytes, void* cuda_stream);
+
+/* ---- training of the noise-scale network (learned extension) -------------
+ * Weight vector (FP32, 1382 values): W1 (32x3) | W2 (32x32) | W3 (6x32) | b1 (32)
+ * | b2 (32) | b3 (6), row-major; the order flb_set_mlp takes (weights, biases).
+ * Loss over R training runs, K included wave vectors and the P = 6 hydrodynamic
+ * pairs (rho rho, rho u_x, rho u_y, u_x u_x, u_x u_y, u_y u_y):
+ *   L = 1/(R P K) sum_{r,p,k} |S^plain_rp(k) + sum_c (m_rc - 1) G^c_rp(k) - delta_p|^2,
+ *   m_rc = mean over the run's B inputs of s_c(x)^2, s = 1 + network(x),
+ * with S^plain the plain method's correlators and G^c those of runs with only
+ * the noise of moment 3 + c (linear response of the equal-time covariance). */
+int flb_mlp_param_count(void);
+
+/* Per-run Gram terms of the loss: gram_dev[R][43] = (sum |D|^2, Re sum D^* G^c
+ * (6), Re sum G^c* G^c' (36)), D = S^plain - delta_p.  splain_dev: device FP64
+ * [R][P][K][2] (re, im); g_dev: [R][6][P][K][2].  P must be 6.  Asynchronous. */
+int flb_mlp_gram(const double* splain_dev, const double* g_dev, int R, int P, int K,
+                 double* gram_dev, void* cuda_stream);
+
+/* Scratch bytes of flb_mlp_train_step for R runs of B inputs. */
+int flb_mlp_scratch_bytes(int R, int B, size_t* bytes);
+
+/* One training step: FP32 forward of all inputs x_dev [R][B][3] = (u_x, u_y,
+ * rho - rho0), loss and m (written to loss_dev[1], m_dev[R][6], FP64), backward,
+ * gradient (written to grad_dev[1382] if not NULL; summed in a fixed order), and
+ * when lr > 0 an Adam update of w_dev with moments adam_m/v_dev and step t >= 1
+ * (bias-corrected).  lr = 0: gradient only, weights unchanged.  Asynchronous. */
+int flb_mlp_train_step(float* w_dev, float* adam_m_dev, float* adam_v_dev, int t, float lr,
+                       float beta1, float beta2, float eps, const float* x_dev, int R, int B,
+                       const double* gram_dev, int P, int K, double* loss_dev, double* m_dev,
+                       float* grad_dev, void* scratch_dev, size_t scratch_bytes, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -40,12 +40,25 @@ _SIGS = {
     "flb_set_populations": (c_int, [c_void_p, c_int, POINTER(c_double)]),
     "flb_get_populations_window": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, POINTER(c_double)]),
     "flb_get_conserved": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_get_fields": (c_int, [c_void_p, c_int, POINTER(c_double)]),
+    "flb_mlp_param_count": (c_int, []),
+    "flb_mlp_gram": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "flb_mlp_scratch_bytes": (c_int, [c_int, c_int, POINTER(c_size_t)]),
+    "flb_mlp_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_float, c_float, c_float, c_float,
+                                   c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_size_t, c_void_p]),
     "flb_get_step": (c_int, [c_void_p, POINTER(c_uint64)]),
     "flb_set_mlp": (c_int, [c_void_p, POINTER(c_uint16), POINTER(c_float), c_int]),
     "flb_save": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
     "flb_load": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "flb_set_step_config": (c_int, [c_void_p, c_int, c_int]),
+    "flb_get_step_config": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_destroy": (None, [c_void_p]),
     "flb_last_error": (ctypes.c_char_p, []),
+    "flb_spectra_scratch_bytes": (c_int, [c_int, c_int, c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
+    "flb_spectra_accumulate": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_size_t, c_void_p]),
     "flb_philox": (c_int, [c_void_p, c_int, c_uint32, c_uint32, c_uint32, c_uint32, c_uint64, c_int,
                            c_void_p, c_void_p, c_void_p]),
 }

@@ -60,8 +60,6 @@ static const double kW3[3] = {2.0 / 3, 1.0 / 6, 1.0 / 6};
 static const int kVx3[3] = {0, 1, -1};
 
 static constexpr int kStepBlock = 256;
-static constexpr int kColsBlock = 256;
-static constexpr int kColsSmemBudget = 200 * 1024;
 
 struct Layout {
   std::vector<ReplicaDesc> desc;
@@ -73,16 +71,6 @@ struct Layout {
   int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
   bool any_fields = false;
 };
-
-// Column FFT split: one pass of length ny when F columns of 4 fit the shared-memory
-// budget, otherwise the four-step split with N1 = 2^floor(log2(ny)/2).
-static int column_split(int precision, int F, int ny) {
-  const int cs = precision == FLB_FP64 ? 16 : 8;
-  if ((int64_t)F * ny * 4 * cs <= kColsSmemBudget) return 0;
-  int l = 0;
-  while ((1 << l) < ny) ++l;
-  return l / 2;
-}
 
 static int field_valid(int lattice, int f) {
   if (lattice == FLB_D2Q9) return f >= 0 && f <= 10;
@@ -164,6 +152,26 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   d.half_nx = p.nx / 2 + 1;
   d.wpitch = (d.half_nx + 1) & ~1;
   d.log2n1 = F ? column_split(precision, F, p.ny) : 0;
+  d.dco[kCoRho0] = d.rho0; d.dco[kCoU0x] = d.u0x; d.dco[kCoU0y] = d.u0y;
+  for (int a = 0; a < 9; ++a) { d.dco[kCoInvTau + a] = d.inv_tau[a]; d.dco[kCoAmp + a] = d.amp[a]; }
+  for (int f = 0; f < kMaxFields; ++f) d.dco[kCoMref + f] = d.mref[f];
+  for (int i = 0; i < kNumCoef; ++i) d.fco[i] = (float)d.dco[i];
+}
+
+// Step-launch tables for a vector width: VEC consecutive sites per thread, one
+// virtual block of kStepBlock threads never spans two replicas.
+static void plan_step(int lattice, int vec, Layout& L) {
+  L.vec = vec;
+  L.n_vb_step = 0;
+  L.vb_step.resize(L.desc.size());
+  for (size_t r = 0; r < L.desc.size(); ++r) {
+    ReplicaDesc& d = L.desc[r];
+    d.units_per_row = d.nx / (lattice == FLB_D2Q9 ? vec : 1);
+    d.n_units = (int64_t)d.units_per_row * d.ny;
+    L.vb_step[r] = L.n_vb_step;
+    d.block_begin = L.n_vb_step;
+    L.n_vb_step += (d.n_units + kStepBlock - 1) / kStepBlock;
+  }
 }
 
 static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
@@ -204,8 +212,6 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
       d.off_tw_x = off; off = align256(off + (int64_t)(d.nx / 2) * 2 * rs + 16);
       d.off_tw_y = off; off = align256(off + (int64_t)(d.ny / 2) * 2 * rs + 16);
     }
-    d.units_per_row = d.nx / (lat == FLB_D2Q9 ? L.vec : 1);
-    d.n_units = (int64_t)d.units_per_row * d.ny;
   }
   // virtual-block prefixes of the three launches
   L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
@@ -217,10 +223,9 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
     L.cols_smem = maxF * maxlen * L.ncol * cs;
   }
+  plan_step(lat, L.vec, L);
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
-    L.vb_step[r] = L.n_vb_step; d.block_begin = L.n_vb_step;
-    L.n_vb_step += (d.n_units + kStepBlock - 1) / kStepBlock;
     L.vb_rows[r] = L.n_vb_rows;
     L.vb_cols[r] = L.n_vb_cols;
     L.vb_cols_a[r] = L.n_vb_cols_a;
@@ -257,6 +262,7 @@ struct flb_ctx {
   cudaStream_t stream = nullptr;
   uint64_t step = 0, n_samples = 0;
   int sms = 1;
+  int step_grid = 0;          // 0: min(virtual blocks, 16 x SMs)
   bool mlp_on = false;
   std::vector<float> mlp_host;
 };
@@ -372,7 +378,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   S.ws = c->ws;
   S.mlp = c->ws + L.off_mlp;
   S.block = kStepBlock;
-  S.grid = (int)std::min<int64_t>(L.n_vb_step, (int64_t)c->sms * 16);
+  S.grid = (int)std::min<int64_t>(L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
   const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
   const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
   const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
@@ -515,6 +521,24 @@ int flb_get_populations_window(flb_ctx* c, int replica, int x0, int y0, int w, i
   return FLB_OK;
 }
 
+int flb_get_fields(flb_ctx* c, int replica, double* host_out) {
+  if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  const ReplicaDesc& d = c->L.desc[replica];
+  if (!d.n_fields) return set_error(FLB_EINVAL, "replica %d samples no fields", replica);
+  if (c->n_samples == 0) return set_error(FLB_ESTATE, "no samples taken");
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  const size_t n = (size_t)d.n_fields * d.nx * d.ny;
+  if (c->precision == FLB_FP64)
+    return cuda_check(cudaMemcpy(host_out, c->ws + d.off_fields, n * 8, cudaMemcpyDeviceToHost), "read fields");
+  std::vector<float> tmp(n);
+  rc = cuda_check(cudaMemcpy(tmp.data(), c->ws + d.off_fields, n * 4, cudaMemcpyDeviceToHost), "read fields");
+  if (rc) return rc;
+  for (size_t i = 0; i < n; ++i) host_out[i] = tmp[i];
+  return FLB_OK;
+}
+
 int flb_set_populations(flb_ctx* c, int replica, const double* host_in) {
   if (!c || !host_in) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
@@ -551,6 +575,7 @@ int flb_get_conserved(flb_ctx* c, int replica, double* out3) {
 int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int enable) {
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   if (c->lattice != FLB_D2Q9) return set_error(FLB_EINVAL, "the noise-scale network is D2Q9 only");
+  if (c->precision != FLB_FP32_DEV) return set_error(FLB_EINVAL, "the noise-scale network runs on the FP32 path");
   if (enable && (!w_bf16 || !biases)) return set_error(FLB_EINVAL, "NULL weights");
   if (enable) {
     const size_t nf = mlp_weights_bytes() / 4;
@@ -639,6 +664,90 @@ int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
   }
   c->step = step;
   c->n_samples = hdr[4];
+  return FLB_OK;
+}
+
+int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  if (vec != 1 && vec != 2 && vec != 4) return set_error(FLB_EINVAL, "vec must be 1, 2 or 4");
+  if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9))
+    return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9 path");
+  for (int r = 0; r < c->n; ++r)
+    if (c->L.desc[r].nx % vec) return set_error(FLB_EINVAL, "replica %d: nx not a multiple of vec = %d", r, vec);
+  if (grid_blocks < 0) return set_error(FLB_EINVAL, "grid_blocks must be >= 0");
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "step config");
+  if (rc) return rc;
+  plan_step(c->lattice, vec, c->L);
+  rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
+                             cudaMemcpyHostToDevice), "copy descriptors");
+  if (!rc) rc = cuda_check(cudaMemcpy(c->ws + c->L.off_vb_step, c->L.vb_step.data(), 8 * (size_t)c->n,
+                                      cudaMemcpyHostToDevice), "copy vb");
+  if (!rc) c->step_grid = grid_blocks;
+  return rc;
+}
+
+int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks) {
+  if (!c || !vec || !grid_blocks) return set_error(FLB_EINVAL, "NULL argument");
+  *vec = c->L.vec;
+  *grid_blocks = (int)std::min<int64_t>(c->L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
+  return FLB_OK;
+}
+
+int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms_out) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  if (trials < 1) return set_error(FLB_EINVAL, "trials must be >= 1");
+  cudaEvent_t e0, e1;
+  int rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (rc) return rc;
+  rc = cuda_check(cudaEventCreate(&e1), "event");
+  if (rc) { cudaEventDestroy(e0); return rc; }
+  const int vecs[3] = {1, 2, 4};
+  int best_vec = c->L.vec, best_grid = c->step_grid;
+  float best = 1e30f;
+  for (int vi = 0; vi < 3 && !rc; ++vi) {
+    const int vec = vecs[vi];
+    if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9)) continue;
+    bool ok = true;
+    for (int r = 0; r < c->n; ++r) ok = ok && c->L.desc[r].nx % vec == 0;
+    if (!ok) continue;
+    const int mults[5] = {2, 4, 8, 16, 0};
+    for (int mi = 0; mi < 5 && !rc; ++mi) {
+      const int grid = mults[mi] ? mults[mi] * c->sms : 0;
+      rc = flb_set_step_config(c, vec, grid ? grid : INT32_MAX);
+      if (rc) break;
+      // dry runs: the same step (same input buffer, same step index) launched
+      // repeatedly; it only rewrites the buffer the next real step overwrites.
+      StepLaunch S;
+      S.descs = descs_dev(c);
+      S.vb_begin = reinterpret_cast<const int64_t*>(c->ws + c->L.off_vb_step);
+      S.n_reps = c->n;
+      S.n_vblocks = c->L.n_vb_step;
+      S.ws = c->ws;
+      S.mlp = c->ws + c->L.off_mlp;
+      S.block = kStepBlock;
+      S.grid = (int)std::min<int64_t>(c->L.n_vb_step, c->step_grid);
+      S.parity = (int)(c->step & 1);
+      S.step = (uint32_t)c->step;
+      launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
+      cudaEventRecord(e0, c->stream);
+      for (int t = 0; t < trials; ++t) launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
+      cudaEventRecord(e1, c->stream);
+      rc = cuda_check(cudaEventSynchronize(e1), "autotune");
+      if (rc) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= trials;
+      if (ms < best) { best = ms; best_vec = vec; best_grid = S.grid; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = flb_set_step_config(c, best_vec, best_grid);
+  if (rc) return rc;
+  if (vec_out) *vec_out = best_vec;
+  if (grid_out) *grid_out = best_grid;
+  if (ms_out) *ms_out = best;
   return FLB_OK;
 }
 

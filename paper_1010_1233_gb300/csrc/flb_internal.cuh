@@ -13,11 +13,15 @@ namespace flb {
 
 constexpr int kMaxFields = FLB_MAX_FIELDS;
 constexpr int kMaxPairs = kMaxFields * (kMaxFields + 1) / 2;
+constexpr int kStepThreads = 256;     // threads per block of the step kernels
 constexpr int kReduceBlocks = 2048;   // partial sums of the deterministic reductions
 constexpr int kMlpHidden = 32;
 constexpr int kMlpOut = 6;
 constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden;  // 1312
 constexpr int kMlpBiases = kMlpHidden + kMlpHidden + kMlpOut;                               // 70
+
+constexpr int kCoRho0 = 0, kCoU0x = 1, kCoU0y = 2, kCoInvTau = 3, kCoAmp = 12, kCoMref = 21;
+constexpr int kNumCoef = kCoMref + 11;
 
 // Per-replica description, resident in device memory (one array per context).
 // Offsets are byte offsets from the workspace base.
@@ -45,7 +49,16 @@ struct ReplicaDesc {
   int32_t half_nx;                  // nx / 2 + 1
   int32_t wpitch;                   // pitch (complex elements) of spec rows
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
+  // the per-replica coefficients in the arithmetic type of the path (host-filled),
+  // so the FP32 kernels never convert from FP64: [kCoRho0], [kCoU0x], [kCoU0y],
+  // [kCoInvTau + a], [kCoAmp + a], [kCoMref + field]
+  float fco[kNumCoef];
+  double dco[kNumCoef];
 };
+
+template <typename R> __device__ __forceinline__ R coef(const ReplicaDesc& d, int i);
+template <> __device__ __forceinline__ float coef<float>(const ReplicaDesc& d, int i) { return d.fco[i]; }
+template <> __device__ __forceinline__ double coef<double>(const ReplicaDesc& d, int i) { return d.dco[i]; }
 
 struct DevStatus {
   int32_t error;        // 0 ok; FLB_EUNSTABLE / FLB_ETIMEOUT set by kernels
@@ -57,13 +70,10 @@ struct DevStatus {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 128-bit counter, 64-bit key.
 __host__ __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2,
                                                       uint32_t& c3, uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-#ifdef __CUDA_ARCH__
-  const uint32_t hi0 = __umulhi(M0, c0), hi1 = __umulhi(M1, c2);
-#else
-  const uint32_t hi0 = (uint32_t)(((uint64_t)M0 * c0) >> 32), hi1 = (uint32_t)(((uint64_t)M1 * c2) >> 32);
-#endif
-  const uint32_t lo0 = M0 * c0, lo1 = M1 * c2;
+  // 32 x 32 -> 64-bit products: one wide multiply gives both halves
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
   const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
   c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
 }
@@ -94,10 +104,14 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0,
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
   const float ua = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
   const float ub = fmaf(__uint2float_rn(wb), 0x1p-32f, 0x1p-33f);
-  const float r = sqrtf(-2.0f * logf(ua));
+  // r = sqrt(-2 ln ua); ua <= 1 so x >= 0, and x = 0 only when ua rounds to 1
+  const float x = fmaxf(-2.0f * logf(ua), 1e-30f);
+  const float r = x * rsqrtf(x);
+  // (cos, sin)(2 pi ub) = -(cos, sin)(theta) with theta = 2 pi (ub - 1/2) in [-pi, pi],
+  // the range where the hardware sine and cosine are accurate to ~2^-21 absolute
   float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  n0 = r * c; n1 = r * s;
+  __sincosf(6.283185307179586f * (ub - 0.5f), &s, &c);
+  n0 = -r * c; n1 = -r * s;
 }
 
 template <typename T> struct cplx { T x, y; };
@@ -110,6 +124,19 @@ struct StepLaunch {
   const ReplicaDesc* descs; const int64_t* vb_begin; int n_reps; int64_t n_vblocks;
   char* ws; int parity; uint32_t step; const void* mlp; int grid; int block;
 };
+
+// Shared-memory budget of the column transforms and their split rule: one pass of
+// length ny when F columns of 4 fit the budget, else ny = N1 * N2 with
+// N1 = 2^floor(log2(ny)/2) (four-step).
+constexpr int kColsSmemBudget = 200 * 1024;
+constexpr int kColsBlock = 256;
+inline int column_split(int precision, int F, int ny) {
+  const int cs = precision == FLB_FP64 ? 16 : 8;
+  if ((int64_t)F * ny * 4 * cs <= kColsSmemBudget) return 0;
+  int l = 0;
+  while ((1 << l) < ny) ++l;
+  return l / 2;
+}
 
 // host-side helpers (api.cu)
 int set_error(int code, const char* fmt, ...);

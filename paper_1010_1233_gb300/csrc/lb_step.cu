@@ -59,76 +59,172 @@ template <> struct VecIO<double, 2> {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]); }
 };
 
-__device__ __forceinline__ float bf16_round(float x) {
-  return __bfloat162float(__float2bfloat16_rn(x));
+// ---------------------------------------------------------------------------
+// Noise-scale network on the tensor cores (warp-level mma.sync m16n8k16, bfloat16
+// operands, FP32 accumulation).  The sites of a warp are the M dimension: tile m
+// holds warp sites 16m .. 16m+15, thread (g = lane/4, q = lane%4) owns rows g and
+// g+8 of the accumulator and columns 2q, 2q+1.  The accumulator layout of two
+// adjacent 8-column tiles is exactly the A-operand layout of the next layer, so
+// h1 and h2 never leave registers; ReLU and the bfloat16 rounding are one cvt.
+// Biases enter as the FP32 C operand.
+// One lane's share of the network (176 B, 16-B aligned, so a lane reads it with
+// 128-bit shared loads and the 32 lanes hit distinct banks): B-fragment words of
+// layer 1 (per n-tile; the second word is 0 since K = 3), layer 2 ([n-tile][k-tile][2])
+// and layer 3 ([k-tile][2]); bias pairs (b[8j+2q], b[8j+2q+1]) per n-tile.
+struct __align__(16) MlpLane {
+  uint4 b1;
+  uint4 b2[4];
+  uint4 b3;
+  float4 c1[2], c2[2];
+  float4 c3;
+};
+struct MlpFrags {
+  MlpLane lanes[32];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// s_c = 1 + o_c(u_x, u_y, rho - rho0) with bfloat16 operands and FP32 accumulation.
-__device__ __forceinline__ void mlp_scales(const MlpWeights& w, float ux, float uy, float drho,
-                                           float (&s)[kMlpOut]) {
-  const float x0 = bf16_round(ux), x1 = bf16_round(uy), x2 = bf16_round(drho);
-  float h1[kMlpHidden];
-#pragma unroll
-  for (int h = 0; h < kMlpHidden; ++h) {
-    float z = w.b1[h];
-    z = fmaf(w.W1[3 * h + 0], x0, z);
-    z = fmaf(w.W1[3 * h + 1], x1, z);
-    z = fmaf(w.W1[3 * h + 2], x2, z);
-    h1[h] = bf16_round(fmaxf(z, 0.f));
+// relu, round to bfloat16 and pack (lo in the low half)
+__device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// d = a b + (c0, c1, c0, c1)
+__device__ __forceinline__ void mma_bias(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1,
+                                         float2 c) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%10,%11};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c.x), "f"(c.y));
+}
+
+// d += a b
+__device__ __forceinline__ void mma_acc(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ void build_mlp_frags(const MlpWeights& w, MlpFrags& F) {
+  for (int i = threadIdx.x; i < 32 * 4; i += blockDim.x) {
+    const int lane = i >> 2, j = i & 3, g = lane >> 2, q = lane & 3, n = 8 * j + g;
+    MlpLane& M = F.lanes[lane];
+    uint32_t* b1 = reinterpret_cast<uint32_t*>(&M.b1);
+    uint32_t* b2 = reinterpret_cast<uint32_t*>(M.b2);
+    uint32_t* b3 = reinterpret_cast<uint32_t*>(&M.b3);
+    float* c1 = reinterpret_cast<float*>(M.c1);
+    float* c2 = reinterpret_cast<float*>(M.c2);
+    float lo = 0.f, hi = 0.f;                       // B1[k][n] = W1[n][k], k < 3
+    if (q == 0) { lo = w.W1[3 * n]; hi = w.W1[3 * n + 1]; }
+    if (q == 1) { lo = w.W1[3 * n + 2]; }
+    b1[j] = pack_bf16(lo, hi);
+    c1[2 * j] = w.b1[8 * j + 2 * q]; c1[2 * j + 1] = w.b1[8 * j + 2 * q + 1];
+    c2[2 * j] = w.b2[8 * j + 2 * q]; c2[2 * j + 1] = w.b2[8 * j + 2 * q + 1];
+    for (int t = 0; t < 2; ++t)
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * t + 8 * h + 2 * q;
+        b2[(j * 2 + t) * 2 + h] = pack_bf16(w.W2[n * kMlpHidden + k], w.W2[n * kMlpHidden + k + 1]);
+      }
+    if (j < 2) {
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * j + 8 * h + 2 * q;
+        b3[j * 2 + h] = g < kMlpOut ? pack_bf16(w.W3[g * kMlpHidden + k], w.W3[g * kMlpHidden + k + 1]) : 0u;
+      }
+    }
+    if (j == 0) M.c3 = q < 3 ? make_float4(w.b3[2 * q], w.b3[2 * q + 1], 0.f, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  float o[kMlpOut];
+}
+
+// One 16-site tile: feature words of rows g and g+8 (x0 = (u_x, u_y), x1 = (rho - rho0, 0)),
+// outputs o_c for c in {2q, 2q+1} of both rows.  The lane's fragments come from shared memory.
+__device__ __forceinline__ void mlp_tile(const MlpLane& M, int q, uint2 f0, uint2 f1, float (&o)[4]) {
+  uint32_t a[4] = {0u, 0u, 0u, 0u};
+  if (q == 0) { a[0] = f0.x; a[1] = f1.x; }
+  if (q == 1) { a[0] = f0.y; a[1] = f1.y; }
+  const uint4 b1 = M.b1;
+  const float4 c1a = M.c1[0], c1b = M.c1[1];
+  float h[4][4];
+  mma_bias(h[0], a, b1.x, 0u, make_float2(c1a.x, c1a.y));                         // layer 1
+  mma_bias(h[1], a, b1.y, 0u, make_float2(c1a.z, c1a.w));
+  mma_bias(h[2], a, b1.z, 0u, make_float2(c1b.x, c1b.y));
+  mma_bias(h[3], a, b1.w, 0u, make_float2(c1b.z, c1b.w));
+  uint32_t a2[2][4];
 #pragma unroll
-  for (int c = 0; c < kMlpOut; ++c) o[c] = w.b3[c];
-#pragma unroll 4
-  for (int h = 0; h < kMlpHidden; ++h) {
-    float z = w.b2[h];
+  for (int t = 0; t < 2; ++t) {
+    a2[t][0] = relu_pack(h[2 * t][0], h[2 * t][1]);
+    a2[t][1] = relu_pack(h[2 * t][2], h[2 * t][3]);
+    a2[t][2] = relu_pack(h[2 * t + 1][0], h[2 * t + 1][1]);
+    a2[t][3] = relu_pack(h[2 * t + 1][2], h[2 * t + 1][3]);
+  }
+  const float4 c2a = M.c2[0], c2b = M.c2[1];
+  const float2 c2[4] = {make_float2(c2a.x, c2a.y), make_float2(c2a.z, c2a.w), make_float2(c2b.x, c2b.y),
+                        make_float2(c2b.z, c2b.w)};
 #pragma unroll
-    for (int k = 0; k < kMlpHidden; ++k) z = fmaf(w.W2[h * kMlpHidden + k], h1[k], z);
-    const float h2 = bf16_round(fmaxf(z, 0.f));
-#pragma unroll
-    for (int c = 0; c < kMlpOut; ++c) o[c] = fmaf(w.W3[c * kMlpHidden + h], h2, o[c]);
+  for (int j = 0; j < 4; ++j) {                                                    // layer 2
+    const uint4 b = M.b2[j];                       // (k-tile 0: w0 w1, k-tile 1: w0 w1)
+    mma_bias(h[j], a2[0], b.x, b.y, c2[j]);
+    mma_acc(h[j], a2[1], b.z, b.w);
   }
 #pragma unroll
-  for (int c = 0; c < kMlpOut; ++c) s[c] = 1.f + o[c];
+  for (int t = 0; t < 2; ++t) {
+    a2[t][0] = relu_pack(h[2 * t][0], h[2 * t][1]);
+    a2[t][1] = relu_pack(h[2 * t][2], h[2 * t][3]);
+    a2[t][2] = relu_pack(h[2 * t + 1][0], h[2 * t + 1][1]);
+    a2[t][3] = relu_pack(h[2 * t + 1][2], h[2 * t + 1][3]);
+  }
+  const uint4 b3 = M.b3;
+  const float4 c3 = M.c3;
+  mma_bias(o, a2[0], b3.x, b3.y, make_float2(c3.x, c3.y));                         // layer 3
+  mma_acc(o, a2[1], b3.z, b3.w);
 }
 
 // ---------------------------------------------------------------------------
 // D2Q9.  Population order (Sec. 3): 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1),
 // 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).
-__device__ __constant__ int c_vx9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__device__ __constant__ int c_vy9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-
 template <typename R, bool DEV, int VEC, bool SAMPLE, bool MLP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kStepThreads)
 k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin, int n_reps,
             int64_t n_vblocks, char* __restrict__ ws, int parity, uint32_t step,
             const MlpWeights* __restrict__ mlp_w) {
   constexpr int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int VY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  __shared__ MlpWeights sw;
+  static_assert(!MLP || sizeof(R) == 4, "the network runs on the FP32 path");
+  __shared__ MlpFrags sfr;
+  __shared__ uint2 s_feat[MLP ? kStepThreads * VEC : 1];
+  __shared__ float2 s_out[MLP ? kStepThreads * VEC * 4 : 1];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   if constexpr (MLP) {
-    const float* src = reinterpret_cast<const float*>(mlp_w);
-    float* dst = reinterpret_cast<float*>(&sw);
-    for (int i = threadIdx.x; i < (int)(sizeof(MlpWeights) / 4); i += blockDim.x) dst[i] = src[i];
+    build_mlp_frags(*mlp_w, sfr);
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
-    const int r = find_replica(vb_begin, n_reps, vb);
+    const int r = n_reps == 1 ? 0 : find_replica(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
     const int nx = d.nx, ny = d.ny;
-    const int64_t unit_raw = (vb - vb_begin[r]) * blockDim.x + threadIdx.x;
-    const bool active = unit_raw < d.n_units;
-    const int64_t unit = active ? unit_raw : d.n_units - 1;
-    const int y = (int)(unit / d.units_per_row);
-    const int xq = (int)(unit - (int64_t)y * d.units_per_row);
+    // per-replica unit counts stay below 2^31 (sites < 2^32, at least 2 sites per unit or VEC = 1
+    // on lattices of < 2^31 sites), so the index arithmetic is 32-bit
+    const int n_units = (int)d.n_units, upr = d.units_per_row;
+    const int unit_raw = (int)(vb - vb_begin[r]) * (int)blockDim.x + (int)threadIdx.x;
+    const bool active = unit_raw < n_units;
+    const int unit = active ? unit_raw : n_units - 1;
+    const int y = (int)((unsigned)unit / (unsigned)upr);
+    const int xq = unit - y * upr;
     const int x0 = xq * VEC;
     const int64_t plane = (int64_t)nx * ny;
     const R* __restrict__ src = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
     R* __restrict__ dst = reinterpret_cast<R*>(ws + d.off_pop[parity ^ 1]);
     // neighbour lanes hold the adjacent unit of the same row?
     const bool left_in_warp = lane > 0 && xq > 0;
-    const bool right_in_warp = lane < 31 && (xq + 1) < d.units_per_row && (unit_raw + 1) < d.n_units;
+    const bool right_in_warp = lane < 31 && (xq + 1) < upr && (unit_raw + 1) < n_units;
 
     // ---- pull streaming: f_i(x) = f*_i(x - v_i) -------------------------
     R f[9][VEC];
@@ -157,11 +253,44 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
       }
     }
 
-    const R rho0 = (R)d.rho0;
-    const R it3 = (R)d.inv_tau[3], it4 = (R)d.inv_tau[4], it5 = (R)d.inv_tau[5];
-    const R it6 = (R)d.inv_tau[6], it7 = (R)d.inv_tau[7], it8 = (R)d.inv_tau[8];
-    const R a3 = (R)d.amp[3], a4 = (R)d.amp[4], a5 = (R)d.amp[5];
-    const R a6 = (R)d.amp[6], a7 = (R)d.amp[7], a8 = (R)d.amp[8];
+    const R rho0 = coef<R>(d, kCoRho0);
+    // ---- density, momentum, velocity (Sec. 2) ----------------------------
+    // deviation storage: sum_i w_i rho0 = rho0 and sum_i w_i rho0 v_i = 0
+    R sum[VEC], ux[VEC], uy[VEC];
+#pragma unroll
+    for (int s = 0; s < VEC; ++s) {
+      sum[s] = ((f[0][s] + (f[1][s] + f[3][s])) + (f[2][s] + f[4][s])) + ((f[5][s] + f[7][s]) + (f[6][s] + f[8][s]));
+      const R jx = (f[1][s] - f[3][s]) + ((f[5][s] - f[7][s]) + (f[8][s] - f[6][s]));
+      const R jy = (f[2][s] - f[4][s]) + ((f[5][s] - f[7][s]) + (f[6][s] - f[8][s]));
+      const R irho = (R)1 / (DEV ? rho0 + sum[s] : sum[s]);
+      ux[s] = jx * irho;
+      uy[s] = jy * irho;
+    }
+    // ---- per-site noise scales from the network (tensor cores) --------------
+    if constexpr (MLP) {
+      uint2* feat = s_feat + warp * 32 * VEC;
+      float2* outw = s_out + warp * 32 * VEC * 4;
+#pragma unroll
+      for (int s = 0; s < VEC; ++s)
+        feat[lane * VEC + s] = make_uint2(pack_bf16((float)ux[s], (float)uy[s]),
+                                          pack_bf16((float)(DEV ? sum[s] : sum[s] - rho0), 0.f));
+      __syncwarp();
+      const int g = lane >> 2, q = lane & 3;
+#pragma unroll 1
+      for (int m = 0; m < 2 * VEC; ++m) {
+        float o[4];
+        mlp_tile(sfr.lanes[lane], q, feat[16 * m + g], feat[16 * m + g + 8], o);
+        if (q < 3) {
+          outw[(16 * m + g) * 4 + q] = make_float2(o[0], o[1]);
+          outw[(16 * m + g + 8) * 4 + q] = make_float2(o[2], o[3]);
+        }
+      }
+      __syncwarp();
+    }
+    const R it3 = coef<R>(d, kCoInvTau + 3), it4 = coef<R>(d, kCoInvTau + 4), it5 = coef<R>(d, kCoInvTau + 5);
+    const R it6 = coef<R>(d, kCoInvTau + 6), it7 = coef<R>(d, kCoInvTau + 7), it8 = coef<R>(d, kCoInvTau + 8);
+    const R a3 = coef<R>(d, kCoAmp + 3), a4 = coef<R>(d, kCoAmp + 4), a5 = coef<R>(d, kCoAmp + 5);
+    const R a6 = coef<R>(d, kCoAmp + 6), a7 = coef<R>(d, kCoAmp + 7), a8 = coef<R>(d, kCoAmp + 8);
     const bool noisy = d.noise_mask != 0;
     const R S3 = (R)1.7320508075688772935, S32 = (R)1.2247448713915890491,
             S6 = (R)2.4494897427831780982;
@@ -171,13 +300,7 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
     for (int s = 0; s < VEC; ++s) {
       const R g0 = f[0][s], g1 = f[1][s], g2 = f[2][s], g3 = f[3][s], g4 = f[4][s];
       const R g5 = f[5][s], g6 = f[6][s], g7 = f[7][s], g8 = f[8][s];
-      // density and momentum (Sec. 2); in deviation storage sum_i w_i rho0 = rho0, sum w v = 0
-      const R sum = ((g0 + (g1 + g3)) + (g2 + g4)) + ((g5 + g7) + (g6 + g8));
-      const R rho = DEV ? rho0 + sum : sum;
-      const R jx = (g1 - g3) + ((g5 - g7) + (g8 - g6));
-      const R jy = (g2 - g4) + ((g5 - g7) + (g6 - g8));
-      const R irho = (R)1 / rho;
-      const R ux = jx * irho, uy = jy * irho;
+      const R rho = DEV ? rho0 + sum[s] : sum[s];
       // non-conserved moments of Eq. 9 (identical for f and f - w rho0)
       const R ax = g1 + g3, ay = g2 + g4, dg = (g5 + g7) + (g6 + g8);
       const R M3 = (R)1.5 * (ax - ay);
@@ -187,16 +310,17 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
       const R M7 = S32 * (g4 - g2) + S6 * ((g5 - g7) + (g6 - g8));
       const R M8 = (R)0.5 * g0 - (ax + ay) + (R)2 * dg;
       // equilibrium moments, Eq. 10
-      const R ux2 = ux * ux, uy2 = uy * uy;
+      const R ux2 = ux[s] * ux[s], uy2 = uy[s] * uy[s];
       const R E3 = (R)1.5 * rho * (ux2 - uy2);
-      const R E4 = (R)3 * rho * ux * uy;
+      const R E4 = (R)3 * rho * ux[s] * uy[s];
       const R E5 = (R)1.5 * rho * (ux2 + uy2);
       if constexpr (SAMPLE) {
-        const R mom[9] = {sum, S3 * jx, S3 * jy, M3, M4, M5, M6, M7, M8};
+        const R jx = ux[s] * rho, jy = uy[s] * rho;
+        const R mom[9] = {sum[s], S3 * jx, S3 * jy, M3, M4, M5, M6, M7, M8};
 #pragma unroll
-        for (int a = 0; a < 9; ++a) fld[a][s] = mom[a] - (R)d.mref[a];
-        fld[9][s] = ux - (R)d.u0x;
-        fld[10][s] = uy - (R)d.u0y;
+        for (int a = 0; a < 9; ++a) fld[a][s] = mom[a] - coef<R>(d, kCoMref + a);
+        fld[9][s] = ux[s] - coef<R>(d, kCoU0x);
+        fld[10][s] = uy[s] - coef<R>(d, kCoU0y);
       }
       // relaxation (Eq. 5)
       R D3 = (E3 - M3) * it3, D4 = (E4 - M4) * it4, D5 = (E5 - M5) * it5;
@@ -211,10 +335,10 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
         box_muller(w1.x, w1.y, n4, n5);
         R sc[6] = {(R)1, (R)1, (R)1, (R)1, (R)1, (R)1};
         if constexpr (MLP) {
-          float sf[kMlpOut];
-          mlp_scales(sw, (float)ux, (float)uy, (float)(rho - rho0), sf);
-#pragma unroll
-          for (int c = 0; c < 6; ++c) sc[c] = (R)sf[c];
+          const float2* o = s_out + (warp * 32 * VEC + lane * VEC + s) * 4;
+          const float2 o01 = o[0], o23 = o[1], o45 = o[2];
+          sc[0] = (R)1 + (R)o01.x; sc[1] = (R)1 + (R)o01.y; sc[2] = (R)1 + (R)o23.x;
+          sc[3] = (R)1 + (R)o23.y; sc[4] = (R)1 + (R)o45.x; sc[5] = (R)1 + (R)o45.y;
         }
         D3 += sc[0] * a3 * n0; D4 += sc[1] * a4 * n1; D5 += sc[2] * a5 * n2;
         D6 += sc[3] * a6 * n3; D7 += sc[4] * a7 * n4; D8 += sc[5] * a8 * n5;
@@ -280,7 +404,7 @@ k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
     const R g1 = src[nx + (x == 0 ? nx - 1 : x - 1)];
     const R g2 = src[2 * nx + (x == nx - 1 ? 0 : x + 1)];
     const R sum = g0 + (g1 + g2);
-    const R rho = DEV ? (R)d.rho0 + sum : sum;
+    const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
     const R j = g1 - g2;
     const R u = j / rho;
     const R S2 = (R)1.4142135623730950488, IS2 = (R)0.70710678118654752440;
@@ -291,16 +415,16 @@ k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
       const R mom[3] = {sum, (R)1.7320508075688772935 * j, M2};
       for (int slot = 0; slot < (int)d.n_fields; ++slot) {
         const int fid = d.field_id[slot];
-        const R val = fid < 3 ? mom[fid] - (R)d.mref[fid] : u - (R)d.u0x;
+        const R val = fid < 3 ? mom[fid] - coef<R>(d, kCoMref + fid) : u - coef<R>(d, kCoU0x);
         fields[(int64_t)slot * nx + x] = val;
       }
     }
-    R D2 = (E2 - M2) * (R)d.inv_tau[2];
+    R D2 = (E2 - M2) * coef<R>(d, kCoInvTau + 2);
     if (d.noise_mask) {
       const uint4 w = philox4x32_10((uint32_t)x, step, 0u, d.stream, d.seed_lo, d.seed_hi);
       R n0, n1;
       box_muller(w.x, w.y, n0, n1);
-      D2 += (R)d.amp[2] * n0;
+      D2 += coef<R>(d, kCoAmp + 2) * n0;
     }
     dst[x] = g0 - (R)(2.0 / 3.0) * IS2 * D2;
     const R side = (R)(1.0 / 6.0) * S2 * D2;
@@ -472,15 +596,20 @@ static void launch_d2q9_vec(const StepLaunch& L, bool sample, bool mlp, cudaStre
   auto w = reinterpret_cast<const MlpWeights*>(L.mlp);
 #define FLB_L(S, M) k_step_d2q9<R, DEV, VEC, S, M><<<L.grid, L.block, 0, st>>>( \
       L.descs, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, w)
-  if (sample) { if (mlp) FLB_L(true, true); else FLB_L(true, false); }
-  else { if (mlp) FLB_L(false, true); else FLB_L(false, false); }
+  if constexpr (sizeof(R) == 4) {
+    if (mlp) {
+      if (sample) FLB_L(true, true); else FLB_L(false, true);
+      return;
+    }
+  }
+  if (sample) FLB_L(true, false); else FLB_L(false, false);
 #undef FLB_L
 }
 
 void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool sample, bool mlp,
                  cudaStream_t st) {
   if (lattice == FLB_D2Q9) {
-    if (precision == FLB_FP64) launch_d2q9_vec<double, false, 1>(L, sample, mlp, st);
+    if (precision == FLB_FP64) launch_d2q9_vec<double, false, 1>(L, sample, false, st);
     else if (vec == 4) launch_d2q9_vec<float, true, 4>(L, sample, mlp, st);
     else if (vec == 2) launch_d2q9_vec<float, true, 2>(L, sample, mlp, st);
     else launch_d2q9_vec<float, true, 1>(L, sample, mlp, st);

@@ -116,6 +116,14 @@ class Sim:
                                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
+    def fields(self, r=0):
+        """Fields of the most recent sample, [n_fields][ny][nx] in increasing field id order."""
+        ny, nx = self._shape(r)
+        F = len(self.params[r].get("fields", ()))
+        out = np.empty((F, ny, nx))
+        L.check(L.lib().flb_get_fields(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
     def set_populations(self, f, r=0):
         f = np.ascontiguousarray(f, dtype=np.float64)
         L.check(L.lib().flb_set_populations(self._ctx, r, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
@@ -138,6 +146,21 @@ class Sim:
         b = np.ascontiguousarray(b, dtype=np.float32)
         L.check(lib.flb_set_mlp(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    # -- launch configuration ---------------------------------------------
+    def set_step_config(self, vec, grid_blocks=0):
+        L.check(L.lib().flb_set_step_config(self._ctx, int(vec), int(grid_blocks)))
+
+    def step_config(self):
+        v, g = ctypes.c_int(), ctypes.c_int()
+        L.check(L.lib().flb_get_step_config(self._ctx, ctypes.byref(v), ctypes.byref(g)))
+        return int(v.value), int(g.value)
+
+    def autotune(self, trials=5):
+        """Pick the fastest step-kernel configuration; returns (vec, grid, ms per step)."""
+        v, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        L.check(L.lib().flb_autotune(self._ctx, int(trials), ctypes.byref(v), ctypes.byref(g), ctypes.byref(ms)))
+        return int(v.value), int(g.value), float(ms.value)
 
     # -- checkpoint -------------------------------------------------------
     def save(self):
@@ -176,3 +199,53 @@ def philox(sites, step, call, tag, stream, seed, fp32=False, device="cuda"):
                                ctypes.c_void_p(st.cuda_stream)))
     torch.cuda.synchronize()
     return (words.cpu().numpy().view(np.uint32).reshape(n, 4), normals.cpu().numpy().reshape(n, 4))
+
+
+def spectra_sizes(F, ny, nx, precision="fp32"):
+    """(scratch bytes, number of FP64 pair sums) of flb_spectra_accumulate."""
+    b, n = ctypes.c_size_t(), ctypes.c_size_t()
+    L.check(L.lib().flb_spectra_scratch_bytes(_PREC[precision], nx, ny, F, ctypes.byref(b), ctypes.byref(n)))
+    return int(b.value), int(n.value)
+
+
+def spectra_accumulate(fields, sums=None, mean0=None, scratch=None):
+    """Add X_a(k) X_b(k)^* of every pair of the device fields (F, ny, nx) to FP64 sums.
+
+    fields: CUDA tensor, float32 (FP32 transforms) or float64.  Returns (sums, mean0),
+    allocating zeroed ones when not given.  The pair layout is that of flb.h.
+    """
+    F, ny, nx = fields.shape
+    precision = "fp64" if fields.dtype == torch.float64 else "fp32"
+    nb, ns = spectra_sizes(F, ny, nx, precision)
+    dev = fields.device
+    if sums is None:
+        sums = torch.zeros(ns, dtype=torch.float64, device=dev)
+    if mean0 is None:
+        mean0 = torch.zeros(F, dtype=torch.float64, device=dev)
+    if scratch is None:
+        scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+    fields = fields.contiguous()
+    st = torch.cuda.current_stream(dev)
+    L.check(L.lib().flb_spectra_accumulate(_PREC[precision], nx, ny, F, ctypes.c_void_p(fields.data_ptr()),
+                                           ctypes.c_void_p(sums.data_ptr()), ctypes.c_void_p(mean0.data_ptr()),
+                                           ctypes.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                           ctypes.c_void_p(st.cuda_stream)))
+    return sums, mean0
+
+
+def unpack_pair_sums(sums, F, ny, nx):
+    """Split the flat pair-sum array into {(a, b): complex (ny, nx/2+1)} (host numpy)."""
+    s = sums.detach().cpu().numpy() if hasattr(sums, "detach") else np.asarray(sums)
+    hn = nx // 2 + 1
+    out, off = {}, 0
+    for a in range(F):
+        for b in range(a, F):
+            n = ny * hn
+            if a == b:
+                out[(a, b)] = s[off:off + n].reshape(ny, hn).astype(np.complex128)
+                off += n
+            else:
+                v = s[off:off + 2 * n].reshape(ny, hn, 2)
+                out[(a, b)] = v[..., 0] + 1j * v[..., 1]
+                off += 2 * n
+    return out

@@ -236,3 +236,38 @@ def test_four_step_column_fft_matches_oracle(precision, nx, ny, tol):
         o = ref.acc.correlator(a, b)
         err = np.abs(sim.correlator(0, a, b) - o).max() / max(1.0, np.abs(o).max())
         assert err < tol, (a, b, err)
+
+
+@pytest.mark.parametrize("with_mlp", [False, True])
+def test_step_configs_and_autotune(with_mlp):
+    # every launch configuration computes the same step; the template variants may contract
+    # multiply-adds differently, so agreement is to FP32 rounding, not bitwise
+    p = W.replica("D2Q9", 64, 32, W.taus_d2q9(0.8), kT=1e-4, u0=(0.1, 0.02), seed=12, init_mode=1,
+                  fields=(0, 9, 10))
+    wts = W.mlp_weights(5, out_scale=0.3)
+    ref = None
+    for vec, grid in [(4, 0), (1, 0), (2, 3), (4, 1), (1, 100000)]:
+        sim = Sim(p, precision="fp32")
+        if with_mlp:
+            sim.set_mlp(wts)
+        sim.set_step_config(vec, grid)
+        assert sim.step_config()[0] == vec
+        sim.run(12, 4)
+        out = (sim.populations(), sim.correlator(0, 0, 9))
+        if ref is None:
+            ref = out
+            feq = lb.uniform_state(lb.Params(**p))
+        else:
+            assert _rel(out[0], ref[0], ref[0] - feq) < 1e-5, (vec, grid)
+            assert np.abs(out[1] - ref[1]).max() < 1e-4 * np.abs(ref[1]).max(), (vec, grid)
+    # the autotuner's timing launches leave the state and the step counter unchanged
+    sim = Sim(p, precision="fp32")
+    if with_mlp:
+        sim.set_mlp(wts)
+    sim.run(6, 4)
+    before, step = sim.populations(), sim.step
+    vec, grid, ms = sim.autotune(trials=3)
+    assert vec in (1, 2, 4) and grid > 0 and ms > 0
+    assert np.array_equal(sim.populations(), before) and sim.step == step
+    sim.run(6, 4)
+    assert _rel(sim.populations(), ref[0], ref[0] - feq) < 1e-5
