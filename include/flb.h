@@ -207,6 +207,22 @@ int flb_spectra_accumulate(int precision, int nx, int ny, int n_fields, const vo
                            double* pair_sums_dev, double* mean0_dev, void* scratch_dev,
                            size_t scratch_bytes, void* cuda_stream);
 
+/* Same as flb_spectra_accumulate, for callers that cannot allocate device memory
+ * (a framework that owns the whole device memory budget through its own pool, a
+ * service under a fixed memory cap, a latency-critical loop that must not pay
+ * for cudaMalloc / cudaFree and their device-wide synchronisation).  The paper
+ * has no counterpart: this is a deployment variant.  Its scratch is a fixed
+ * 8 MiB device array inside the library, held by every GPU that loads the
+ * library until the process exits; sizes whose plan needs more return
+ * FLB_EINVAL with a message.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Calls allocate nothing.  All calls on
+ * a device share the array, which keeps the last call's contents (each call
+ * rewrites what it reads); calls whose GPU work overlaps race on it and must be
+ * serialised.  Outputs and semantics as flb_spectra_accumulate. */
+int flb_spectra_accumulate_static(int precision, int nx, int ny, int n_fields, const void* fields_dev,
+                                  double* pair_sums_dev, double* mean0_dev, void* cuda_stream);
+
 /* ---- training of the noise-scale network (learned extension) -------------
  * Weight vector (FP32, 1382 values): W1 (32x3) | W2 (32x32) | W3 (6x32) | b1 (32)
  * | b2 (32) | b3 (6), row-major; the order flb_set_mlp takes (weights, biases).

@@ -59,6 +59,8 @@ _SIGS = {
     "flb_spectra_scratch_bytes": (c_int, [c_int, c_int, c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
     "flb_spectra_accumulate": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_size_t, c_void_p]),
+    "flb_spectra_accumulate_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                              c_void_p]),
     "flb_philox": (c_int, [c_void_p, c_int, c_uint32, c_uint32, c_uint32, c_uint32, c_uint64, c_int,
                            c_void_p, c_void_p, c_void_p]),
 }
