@@ -46,6 +46,22 @@ def parse():
     return ap.parse_args()
 
 
+def rank_replica(p, rank):
+    """Weak scaling: every rank runs its own replica with its own Philox key and stream."""
+    return dict(p, seed=p["seed"] + rank, stream=rank)
+
+
+def job_throughput(sites_per_rank, steps, seconds_local, world, device="cpu"):
+    """(MLUPS of the whole job, slowest rank's seconds): the time is the maximum over ranks."""
+    import torch
+    t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return world * sites_per_rank * steps / tmax / 1e6, tmax
+
+
 def workload(n):
     from paper_1010_1233_gb300 import workloads as W
     wl = W.d2q9_16384(n)
@@ -180,7 +196,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     wl, p = workload(args.n)
-    p = dict(p, seed=p["seed"] + rank, stream=rank)
+    p = rank_replica(p, rank)
     sim = Sim(p, precision="fp32")
     wts = W.mlp_weights(1234, out_scale=0.1)
     sim.set_mlp(wts)
@@ -204,11 +220,8 @@ def run_ours(args):
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * V * K / (ms_max * 1e-3) / 1e6
+    value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
+    ms_max = t_max * 1e3
     n_samples = sum(1 for s in range(Wm, Wm + K) if s % SAMPLE_EVERY == 0)
     four_step = 1 if p["ny"] > 2048 else 0
     launches = K + n_samples * (2 + four_step)
@@ -250,10 +263,8 @@ def run_ours(args):
         L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * V * K / float(tt.item()) / 1e6, "unit": "MLUPS",
+        e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
+        e2e = {"value": e2e_value, "unit": "MLUPS",
                "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
                "pinned": pinned, "what": "flb_load(host state) + K steps + flb_save(host state)"}
 

@@ -166,6 +166,13 @@ int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks);
  * advancing it, so the simulation is unchanged.  Synchronises. */
 int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, double* ms_out);
 
+/* CUDA graphs (default on): flb_run replays a captured graph for every aligned
+ * chunk of sample_every steps (32 steps without sampling), which removes the
+ * per-kernel launch cost on small lattices.  Results are identical either way.
+ * The captured graphs are dropped when the launch configuration or the network
+ * switch changes.  enable = 0 issues every kernel directly. */
+int flb_set_graphs(flb_ctx* ctx, int enable);
+
 /* Destroy the context (does not free the caller's workspace). */
 void flb_destroy(flb_ctx* ctx);
 

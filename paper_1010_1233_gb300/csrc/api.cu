@@ -21,6 +21,8 @@ void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char
 void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,
                    uint64_t seed, int fp32, uint32_t* words, double* normals, cudaStream_t st);
 size_t mlp_weights_bytes();
+void launch_set_step(uint64_t* s, uint64_t v, cudaStream_t st);
+void launch_advance_step(uint64_t* s, uint64_t n, cudaStream_t st);
 void launch_twiddles(int precision, void* tw, int n, cudaStream_t st);
 int fft_rows_smem(int precision, int nx);
 int fft_cols_smem(int precision, int F, int ny, int ncol);
@@ -64,7 +66,7 @@ static constexpr int kStepBlock = 256;
 struct Layout {
   std::vector<ReplicaDesc> desc;
   int64_t off_descs = 0, off_vb_step = 0, off_vb_rows = 0, off_vb_cols = 0, off_vb_cols_a = 0;
-  int64_t off_status = 0, off_sums = 0, off_partial = 0, off_feq0 = 0, off_mlp = 0;
+  int64_t off_status = 0, off_sums = 0, off_partial = 0, off_feq0 = 0, off_mlp = 0, off_stepdev = 0;
   int64_t total = 0;
   int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0, n_vb_cols_a = 0;
   std::vector<int64_t> vb_step, vb_rows, vb_cols, vb_cols_a;
@@ -218,10 +220,10 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   if (L.any_fields) {
     const int cs = precision == FLB_FP64 ? 16 : 8;
     L.ncol = 16;
-    while (L.ncol > 1 && (int64_t)maxF * maxlen * L.ncol * cs > kColsSmemBudget) L.ncol >>= 1;
-    L.rows_smem = maxnx * cs;
+    while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
+    L.rows_smem = fft_rows_smem(precision, maxnx);
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
-    L.cols_smem = maxF * maxlen * L.ncol * cs;
+    L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
   }
   plan_step(lat, L.vec, L);
   for (int r = 0; r < n; ++r) {
@@ -246,6 +248,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   L.off_partial = off; off = align256(off + 8 * 3 * (int64_t)kReduceBlocks);
   L.off_feq0 = off; off = align256(off + 8 * 18 * (int64_t)n);
   L.off_mlp = off; off = align256(off + (int64_t)mlp_weights_bytes());
+  L.off_stepdev = off; off = align256(off + 8);
   L.total = off;
   return FLB_OK;
 }
@@ -253,6 +256,9 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
 }  // namespace flb
 
 using namespace flb;
+
+static constexpr uint32_t kGraphChunk = 32;      // steps per captured chunk without sampling
+static constexpr uint32_t kMaxGraphChunk = 4096;  // longer sampling periods are issued directly
 
 struct flb_ctx {
   int precision = 0, lattice = 0, n = 0;
@@ -264,6 +270,10 @@ struct flb_ctx {
   int sms = 1;
   int step_grid = 0;          // 0: min(virtual blocks, 16 x SMs)
   bool mlp_on = false;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  struct Graph { uint32_t len; bool sample; cudaGraphExec_t exec; };
+  std::vector<Graph> graphs;
   std::vector<float> mlp_host;
 };
 
@@ -367,8 +377,26 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
   return FLB_OK;
 }
 
-int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
-  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+// Issue one step (and its sampling) on stream st.  With S.step_dev set, S.step is the
+// offset from the device step counter (graph capture); otherwise the absolute step.
+static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
+  const Layout& L = c->L;
+  launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, st);
+  if (sample) {
+    const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
+    const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
+    const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
+    launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
+                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st);
+    if (L.n_vb_cols_a)
+      launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
+                        L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st);
+    launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
+                    L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st);
+  }
+}
+
+static StepLaunch step_launch(flb_ctx* c) {
   const Layout& L = c->L;
   StepLaunch S;
   S.descs = descs_dev(c);
@@ -379,28 +407,94 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   S.mlp = c->ws + L.off_mlp;
   S.block = kStepBlock;
   S.grid = (int)std::min<int64_t>(L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
-  const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
-  const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
-  const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
-  for (uint64_t i = 0; i < n_steps; ++i) {
+  S.parity = 0;
+  S.step = 0;
+  return S;
+}
+
+static void drop_graphs(flb_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+// A chunk of `len` steps starting at a step that is a multiple of len, sampling at its
+// first step when `sample`; it ends by advancing the device step counter by len.
+static int chunk_graph(flb_ctx* c, uint32_t len, bool sample, cudaGraphExec_t* out) {
+  for (auto& g : c->graphs)
+    if (g.len == len && g.sample == sample) { *out = g.exec; return FLB_OK; }
+  if (!c->cap_stream) {
+    int rc = cuda_check(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+    if (rc) return rc;
+  }
+  StepLaunch S = step_launch(c);
+  S.step_dev = reinterpret_cast<const uint64_t*>(c->ws + c->L.off_stepdev);
+  int rc = cuda_check(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (rc) return rc;
+  for (uint32_t o = 0; o < len; ++o) {
+    S.step = o;
+    issue_step(c, S, sample && o == 0, c->cap_stream);
+  }
+  launch_advance_step(reinterpret_cast<uint64_t*>(c->ws + c->L.off_stepdev), len, c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  rc = cuda_check(cudaStreamEndCapture(c->cap_stream, &graph), "end capture");
+  if (rc) return rc;
+  cudaGraphExec_t exec = nullptr;
+  rc = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "instantiate graph");
+  cudaGraphDestroy(graph);
+  if (rc) return rc;
+  c->graphs.push_back({len, sample, exec});
+  *out = exec;
+  return FLB_OK;
+}
+
+int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  const Layout& L = c->L;
+  const bool sampling = sample_every && L.any_fields;
+  StepLaunch S = step_launch(c);
+  auto plain = [&]() {
     const uint64_t t = c->step;
-    const bool sample = sample_every && L.any_fields && (t % sample_every) == 0;
+    const bool sample = sampling && (t % sample_every) == 0;
     S.parity = (int)(t & 1);
     S.step = (uint32_t)t;
-    launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, c->stream);
-    if (sample) {
-      launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
-                      L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, c->stream);
-      if (L.n_vb_cols_a)
-        launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
-                          L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, c->stream);
-      launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
-                      L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, c->stream);
-      ++c->n_samples;
-    }
+    issue_step(c, S, sample, c->stream);
+    if (sample) ++c->n_samples;
     ++c->step;
+  };
+  // chunks of `len` steps replay a captured graph; steps before the first aligned chunk
+  // and after the last one are issued directly
+  const uint32_t len = sampling ? sample_every : kGraphChunk;
+  uint64_t i = 0;
+  if (c->use_graphs && n_steps >= 2 * (uint64_t)len && len <= kMaxGraphChunk) {
+    while (i < n_steps && (c->step % len) != 0) { plain(); ++i; }
+    const uint64_t chunks = (n_steps - i) / len;
+    if (chunks) {
+      cudaGraphExec_t exec = nullptr;
+      int rc = chunk_graph(c, len, sampling, &exec);
+      if (rc) return rc;
+      launch_set_step(reinterpret_cast<uint64_t*>(c->ws + L.off_stepdev), c->step, c->stream);
+      for (uint64_t k = 0; k < chunks; ++k) {
+        rc = cuda_check(cudaGraphLaunch(exec, c->stream), "graph launch");
+        if (rc) return rc;
+      }
+      c->step += chunks * len;
+      if (sampling) c->n_samples += chunks;
+      i += chunks * len;
+    }
   }
+  while (i < n_steps) { plain(); ++i; }
   return cuda_check(cudaGetLastError(), "flb_run launch");
+}
+
+int flb_set_graphs(flb_ctx* c, int enable) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  c->use_graphs = enable != 0;
+  if (!enable) {
+    int rc = cuda_check(cudaStreamSynchronize(c->stream), "graphs");
+    if (rc) return rc;
+    drop_graphs(c);
+  }
+  return FLB_OK;
 }
 
 int flb_sync(flb_ctx* c) {
@@ -593,6 +687,11 @@ int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int ena
     rc = cuda_check(cudaStreamSynchronize(c->stream), "copy mlp");
     if (rc) return rc;
   }
+  if ((enable != 0) != c->mlp_on) {
+    int rc = cuda_check(cudaStreamSynchronize(c->stream), "set mlp");
+    if (rc) return rc;
+    drop_graphs(c);
+  }
   c->mlp_on = enable != 0;
   return FLB_OK;
 }
@@ -677,6 +776,7 @@ int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks) {
   if (grid_blocks < 0) return set_error(FLB_EINVAL, "grid_blocks must be >= 0");
   int rc = cuda_check(cudaStreamSynchronize(c->stream), "step config");
   if (rc) return rc;
+  drop_graphs(c);
   plan_step(c->lattice, vec, c->L);
   rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
                              cudaMemcpyHostToDevice), "copy descriptors");
@@ -751,7 +851,13 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms
   return FLB_OK;
 }
 
-void flb_destroy(flb_ctx* c) { delete c; }
+void flb_destroy(flb_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
 
 int flb_philox(const uint32_t* site_dev, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,
                uint64_t seed, int fp32, uint32_t* words_out_dev, double* normals_out_dev, void* cuda_stream) {

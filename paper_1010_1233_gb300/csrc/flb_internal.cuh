@@ -123,6 +123,7 @@ template <> struct vec2_of<double> { using type = double2; };
 struct StepLaunch {
   const ReplicaDesc* descs; const int64_t* vb_begin; int n_reps; int64_t n_vblocks;
   char* ws; int parity; uint32_t step; const void* mlp; int grid; int block;
+  const uint64_t* step_dev = nullptr;   // non-NULL (graph replay): step = *step_dev + step
 };
 
 // Shared-memory budget of the column transforms and their split rule: one pass of
@@ -132,7 +133,7 @@ constexpr int kColsSmemBudget = 200 * 1024;
 constexpr int kColsBlock = 256;
 inline int column_split(int precision, int F, int ny) {
   const int cs = precision == FLB_FP64 ? 16 : 8;
-  if ((int64_t)F * ny * 4 * cs <= kColsSmemBudget) return 0;
+  if ((int64_t)F * (ny + 1) * 4 * cs <= kColsSmemBudget) return 0;
   int l = 0;
   while ((1 << l) < ny) ++l;
   return l / 2;

@@ -11,7 +11,25 @@
 #include <cstdio>
 #include "flb_internal.cuh"
 
+#ifndef FLB_MMA_VOLATILE
+#define FLB_MMA_VOLATILE 1   // keep the MMA chains in program order (the compiler may not interleave tiles)
+#endif
+#if FLB_MMA_VOLATILE
+#define FLB_MMA_ASM asm volatile
+#else
+#define FLB_MMA_ASM asm
+#endif
+#ifndef FLB_STEP_MINB
+#define FLB_STEP_MINB 2        // minimum resident blocks per SM (network variants: <= 128 registers)
+#endif
+#ifndef FLB_STEP_MINB_PLAIN
+#define FLB_STEP_MINB_PLAIN 3  // minimum resident blocks per SM (plain variants: caps registers at 85)
+#endif
+
+
+
 namespace flb {
+
 
 // Per-site noise-scale network weights, FP32 copies of the bfloat16 weights.
 struct MlpWeights {
@@ -97,7 +115,7 @@ __device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
 // d = a b + (c0, c1, c0, c1)
 __device__ __forceinline__ void mma_bias(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1,
                                          float2 c) {
-  asm volatile(
+  FLB_MMA_ASM(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%10,%11,%10,%11};\n"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
@@ -106,7 +124,7 @@ __device__ __forceinline__ void mma_bias(float (&d)[4], const uint32_t (&a)[4], 
 
 // d += a b
 __device__ __forceinline__ void mma_acc(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
+  FLB_MMA_ASM(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -186,16 +204,80 @@ __device__ __forceinline__ void mlp_tile(const MlpLane& M, int q, uint2 f0, uint
   mma_acc(o, a2[1], b3.z, b3.w);
 }
 
+// Two independent 16-site tiles with their instruction streams interleaved by hand,
+// so the tensor pipe always has a second MMA chain to work on while one waits.
+__device__ __forceinline__ void mlp_tile2(const MlpLane& M, int q, uint2 fa0, uint2 fa1, uint2 fb0, uint2 fb1,
+                                          float (&oa)[4], float (&ob)[4]) {
+  uint32_t a[4] = {0u, 0u, 0u, 0u}, b[4] = {0u, 0u, 0u, 0u};
+  if (q == 0) { a[0] = fa0.x; a[1] = fa1.x; b[0] = fb0.x; b[1] = fb1.x; }
+  if (q == 1) { a[0] = fa0.y; a[1] = fa1.y; b[0] = fb0.y; b[1] = fb1.y; }
+  const uint4 b1 = M.b1;
+  const float4 c1a = M.c1[0], c1b = M.c1[1];
+  const float2 c1[4] = {make_float2(c1a.x, c1a.y), make_float2(c1a.z, c1a.w), make_float2(c1b.x, c1b.y),
+                        make_float2(c1b.z, c1b.w)};
+  const uint32_t b1w[4] = {b1.x, b1.y, b1.z, b1.w};
+  float ha[4][4], hb[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {                                                    // layer 1
+    mma_bias(ha[j], a, b1w[j], 0u, c1[j]);
+    mma_bias(hb[j], b, b1w[j], 0u, c1[j]);
+  }
+  uint32_t pa[2][4], pb[2][4];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    pa[t][0] = relu_pack(ha[2 * t][0], ha[2 * t][1]);         pb[t][0] = relu_pack(hb[2 * t][0], hb[2 * t][1]);
+    pa[t][1] = relu_pack(ha[2 * t][2], ha[2 * t][3]);         pb[t][1] = relu_pack(hb[2 * t][2], hb[2 * t][3]);
+    pa[t][2] = relu_pack(ha[2 * t + 1][0], ha[2 * t + 1][1]); pb[t][2] = relu_pack(hb[2 * t + 1][0], hb[2 * t + 1][1]);
+    pa[t][3] = relu_pack(ha[2 * t + 1][2], ha[2 * t + 1][3]); pb[t][3] = relu_pack(hb[2 * t + 1][2], hb[2 * t + 1][3]);
+  }
+  const float4 c2a = M.c2[0], c2b = M.c2[1];
+  const float2 c2[4] = {make_float2(c2a.x, c2a.y), make_float2(c2a.z, c2a.w), make_float2(c2b.x, c2b.y),
+                        make_float2(c2b.z, c2b.w)};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {                                                    // layer 2
+    const uint4 w = M.b2[j];
+    mma_bias(ha[j], pa[0], w.x, w.y, c2[j]);
+    mma_bias(hb[j], pb[0], w.x, w.y, c2[j]);
+    mma_acc(ha[j], pa[1], w.z, w.w);
+    mma_acc(hb[j], pb[1], w.z, w.w);
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    pa[t][0] = relu_pack(ha[2 * t][0], ha[2 * t][1]);         pb[t][0] = relu_pack(hb[2 * t][0], hb[2 * t][1]);
+    pa[t][1] = relu_pack(ha[2 * t][2], ha[2 * t][3]);         pb[t][1] = relu_pack(hb[2 * t][2], hb[2 * t][3]);
+    pa[t][2] = relu_pack(ha[2 * t + 1][0], ha[2 * t + 1][1]); pb[t][2] = relu_pack(hb[2 * t + 1][0], hb[2 * t + 1][1]);
+    pa[t][3] = relu_pack(ha[2 * t + 1][2], ha[2 * t + 1][3]); pb[t][3] = relu_pack(hb[2 * t + 1][2], hb[2 * t + 1][3]);
+  }
+  const uint4 b3 = M.b3;
+  const float4 c3 = M.c3;
+  mma_bias(oa, pa[0], b3.x, b3.y, make_float2(c3.x, c3.y));                       // layer 3
+  mma_bias(ob, pb[0], b3.x, b3.y, make_float2(c3.x, c3.y));
+  mma_acc(oa, pa[1], b3.z, b3.w);
+  mma_acc(ob, pb[1], b3.z, b3.w);
+}
+
 // ---------------------------------------------------------------------------
 // D2Q9.  Population order (Sec. 3): 0 (0,0), 1 (1,0), 2 (0,1), 3 (-1,0), 4 (0,-1),
 // 5 (1,1), 6 (-1,1), 7 (-1,-1), 8 (1,-1).
-template <typename R, bool DEV, int VEC, bool SAMPLE, bool MLP>
-__global__ void __launch_bounds__(kStepThreads)
+// Network modes of the D2Q9 step kernel: kMlpOff (s = 1) or kMlpWarp (each warp evaluates
+// the network for its own sites between the loads and the collision, two 16-site tiles at
+// a time).  A warp-specialised variant (separate network warps, block barriers) measured
+// slower on GB300: its register union halves the resident blocks.
+constexpr int kMlpOff = 0, kMlpWarp = 1;
+
+template <typename R, bool DEV, int VEC, bool SAMPLE, int NET>
+__global__ void __launch_bounds__(kStepThreads, NET == kMlpOff ? FLB_STEP_MINB_PLAIN : FLB_STEP_MINB)
 k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin, int n_reps,
             int64_t n_vblocks, char* __restrict__ ws, int parity, uint32_t step,
-            const MlpWeights* __restrict__ mlp_w) {
+            const MlpWeights* __restrict__ mlp_w, const uint64_t* __restrict__ step_dev) {
+  if (step_dev) {                  // graph replay: step = device base + offset
+    const uint64_t t = *step_dev + step;
+    step = (uint32_t)t;
+    parity = (int)(t & 1);
+  }
   constexpr int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
   constexpr int VY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr bool MLP = NET != kMlpOff;
   static_assert(!MLP || sizeof(R) == 4, "the network runs on the FP32 path");
   __shared__ MlpFrags sfr;
   __shared__ uint2 s_feat[MLP ? kStepThreads * VEC : 1];
@@ -213,9 +295,10 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
     // per-replica unit counts stay below 2^31 (sites < 2^32, at least 2 sites per unit or VEC = 1
     // on lattices of < 2^31 sites), so the index arithmetic is 32-bit
     const int n_units = (int)d.n_units, upr = d.units_per_row;
-    const int unit_raw = (int)(vb - vb_begin[r]) * (int)blockDim.x + (int)threadIdx.x;
+    const int tid = (int)threadIdx.x;
+    const int unit_raw = (int)(vb - vb_begin[r]) * kStepThreads + tid;
     const bool active = unit_raw < n_units;
-    const int unit = active ? unit_raw : n_units - 1;
+    const int unit = unit_raw < n_units ? unit_raw : n_units - 1;
     const int y = (int)((unsigned)unit / (unsigned)upr);
     const int xq = unit - y * upr;
     const int x0 = xq * VEC;
@@ -225,73 +308,82 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
     // neighbour lanes hold the adjacent unit of the same row?
     const bool left_in_warp = lane > 0 && xq > 0;
     const bool right_in_warp = lane < 31 && (xq + 1) < upr && (unit_raw + 1) < n_units;
+    const R rho0 = coef<R>(d, kCoRho0);
+    const bool noisy = d.noise_mask != 0;
 
-    // ---- pull streaming: f_i(x) = f*_i(x - v_i) -------------------------
     R f[9][VEC];
+    R sum[VEC], ux[VEC], uy[VEC];
+    {
+      // ---- pull streaming: f_i(x) = f*_i(x - v_i) -------------------------
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      int ys = y - VY[i];
-      ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-      const R* row = src + i * plane + (int64_t)ys * nx;
-      R v[VEC];
-      VecIO<R, VEC>::ld(row + x0, v);
-      if (VX[i] == 0) {
+      for (int i = 0; i < 9; ++i) {
+        int ys = y - VY[i];
+        ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+        const R* row = src + i * plane + (int64_t)ys * nx;
+        R v[VEC];
+        VecIO<R, VEC>::ld(row + x0, v);
+        if (VX[i] == 0) {
 #pragma unroll
-        for (int s = 0; s < VEC; ++s) f[i][s] = v[s];
-      } else if (VX[i] == 1) {                    // needs x0-1 .. x0+VEC-2
-        R left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
-        if (!left_in_warp) left = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
-        f[i][0] = left;
+          for (int s = 0; s < VEC; ++s) f[i][s] = v[s];
+        } else if (VX[i] == 1) {                    // needs x0-1 .. x0+VEC-2
+          R left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
+          if (!left_in_warp) left = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
+          f[i][0] = left;
 #pragma unroll
-        for (int s = 1; s < VEC; ++s) f[i][s] = v[s - 1];
-      } else {                                   // needs x0+1 .. x0+VEC
-        R right = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (!right_in_warp) right = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
+          for (int s = 1; s < VEC; ++s) f[i][s] = v[s - 1];
+        } else {                                   // needs x0+1 .. x0+VEC
+          R right = __shfl_down_sync(0xffffffffu, v[0], 1);
+          if (!right_in_warp) right = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
 #pragma unroll
-        for (int s = 0; s < VEC - 1; ++s) f[i][s] = v[s + 1];
-        f[i][VEC - 1] = right;
+          for (int s = 0; s < VEC - 1; ++s) f[i][s] = v[s + 1];
+          f[i][VEC - 1] = right;
+        }
+      }
+      // ---- density, momentum, velocity (Sec. 2) ----------------------------
+      // deviation storage: sum_i w_i rho0 = rho0 and sum_i w_i rho0 v_i = 0
+#pragma unroll
+      for (int s = 0; s < VEC; ++s) {
+        sum[s] = ((f[0][s] + (f[1][s] + f[3][s])) + (f[2][s] + f[4][s])) + ((f[5][s] + f[7][s]) + (f[6][s] + f[8][s]));
+        const R jx = (f[1][s] - f[3][s]) + ((f[5][s] - f[7][s]) + (f[8][s] - f[6][s]));
+        const R jy = (f[2][s] - f[4][s]) + ((f[5][s] - f[7][s]) + (f[6][s] - f[8][s]));
+        const R irho = (R)1 / (DEV ? rho0 + sum[s] : sum[s]);
+        ux[s] = jx * irho;
+        uy[s] = jy * irho;
+      }
+      if constexpr (MLP) {
+#pragma unroll
+        for (int s = 0; s < VEC; ++s)
+          s_feat[tid * VEC + s] = make_uint2(pack_bf16((float)ux[s], (float)uy[s]),
+                                             pack_bf16((float)(DEV ? sum[s] : sum[s] - rho0), 0.f));
       }
     }
 
-    const R rho0 = coef<R>(d, kCoRho0);
-    // ---- density, momentum, velocity (Sec. 2) ----------------------------
-    // deviation storage: sum_i w_i rho0 = rho0 and sum_i w_i rho0 v_i = 0
-    R sum[VEC], ux[VEC], uy[VEC];
-#pragma unroll
-    for (int s = 0; s < VEC; ++s) {
-      sum[s] = ((f[0][s] + (f[1][s] + f[3][s])) + (f[2][s] + f[4][s])) + ((f[5][s] + f[7][s]) + (f[6][s] + f[8][s]));
-      const R jx = (f[1][s] - f[3][s]) + ((f[5][s] - f[7][s]) + (f[8][s] - f[6][s]));
-      const R jy = (f[2][s] - f[4][s]) + ((f[5][s] - f[7][s]) + (f[6][s] - f[8][s]));
-      const R irho = (R)1 / (DEV ? rho0 + sum[s] : sum[s]);
-      ux[s] = jx * irho;
-      uy[s] = jy * irho;
-    }
     // ---- per-site noise scales from the network (tensor cores) --------------
-    if constexpr (MLP) {
-      uint2* feat = s_feat + warp * 32 * VEC;
-      float2* outw = s_out + warp * 32 * VEC * 4;
-#pragma unroll
-      for (int s = 0; s < VEC; ++s)
-        feat[lane * VEC + s] = make_uint2(pack_bf16((float)ux[s], (float)uy[s]),
-                                          pack_bf16((float)(DEV ? sum[s] : sum[s] - rho0), 0.f));
+    // warp sites w = tid * VEC + s; 16-site tile m covers w in [16m, 16m + 16)
+    if constexpr (NET == kMlpWarp) {
       __syncwarp();
       const int g = lane >> 2, q = lane & 3;
+      const uint2* feat = s_feat + warp * 32 * VEC;
+      float2* outw = s_out + warp * 32 * VEC * 4;
 #pragma unroll 1
-      for (int m = 0; m < 2 * VEC; ++m) {
-        float o[4];
-        mlp_tile(sfr.lanes[lane], q, feat[16 * m + g], feat[16 * m + g + 8], o);
+      for (int m = 0; m < 2 * VEC; m += 2) {
+        float oa[4], ob[4];
+        mlp_tile2(sfr.lanes[lane], q, feat[16 * m + g], feat[16 * m + g + 8], feat[16 * m + 16 + g],
+                  feat[16 * m + 24 + g], oa, ob);
         if (q < 3) {
-          outw[(16 * m + g) * 4 + q] = make_float2(o[0], o[1]);
-          outw[(16 * m + g + 8) * 4 + q] = make_float2(o[2], o[3]);
+          outw[(16 * m + g) * 4 + q] = make_float2(oa[0], oa[1]);
+          outw[(16 * m + g + 8) * 4 + q] = make_float2(oa[2], oa[3]);
+          outw[(16 * m + 16 + g) * 4 + q] = make_float2(ob[0], ob[1]);
+          outw[(16 * m + 24 + g) * 4 + q] = make_float2(ob[2], ob[3]);
         }
       }
       __syncwarp();
     }
+
     const R it3 = coef<R>(d, kCoInvTau + 3), it4 = coef<R>(d, kCoInvTau + 4), it5 = coef<R>(d, kCoInvTau + 5);
     const R it6 = coef<R>(d, kCoInvTau + 6), it7 = coef<R>(d, kCoInvTau + 7), it8 = coef<R>(d, kCoInvTau + 8);
     const R a3 = coef<R>(d, kCoAmp + 3), a4 = coef<R>(d, kCoAmp + 4), a5 = coef<R>(d, kCoAmp + 5);
     const R a6 = coef<R>(d, kCoAmp + 6), a7 = coef<R>(d, kCoAmp + 7), a8 = coef<R>(d, kCoAmp + 8);
-    const bool noisy = d.noise_mask != 0;
     const R S3 = (R)1.7320508075688772935, S32 = (R)1.2247448713915890491,
             S6 = (R)2.4494897427831780982;
     R fld[kMaxFields][VEC];
@@ -326,22 +418,24 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
       R D3 = (E3 - M3) * it3, D4 = (E4 - M4) * it4, D5 = (E5 - M5) * it5;
       R D6 = -M6 * it6, D7 = -M7 * it7, D8 = -M8 * it8;
       if (noisy) {
-        const uint32_t site = (uint32_t)y * (uint32_t)nx + (uint32_t)(x0 + s);
-        const uint4 w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
-        const uint4 w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
-        R n0, n1, n2, n3, n4, n5;
-        box_muller(w0.x, w0.y, n0, n1);
-        box_muller(w0.z, w0.w, n2, n3);
-        box_muller(w1.x, w1.y, n4, n5);
+        R nrm[6];
+        {
+          const uint32_t site = (uint32_t)y * (uint32_t)nx + (uint32_t)(x0 + s);
+          const uint4 w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
+          const uint4 w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
+          box_muller(w0.x, w0.y, nrm[0], nrm[1]);
+          box_muller(w0.z, w0.w, nrm[2], nrm[3]);
+          box_muller(w1.x, w1.y, nrm[4], nrm[5]);
+        }
         R sc[6] = {(R)1, (R)1, (R)1, (R)1, (R)1, (R)1};
         if constexpr (MLP) {
-          const float2* o = s_out + (warp * 32 * VEC + lane * VEC + s) * 4;
+          const float2* o = s_out + (tid * VEC + s) * 4;
           const float2 o01 = o[0], o23 = o[1], o45 = o[2];
           sc[0] = (R)1 + (R)o01.x; sc[1] = (R)1 + (R)o01.y; sc[2] = (R)1 + (R)o23.x;
           sc[3] = (R)1 + (R)o23.y; sc[4] = (R)1 + (R)o45.x; sc[5] = (R)1 + (R)o45.y;
         }
-        D3 += sc[0] * a3 * n0; D4 += sc[1] * a4 * n1; D5 += sc[2] * a5 * n2;
-        D6 += sc[3] * a6 * n3; D7 += sc[4] * a7 * n4; D8 += sc[5] * a8 * n5;
+        D3 += sc[0] * a3 * nrm[0]; D4 += sc[1] * a4 * nrm[1]; D5 += sc[2] * a5 * nrm[2];
+        D6 += sc[3] * a6 * nrm[3]; D7 += sc[4] * a7 * nrm[4]; D8 += sc[5] * a8 * nrm[5];
       }
       // back transform of the moment change, n_i^a = w_i m_i^a
       const R w1 = (R)1 / (R)9, w5 = (R)1 / (R)36;
@@ -390,7 +484,13 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
 template <typename R, bool DEV, bool SAMPLE>
 __global__ void __launch_bounds__(256)
 k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin, int n_reps,
-            int64_t n_vblocks, char* __restrict__ ws, int parity, uint32_t step) {
+            int64_t n_vblocks, char* __restrict__ ws, int parity, uint32_t step,
+            const uint64_t* __restrict__ step_dev) {
+  if (step_dev) {
+    const uint64_t t = *step_dev + step;
+    step = (uint32_t)t;
+    parity = (int)(t & 1);
+  }
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_replica(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
@@ -594,15 +694,15 @@ __global__ void k_philox(const uint32_t* site, int n, uint32_t step, uint32_t ca
 template <typename R, bool DEV, int VEC>
 static void launch_d2q9_vec(const StepLaunch& L, bool sample, bool mlp, cudaStream_t st) {
   auto w = reinterpret_cast<const MlpWeights*>(L.mlp);
-#define FLB_L(S, M) k_step_d2q9<R, DEV, VEC, S, M><<<L.grid, L.block, 0, st>>>( \
-      L.descs, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, w)
+#define FLB_L(S, N, B) k_step_d2q9<R, DEV, VEC, S, N><<<L.grid, B, 0, st>>>( \
+      L.descs, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, w, L.step_dev)
   if constexpr (sizeof(R) == 4) {
     if (mlp) {
-      if (sample) FLB_L(true, true); else FLB_L(false, true);
+      if (sample) FLB_L(true, kMlpWarp, kStepThreads); else FLB_L(false, kMlpWarp, kStepThreads);
       return;
     }
   }
-  if (sample) FLB_L(true, false); else FLB_L(false, false);
+  if (sample) FLB_L(true, kMlpOff, kStepThreads); else FLB_L(false, kMlpOff, kStepThreads);
 #undef FLB_L
 }
 
@@ -615,7 +715,7 @@ void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool 
     else launch_d2q9_vec<float, true, 1>(L, sample, mlp, st);
   } else {
 #define FLB_L1(R, DEV, S) k_step_d1q3<R, DEV, S><<<L.grid, L.block, 0, st>>>( \
-      L.descs, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step)
+      L.descs, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, L.step_dev)
     if (precision == FLB_FP64) { if (sample) FLB_L1(double, false, true); else FLB_L1(double, false, false); }
     else { if (sample) FLB_L1(float, true, true); else FLB_L1(float, true, false); }
 #undef FLB_L1
@@ -651,5 +751,11 @@ void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, ui
 }
 
 size_t mlp_weights_bytes() { return sizeof(MlpWeights); }
+
+__global__ void k_set_step(uint64_t* s, uint64_t v) { *s = v; }
+__global__ void k_advance_step(uint64_t* s, uint64_t n) { *s += n; }
+
+void launch_set_step(uint64_t* s, uint64_t v, cudaStream_t st) { k_set_step<<<1, 1, 0, st>>>(s, v); }
+void launch_advance_step(uint64_t* s, uint64_t n, cudaStream_t st) { k_advance_step<<<1, 1, 0, st>>>(s, n); }
 
 }  // namespace flb

@@ -24,10 +24,12 @@ template <typename R> __device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
 
 // In-place radix-2 decimation-in-time FFTs on n_fft sequences of length 2^logn in
 // shared memory, sequence k at data + k * seq_stride, already in bit-reversed order.
-// tw[m * tw_stride] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  All threads of the block call it.
+// tw[m * tw_stride] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  Element i of a sequence is
+// stored at i + (i >> pad_shift) (one pad slot per 2^pad_shift elements, so that the
+// bit-reversed scatter does not hit one bank).  All threads of the block call it.
 template <typename R>
 __device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C<R>* __restrict__ tw,
-                        int tw_stride) {
+                        int tw_stride, int pad_shift = 31) {
   if (logn == 0) return;
   const int half_n = 1 << (logn - 1);
   const int total = n_fft * half_n;
@@ -41,12 +43,13 @@ __device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C
       const int i0 = ((j >> s) << (s + 1)) + pos;
       C<R>* d = data + k * seq_stride;
       const C<R> w = tw[(pos << tshift) * tw_stride];
-      const C<R> a = d[i0];
-      const C<R> t = cmul<R>(d[i0 + half], w);
+      const int p0 = i0 + (i0 >> pad_shift), p1 = i0 + half + ((i0 + half) >> pad_shift);
+      const C<R> a = d[p0];
+      const C<R> t = cmul<R>(d[p1], w);
       C<R> u, v;
       u.x = a.x + t.x; u.y = a.y + t.y;
       v.x = a.x - t.x; v.y = a.y - t.y;
-      d[i0] = u; d[i0 + half] = v;
+      d[p0] = u; d[p1] = v;
     }
     __syncthreads();
   }
@@ -84,20 +87,23 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
     const R* fields = reinterpret_cast<const R*>(ws + d.off_fields);
     const R* xa = fields + fa * plane + (int64_t)y * nx;
     const R* xb = fields + fb * plane + (int64_t)y * nx;
+    const int ps = logn > 5 ? logn - 5 : 31;        // 32 pad slots per row
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       C<R> v; v.x = xa[x]; v.y = has_b ? xb[x] : (R)0;
-      z[brev(x, logn)] = v;
+      const int i = brev(x, logn);
+      z[i + (i >> ps)] = v;
     }
     __syncthreads();
-    dit_fft<R>(z, logn, 1, 0, reinterpret_cast<const C<R>*>(ws + d.off_tw_x), 1);
+    dit_fft<R>(z, logn, 1, 0, reinterpret_cast<const C<R>*>(ws + d.off_tw_x), 1, ps);
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     C<R>* ra = spec + fa * fplane + (int64_t)y * d.wpitch;
     C<R>* rb = spec + fb * fplane + (int64_t)y * d.wpitch;
     const int hn = nx >> 1;
     for (int k = threadIdx.x; k <= hn; k += blockDim.x) {
-      const C<R> Z = z[k];
-      const C<R> Zm = z[(nx - k) & (nx - 1)];
+      const int km = (nx - k) & (nx - 1);
+      const C<R> Z = z[k + (k >> ps)];
+      const C<R> Zm = z[km + (km >> ps)];
       C<R> A; A.x = (R)0.5 * (Z.x + Zm.x); A.y = (R)0.5 * (Z.y - Zm.y);
       ra[k] = A;
       if (has_b) {            // (Z - conj(Zm)) / (2i)
@@ -133,11 +139,11 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
       const int f = i / (ncol * n1);
       C<R> v; v.x = (R)0; v.y = (R)0;
       if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
-      s[(f * ncol + c) * n1 + brev(y1, logn1)] = v;
+      s[(f * ncol + c) * (n1 + 1) + brev(y1, logn1)] = v;
     }
     __syncthreads();
     const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_y);
-    dit_fft<R>(s, logn1, F * ncol, n1, tw, n2);
+    dit_fft<R>(s, logn1, F * ncol, n1 + 1, tw, n2);
     const int hn = d.ny >> 1;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
       const int c = i % ncol;
@@ -147,7 +153,7 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
       const int e = y2 * k1;                       // < ny
       C<R> w = tw[e < hn ? e : e - hn];
       if (e >= hn) { w.x = -w.x; w.y = -w.y; }
-      spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c] = cmul<R>(s[(f * ncol + c) * n1 + k1], w);
+      spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c] = cmul<R>(s[(f * ncol + c) * (n1 + 1) + k1], w);
     }
     __syncthreads();
   }
@@ -180,10 +186,10 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
       const int f = i / (ncol * n2);
       C<R> v; v.x = (R)0; v.y = (R)0;
       if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
-      s[(f * ncol + c) * n2 + brev(y2, logn2)] = v;
+      s[(f * ncol + c) * (n2 + 1) + brev(y2, logn2)] = v;
     }
     __syncthreads();
-    dit_fft<R>(s, logn2, F * ncol, n2, reinterpret_cast<const C<R>*>(ws + d.off_tw_y), n1);
+    dit_fft<R>(s, logn2, F * ncol, n2 + 1, reinterpret_cast<const C<R>*>(ws + d.off_tw_y), n1);
     // accumulate pair products in FP64; k = 0 sums for the mean subtraction
     const int npts = n2 * ncol;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
@@ -195,23 +201,23 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
       const int64_t pt = (int64_t)ky * d.half_nx + kx;
       for (int pr = 0; pr < d.n_pairs; ++pr) {
         const int a = d.pair_a[pr], b = d.pair_b[pr];
-        const C<R> Xa = s[(a * ncol + c) * n2 + k2];
-        const C<R> Xb = s[(b * ncol + c) * n2 + k2];
-        const double xr = (double)Xa.x, xi = (double)Xa.y, yr = (double)Xb.x, yi = (double)Xb.y;
+        const C<R> Xa = s[(a * ncol + c) * (n2 + 1) + k2];
+        const C<R> Xb = s[(b * ncol + c) * (n2 + 1) + k2];
+        // the product in the transform's precision (exact to its rounding), the sum in FP64
         if (a == b) {
           double* acc = reinterpret_cast<double*>(ws + d.pair_off[pr]);
-          acc[pt] += xr * xr + xi * xi;
+          acc[pt] += (double)(Xa.x * Xa.x + Xa.y * Xa.y);
         } else {
           double2* acc = reinterpret_cast<double2*>(ws + d.pair_off[pr]);
           double2 v = acc[pt];
-          v.x += xr * yr + xi * yi;          // X_a X_b^*
-          v.y += xi * yr - xr * yi;
+          v.x += (double)(Xa.x * Xb.x + Xa.y * Xb.y);          // X_a X_b^*
+          v.y += (double)(Xa.y * Xb.x - Xa.x * Xb.y);
           acc[pt] = v;
         }
       }
       if (kx == 0 && ky == 0) {
         double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
-        for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol + c) * n2].x;
+        for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol + c) * (n2 + 1)].x;
       }
     }
     __syncthreads();
@@ -238,8 +244,8 @@ void launch_twiddles(int precision, void* tw, int n, cudaStream_t st) {
     k_twiddles<float><<<(half + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2*>(tw), n);
 }
 
-int fft_rows_smem(int precision, int nx) { return nx * (precision == FLB_FP64 ? 16 : 8); }
-int fft_cols_smem(int precision, int F, int ny, int ncol) { return F * ny * ncol * (precision == FLB_FP64 ? 16 : 8); }
+int fft_rows_smem(int precision, int nx) { return (nx + 32) * (precision == FLB_FP64 ? 16 : 8); }
+int fft_cols_smem(int precision, int F, int ny, int ncol) { return F * (ny + 1) * ncol * (precision == FLB_FP64 ? 16 : 8); }
 
 cudaError_t set_fft_smem_limits() {
   cudaError_t e;

@@ -52,10 +52,10 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   d.wpitch = (d.half_nx + 1) & ~1;
   d.log2n1 = l1;
   P.ncol = 16;
-  while (P.ncol > 1 && (int64_t)F * len * P.ncol * cs > kColsSmemBudget) P.ncol >>= 1;
-  P.rows_smem = nx * cs;
+  while (P.ncol > 1 && fft_cols_smem(precision, F, len, P.ncol) > kColsSmemBudget) P.ncol >>= 1;
+  P.rows_smem = fft_rows_smem(precision, nx);
   P.rows_block = std::max(32, std::min(512, nx / 2));
-  P.cols_smem = F * len * P.ncol * cs;
+  P.cols_smem = fft_cols_smem(precision, F, len, P.ncol);
   const int64_t tiles = (d.half_nx + P.ncol - 1) / P.ncol;
   P.n_vb_rows = (int64_t)((F + 1) / 2) * ny;
   P.n_vb_cols = tiles << l1;

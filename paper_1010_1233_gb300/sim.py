@@ -156,6 +156,9 @@ class Sim:
         L.check(L.lib().flb_get_step_config(self._ctx, ctypes.byref(v), ctypes.byref(g)))
         return int(v.value), int(g.value)
 
+    def set_graphs(self, enable=True):
+        L.check(L.lib().flb_set_graphs(self._ctx, int(bool(enable))))
+
     def autotune(self, trials=5):
         """Pick the fastest step-kernel configuration; returns (vec, grid, ms per step)."""
         v, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

@@ -271,3 +271,22 @@ def test_step_configs_and_autotune(with_mlp):
     assert np.array_equal(sim.populations(), before) and sim.step == step
     sim.run(6, 4)
     assert _rel(sim.populations(), ref[0], ref[0] - feq) < 1e-5
+
+
+@pytest.mark.parametrize("every", [0, 4, 5])
+def test_graph_replay_bitwise_equal_direct(every):
+    reps = [W.replica("D2Q9", 32, 16, W.taus_d2q9(0.8), kT=1e-4, u0=(0.05, 0), seed=3, init_mode=1,
+                      fields=(0, 9, 10)),
+            W.replica("D2Q9", 16, 16, W.taus_d2q9(0.7), kT=1e-4, seed=4, stream=1, fields=(0, 9, 10))]
+    a, b = Sim(reps, precision="fp32"), Sim(reps, precision="fp32")
+    b.set_graphs(False)
+    for n in (3, 70, 9):                      # unaligned start, replayed chunks, tail
+        a.run(n, every)
+        b.run(n, every)
+    assert a.step == b.step == 82
+    for r in range(2):
+        assert np.array_equal(a.populations(r), b.populations(r))
+        if every:
+            ca, na = a.correlator(r, 0, 9, with_count=True)
+            cb, nb = b.correlator(r, 0, 9, with_count=True)
+            assert na == nb and np.array_equal(ca, cb)
