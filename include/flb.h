@@ -143,8 +143,11 @@ int flb_get_step(flb_ctx* ctx, uint64_t* step_out);
  * s_a = 1 + o_a(u_x, u_y, rho - rho0) multiplies the Eq. 8 amplitude of moment
  * a = 3..8, o = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with W1 32x3, W2 32x32,
  * W3 6x32 (row-major, bfloat16 bit patterns, 96 + 1024 + 192 values in that
- * order) and FP32 biases b1(32) b2(32) b3(6).  enable = 0 switches it off
- * (s = 1, bit-identical to the plain method).  Copies the weights. */
+ * order) and biases b1(32) b2(32) b3(6) given in FP32.  Evaluated on the tensor
+ * cores (tcgen05) with bfloat16 operands and FP32 accumulation: the inputs, the
+ * biases (weights of a constant-1 input) and the hidden activations are rounded
+ * to bfloat16.  FP32 D2Q9 path only.  enable = 0 switches it off (s = 1,
+ * bit-identical to the plain method).  Copies the weights. */
 int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int enable);
 
 /* Checkpoint: the state is the populations, the step counter and the

@@ -49,17 +49,18 @@ def to_bf16(x):
 def forward(w, X, bf16_operands=False):
     """Forward pass on features X (B, 3); returns the intermediate arrays and s (B, 6).
 
-    bf16_operands=True rounds the inputs and both hidden activations to bfloat16
-    before each matrix product, as a tensor-core inference kernel with bfloat16
-    operands and FP32 accumulation does (weights are expected already rounded).
+    bf16_operands=True rounds the inputs, the biases and both hidden activations to
+    bfloat16 before each matrix product, as a tensor-core inference kernel with
+    bfloat16 operands (the bias as the weight of a constant-1 input) and FP32
+    accumulation does (weights are expected already rounded).
     """
     rnd = to_bf16 if bf16_operands else (lambda a: np.asarray(a, dtype=np.float64))
     X = rnd(X)
-    z1 = X @ w["W1"].T + w["b1"]
+    z1 = X @ w["W1"].T + rnd(w["b1"])
     h1 = rnd(np.maximum(z1, 0.0))
-    z2 = h1 @ w["W2"].T + w["b2"]
+    z2 = h1 @ w["W2"].T + rnd(w["b2"])
     h2 = rnd(np.maximum(z2, 0.0))
-    o = h2 @ w["W3"].T + w["b3"]
+    o = h2 @ w["W3"].T + rnd(w["b3"])
     return dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2, o=o, s=1.0 + o)
 
 

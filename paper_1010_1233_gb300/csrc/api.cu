@@ -169,6 +169,12 @@ static void plan_step(int lattice, int vec, Layout& L) {
   for (size_t r = 0; r < L.desc.size(); ++r) {
     ReplicaDesc& d = L.desc[r];
     d.units_per_row = d.nx / (lattice == FLB_D2Q9 ? vec : 1);
+    // m = ceil(2^(31+l) / upr), l = ceil(log2 upr): floor(u m / 2^(31+l)) = floor(u / upr) for u < 2^31
+    int l = 0;
+    while ((1LL << l) < d.units_per_row) ++l;
+    const uint64_t p2 = 1ULL << (31 + l);
+    d.upr_magic = (uint32_t)((p2 + (uint64_t)d.units_per_row - 1) / (uint64_t)d.units_per_row);
+    d.upr_shift = 31 + l;
     d.n_units = (int64_t)d.units_per_row * d.ny;
     L.vb_step[r] = L.n_vb_step;
     d.block_begin = L.n_vb_step;
@@ -409,6 +415,9 @@ static StepLaunch step_launch(flb_ctx* c) {
   S.grid = (int)std::min<int64_t>(L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
   S.parity = 0;
   S.step = 0;
+  S.status = status_dev(c);
+  S.sms = c->sms;
+  S.desc0 = &L.desc[0];
   return S;
 }
 
@@ -828,6 +837,9 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms
       S.grid = (int)std::min<int64_t>(c->L.n_vb_step, c->step_grid);
       S.parity = (int)(c->step & 1);
       S.step = (uint32_t)c->step;
+      S.status = status_dev(c);
+      S.sms = c->sms;
+      S.desc0 = &c->L.desc[0];
       launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
       cudaEventRecord(e0, c->stream);
       for (int t = 0; t < trials; ++t) launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);

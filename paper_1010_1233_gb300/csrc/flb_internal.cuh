@@ -29,6 +29,8 @@ struct ReplicaDesc {
   int32_t nx, ny, log2nx, log2ny;
   int32_t q;
   int32_t units_per_row;        // nx / VEC of the step launch
+  uint32_t upr_magic;           // row of a unit u < 2^31: (u * upr_magic) >> upr_shift
+  int32_t upr_shift;            //   (Granlund & Montgomery, PLDI'94, round-up multiplier)
   int64_t n_units;              // units_per_row * ny
   int64_t block_begin;          // first virtual block of this replica in the step launch
   uint32_t seed_lo, seed_hi, stream, noise_mask;
@@ -91,7 +93,10 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1
 
 // Box-Muller on a word pair.  FP64: u = (w + 1/2) 2^-32 (exact).  FP32: u = RN(w) 2^-32 + 2^-33,
 // which keeps a relative error <= 2^-24 for every u (small u included, where the log is
-// sensitive); u can round up to 1 only where the normal's radius is ~1e-4 anyway.
+// sensitive); u can round up to 1 only where the normal's radius is ~1e-4 anyway.  The FP32
+// log is the hardware one (__logf: absolute error <= 2^-21.4 on [1/2, 1], 3 ulp below), so
+// r = sqrt(-2 ln u) is within a few ulp for typical u and within ~7e-4 absolute in the worst
+// case (u within 1e-7 of 1, where r itself is below ~5e-4).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
   const double ua = ((double)wa + 0.5) * 0x1p-32;
   const double ub = ((double)wb + 0.5) * 0x1p-32;
@@ -105,7 +110,7 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, 
   const float ua = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
   const float ub = fmaf(__uint2float_rn(wb), 0x1p-32f, 0x1p-33f);
   // r = sqrt(-2 ln ua); ua <= 1 so x >= 0, and x = 0 only when ua rounds to 1
-  const float x = fmaxf(-2.0f * logf(ua), 1e-30f);
+  const float x = fmaxf(-2.0f * __logf(ua), 1e-30f);
   const float r = x * rsqrtf(x);
   // (cos, sin)(2 pi ub) = -(cos, sin)(theta) with theta = 2 pi (ub - 1/2) in [-pi, pi],
   // the range where the hardware sine and cosine are accurate to ~2^-21 absolute
@@ -124,6 +129,9 @@ struct StepLaunch {
   const ReplicaDesc* descs; const int64_t* vb_begin; int n_reps; int64_t n_vblocks;
   char* ws; int parity; uint32_t step; const void* mlp; int grid; int block;
   const uint64_t* step_dev = nullptr;   // non-NULL (graph replay): step = *step_dev + step
+  DevStatus* status = nullptr;          // where a kernel reports a bounded wait that gave up
+  int sms = 0;                          // multiprocessors of the device
+  const ReplicaDesc* desc0 = nullptr;   // host copy of descs[0] (kernel argument of one-replica launches)
 };
 
 // Shared-memory budget of the column transforms and their split rule: one pass of

@@ -132,18 +132,30 @@ def test_d1q3_correlators_match_oracle():
 
 
 # ---------------------------------------------------------------------------- batching, checkpoint
-def test_batched_replicas_bitwise_equal_single():
+def test_batched_replicas_equal_single():
+    # a batched launch runs each replica exactly as a launch of that replica alone; the
+    # one-replica launch is a separate kernel instantiation (description in the constant
+    # bank), which may contract multiply-adds differently, so agreement is to rounding.
+    # Cross-talk between replicas would show as O(1) differences.  Two runs of the same
+    # batch are bitwise identical (no atomics in the step or the correlator sums).
     reps = [W.replica("D2Q9", 32, 32, W.taus_d2q9(0.7 + 0.1 * i), kT=1e-4, u0=(0.02 * i, 0), seed=i,
                       stream=i, init_mode=1, fields=(0, 9, 10)) for i in range(3)]
     reps.append(W.replica("D2Q9", 64, 16, W.taus_d2q9(0.9), kT=1e-4, seed=9, stream=9, fields=(0, 9, 10)))
-    for prec in ("fp64", "fp32"):
+    for prec, tol_f, tol_s in (("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-4)):
         batch = Sim(reps, precision=prec)
         batch.run(25, 5)
+        again = Sim(reps, precision=prec)
+        again.run(25, 5)
         for i, p in enumerate(reps):
+            assert np.array_equal(batch.populations(i), again.populations(i))
+            assert np.array_equal(batch.correlator(i, 0, 9), again.correlator(i, 0, 9))
             one = Sim(p, precision=prec)
             one.run(25, 5)
-            assert np.array_equal(batch.populations(i), one.populations())
-            assert np.array_equal(batch.correlator(i, 0, 9), one.correlator(0, 0, 9))
+            feq = lb.uniform_state(lb.Params(**p))
+            ref = one.populations()
+            assert _rel(batch.populations(i), ref, ref - feq) < tol_f, (prec, i)
+            s1 = one.correlator(0, 0, 9)
+            assert np.abs(batch.correlator(i, 0, 9) - s1).max() < tol_s * np.abs(s1).max(), (prec, i)
 
 
 def test_checkpoint_resume_bitwise():
