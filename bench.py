@@ -30,6 +30,11 @@ sys.path.insert(0, ROOT)
 SAMPLE_EVERY = 20
 ALG_BYTES_PER_SITE = 72          # FP32 deviation storage: 9 reads + 9 writes of 4 B
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per site of one launch of the dominant kernel in the tuned
+# launch configuration (direct tensor-core step kernel, vec 2): ncu capture of
+# k_step_d2q9_tc<2,0,1> on the 4096^2 case (profiles/k_step_d2q9_tc_fp32_mlp_4096.md),
+# scaled by the site count; None for any other configuration.
+TRAFFIC_PER_SITE = {(2, 0): (604066560 + 559978240) / 4096**2}
 
 
 def parse():
@@ -60,6 +65,27 @@ def job_throughput(sites_per_rank, steps, seconds_local, world, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     tmax = float(t.item())
     return world * sites_per_rank * steps / tmax / 1e6, tmax
+
+
+def expected_launches(start, K, every, sample_kernels, graph_max=4096):
+    """Kernels flb_run issues for K steps from step `start` (sampling every `every` steps):
+    one step kernel per step, `sample_kernels` FFT kernels per sample, and with CUDA graphs
+    (chunks of `every` steps once aligned, K >= 2 every) one step-counter kernel per
+    chunk plus one that sets the counter before the first."""
+    n = 0
+    i, t = 0, start
+    if K >= 2 * every and every <= graph_max:
+        while i < K and t % every:
+            n += 1 + (sample_kernels if t % every == 0 else 0)
+            i, t = i + 1, t + 1
+        chunks = (K - i) // every
+        if chunks:
+            n += 1 + chunks * (every + sample_kernels + 1)
+            i, t = i + chunks * every, t + chunks * every
+    while i < K:
+        n += 1 + (sample_kernels if t % every == 0 else 0)
+        i, t = i + 1, t + 1
+    return n
 
 
 def workload(n):
@@ -222,9 +248,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
     ms_max = t_max * 1e3
-    n_samples = sum(1 for s in range(Wm, Wm + K) if s % SAMPLE_EVERY == 0)
-    four_step = 1 if p["ny"] > 2048 else 0
-    launches = K + n_samples * (2 + four_step)
+    launches = expected_launches(Wm, K, SAMPLE_EVERY, sample_kernels=3 if p["ny"] > 2048 else 2)
 
     # dominant kernel alone: plain (non-sampling) steps back to back, same launch configuration
     Kd = max(20, min(K, 100))
@@ -236,6 +260,8 @@ def run_ours(args):
     step_ms = d0.elapsed_time(d1) / Kd
     hbm, peak_kind = peaks()
     achieved = ALG_BYTES_PER_SITE * V / (step_ms * 1e-3) / 1e9
+    tps = TRAFFIC_PER_SITE.get((tuned[0], tuned[2]))
+    traffic = tps * V if tps else None
 
     e2e = None
     if not args.no_e2e:
@@ -284,10 +310,10 @@ def run_ours(args):
                        "fields": ["rho", "u_x", "u_y"], "parallelism": f"replica x{world}",
                        "l2": "inputs larger than L2 (%.1f GB state), no flush" % (2 * 9 * 4 * V / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_step_d2q9 (fused pull-stream/collide/noise/network)",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_step_d2q9_tc (fused pull-stream/collide/noise, network on tcgen05)",
                          "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms,
-                         "launch": {"vec": tuned[0], "grid": tuned[1], "block": 256}},
+                         "launch": {"vec": tuned[0], "grid": tuned[1], "staged": tuned[2], "block": 256}},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,

@@ -155,19 +155,24 @@ int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int e
 int flb_save(flb_ctx* ctx, void* host_buf, size_t* bytes_inout);
 int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 
-/* Launch configuration of the step kernel: vec consecutive sites per thread
- * (1, 2 or 4; > 1 only on the FP32 D2Q9 path, every nx a multiple of vec) and
- * the number of persistent blocks (0 = 16 per SM).  Results do not depend on it.
+/* Launch configuration of the step kernel.  staged = 0: direct kernels, vec
+ * consecutive sites per thread (1, 2 or 4; > 1 only on the FP32 D2Q9 path,
+ * every nx a multiple of vec), grid_blocks persistent blocks (0 = 16 per SM).
+ * staged = 1 (FP32 D2Q9 path, every nx a multiple of 4): row tiles of 256 vec
+ * sites staged through shared memory by TMA bulk copies, one persistent block
+ * per resident slot (grid_blocks caps it).  Results agree to rounding across
+ * configurations (kernels may contract multiply-adds differently).
  * Synchronises. */
-int flb_set_step_config(flb_ctx* ctx, int vec, int grid_blocks);
-int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks);
+int flb_set_step_config(flb_ctx* ctx, int vec, int grid_blocks, int staged);
+int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks, int* staged);
 
 /* Autotuner: times `trials` launches of the step kernel (current network
- * setting, no sampling) for every valid vec and grid size in {2,4,8,16} x SMs
- * and all-blocks, keeps the fastest and reports it (ms_out: time per launch).
- * The timing launches recompute the next step from the current state without
- * advancing it, so the simulation is unchanged.  Synchronises. */
-int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, double* ms_out);
+ * setting, no sampling) for every valid configuration: direct kernels with
+ * every vec and grid size in {2,4,8,16} x SMs and all-blocks, and the staged
+ * kernel with every vec; keeps the fastest and reports it (ms_out: time per
+ * launch).  The timing launches recompute the next step from the current state
+ * without advancing it, so the simulation is unchanged.  Synchronises. */
+int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out);
 
 /* CUDA graphs (default on): flb_run replays a captured graph for every aligned
  * chunk of sample_every steps (32 steps without sampling), which removes the

@@ -51,9 +51,9 @@ _SIGS = {
     "flb_set_mlp": (c_int, [c_void_p, POINTER(c_uint16), POINTER(c_float), c_int]),
     "flb_save": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
     "flb_load": (c_int, [c_void_p, c_void_p, c_size_t]),
-    "flb_set_step_config": (c_int, [c_void_p, c_int, c_int]),
-    "flb_get_step_config": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
-    "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
+    "flb_set_step_config": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "flb_get_step_config": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_set_graphs": (c_int, [c_void_p, c_int]),
     "flb_destroy": (None, [c_void_p]),
     "flb_last_error": (ctypes.c_char_p, []),

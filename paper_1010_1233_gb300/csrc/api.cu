@@ -14,6 +14,7 @@ namespace flb {
 
 // launchers (lb_step.cu, spectra.cu)
 void launch_step(int lattice, int precision, int vec, const StepLaunch& L, bool sample, bool mlp, cudaStream_t st);
+void launch_step_bulk(int vec, const StepLaunch& L, bool sample, bool mlp, cudaStream_t st);
 void launch_init(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
                  double* sums, double* partial, int64_t V, cudaStream_t st);
 void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity,
@@ -71,6 +72,7 @@ struct Layout {
   int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0, n_vb_cols_a = 0;
   std::vector<int64_t> vb_step, vb_rows, vb_cols, vb_cols_a;
   int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
+  int staged = 0;             // 1: the step kernel of lb_step_bulk.cu (tiles of 256 vec sites)
   bool any_fields = false;
 };
 
@@ -160,15 +162,18 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   for (int i = 0; i < kNumCoef; ++i) d.fco[i] = (float)d.dco[i];
 }
 
-// Step-launch tables for a vector width: VEC consecutive sites per thread, one
-// virtual block of kStepBlock threads never spans two replicas.
-static void plan_step(int lattice, int vec, Layout& L) {
+// Step-launch tables.  Direct kernels: a unit is VEC consecutive sites (one thread),
+// a virtual block is kStepBlock units of one replica.  Staged kernel: a unit is a row
+// tile of up to 256 VEC sites, and a virtual block is one tile.
+static void plan_step(int lattice, int vec, int staged, Layout& L) {
   L.vec = vec;
+  L.staged = staged;
   L.n_vb_step = 0;
   L.vb_step.resize(L.desc.size());
   for (size_t r = 0; r < L.desc.size(); ++r) {
     ReplicaDesc& d = L.desc[r];
-    d.units_per_row = d.nx / (lattice == FLB_D2Q9 ? vec : 1);
+    const int tile = kStepBlock * vec;
+    d.units_per_row = staged ? (d.nx + tile - 1) / tile : d.nx / (lattice == FLB_D2Q9 ? vec : 1);
     // m = ceil(2^(31+l) / upr), l = ceil(log2 upr): floor(u m / 2^(31+l)) = floor(u / upr) for u < 2^31
     int l = 0;
     while ((1LL << l) < d.units_per_row) ++l;
@@ -178,7 +183,7 @@ static void plan_step(int lattice, int vec, Layout& L) {
     d.n_units = (int64_t)d.units_per_row * d.ny;
     L.vb_step[r] = L.n_vb_step;
     d.block_begin = L.n_vb_step;
-    L.n_vb_step += (d.n_units + kStepBlock - 1) / kStepBlock;
+    L.n_vb_step += staged ? d.n_units : (d.n_units + kStepBlock - 1) / kStepBlock;
   }
 }
 
@@ -231,7 +236,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
   }
-  plan_step(lat, L.vec, L);
+  plan_step(lat, L.vec, 0, L);
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
     L.vb_rows[r] = L.n_vb_rows;
@@ -387,7 +392,8 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
 // offset from the device step counter (graph capture); otherwise the absolute step.
 static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
   const Layout& L = c->L;
-  launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, st);
+  if (L.staged) launch_step_bulk(L.vec, S, sample, c->mlp_on, st);
+  else launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, st);
   if (sample) {
     const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
     const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
@@ -775,18 +781,27 @@ int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
   return FLB_OK;
 }
 
-int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks) {
+static bool staged_ok(const flb_ctx* c) {
+  if (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9) return false;
+  for (int r = 0; r < c->n; ++r)
+    if (c->L.desc[r].nx % 4) return false;
+  return true;
+}
+
+int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks, int staged) {
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   if (vec != 1 && vec != 2 && vec != 4) return set_error(FLB_EINVAL, "vec must be 1, 2 or 4");
+  if (staged != 0 && staged != 1) return set_error(FLB_EINVAL, "staged must be 0 or 1");
+  if (staged && !staged_ok(c)) return set_error(FLB_EINVAL, "the staged kernel needs the FP32 D2Q9 path, every nx a multiple of 4");
   if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9))
     return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9 path");
-  for (int r = 0; r < c->n; ++r)
+  for (int r = 0; r < c->n && !staged; ++r)
     if (c->L.desc[r].nx % vec) return set_error(FLB_EINVAL, "replica %d: nx not a multiple of vec = %d", r, vec);
   if (grid_blocks < 0) return set_error(FLB_EINVAL, "grid_blocks must be >= 0");
   int rc = cuda_check(cudaStreamSynchronize(c->stream), "step config");
   if (rc) return rc;
   drop_graphs(c);
-  plan_step(c->lattice, vec, c->L);
+  plan_step(c->lattice, vec, staged, c->L);
   rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
                              cudaMemcpyHostToDevice), "copy descriptors");
   if (!rc) rc = cuda_check(cudaMemcpy(c->ws + c->L.off_vb_step, c->L.vb_step.data(), 8 * (size_t)c->n,
@@ -795,14 +810,15 @@ int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks) {
   return rc;
 }
 
-int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks) {
-  if (!c || !vec || !grid_blocks) return set_error(FLB_EINVAL, "NULL argument");
+int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks, int* staged) {
+  if (!c || !vec || !grid_blocks || !staged) return set_error(FLB_EINVAL, "NULL argument");
   *vec = c->L.vec;
+  *staged = c->L.staged;
   *grid_blocks = (int)std::min<int64_t>(c->L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
   return FLB_OK;
 }
 
-int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms_out) {
+int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out) {
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   if (trials < 1) return set_error(FLB_EINVAL, "trials must be >= 1");
   cudaEvent_t e0, e1;
@@ -811,18 +827,20 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms
   rc = cuda_check(cudaEventCreate(&e1), "event");
   if (rc) { cudaEventDestroy(e0); return rc; }
   const int vecs[3] = {1, 2, 4};
-  int best_vec = c->L.vec, best_grid = c->step_grid;
+  int best_vec = c->L.vec, best_grid = c->step_grid, best_staged = c->L.staged;
   float best = 1e30f;
-  for (int vi = 0; vi < 3 && !rc; ++vi) {
-    const int vec = vecs[vi];
+  for (int cfg = 0; cfg < 6 && !rc; ++cfg) {
+    const int vec = vecs[cfg % 3], staged = cfg / 3;
     if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9)) continue;
+    if (staged && !staged_ok(c)) continue;
     bool ok = true;
-    for (int r = 0; r < c->n; ++r) ok = ok && c->L.desc[r].nx % vec == 0;
+    for (int r = 0; r < c->n && !staged; ++r) ok = ok && c->L.desc[r].nx % vec == 0;
     if (!ok) continue;
+    // the staged kernel is persistent (its launcher caps the grid at the resident blocks)
     const int mults[5] = {2, 4, 8, 16, 0};
-    for (int mi = 0; mi < 5 && !rc; ++mi) {
+    for (int mi = staged ? 4 : 0; mi < 5 && !rc; ++mi) {
       const int grid = mults[mi] ? mults[mi] * c->sms : 0;
-      rc = flb_set_step_config(c, vec, grid ? grid : INT32_MAX);
+      rc = flb_set_step_config(c, vec, grid ? grid : INT32_MAX, staged);
       if (rc) break;
       // dry runs: the same step (same input buffer, same step index) launched
       // repeatedly; it only rewrites the buffer the next real step overwrites.
@@ -840,25 +858,30 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, double* ms
       S.status = status_dev(c);
       S.sms = c->sms;
       S.desc0 = &c->L.desc[0];
-      launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
+      auto launch = [&] {
+        if (staged) launch_step_bulk(vec, S, false, c->mlp_on, c->stream);
+        else launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
+      };
+      launch();
       cudaEventRecord(e0, c->stream);
-      for (int t = 0; t < trials; ++t) launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
+      for (int t = 0; t < trials; ++t) launch();
       cudaEventRecord(e1, c->stream);
       rc = cuda_check(cudaEventSynchronize(e1), "autotune");
       if (rc) break;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= trials;
-      if (ms < best) { best = ms; best_vec = vec; best_grid = S.grid; }
+      if (ms < best) { best = ms; best_vec = vec; best_grid = S.grid; best_staged = staged; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  rc = flb_set_step_config(c, best_vec, best_grid);
+  rc = flb_set_step_config(c, best_vec, best_grid, best_staged);
   if (rc) return rc;
   if (vec_out) *vec_out = best_vec;
   if (grid_out) *grid_out = best_grid;
+  if (staged_out) *staged_out = best_staged;
   if (ms_out) *ms_out = best;
   return FLB_OK;
 }

@@ -154,23 +154,37 @@ __device__ __forceinline__ void macro_d2q9(const R (&g)[9], R rho0, R& sum, R& u
   uy = jy * irho;
 }
 
-// The six unit normals of a site (Philox counter: site, step, call 0/1, stream).
+// The six unit normals of a site (Philox counter: site, step, call 0/1, stream), in two
+// parts so that a kernel can spread them over independent work: the counter-based words,
+// then the Box-Muller transform of three word pairs.
+__device__ __forceinline__ void philox_words_d2q9(const ReplicaDesc& d, uint32_t site, uint32_t step, uint4& w0,
+                                                  uint4& w1) {
+  w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
+  w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
+}
+
 template <typename R>
-__device__ __forceinline__ void normals_d2q9(const ReplicaDesc& d, uint32_t site, uint32_t step, R (&n)[6]) {
-  const uint4 w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
-  const uint4 w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
+__device__ __forceinline__ void normals_from_words(const uint4& w0, const uint4& w1, R (&n)[6]) {
   box_muller(w0.x, w0.y, n[0], n[1]);
   box_muller(w0.z, w0.w, n[2], n[3]);
   box_muller(w1.x, w1.y, n[4], n[5]);
 }
 
-// Collision of one site in place (Eqs. 5, 8, 10): relax the non-conserved moments
-// M^3..M^8 of Eq. 9 at rates 1/tau^a, add xi^a = s_a amp_a N^a, and add
-// sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a.  fld receives the sampled
-// fields of the pre-collision state when SAMPLE.
+template <typename R>
+__device__ __forceinline__ void normals_d2q9(const ReplicaDesc& d, uint32_t site, uint32_t step, R (&n)[6]) {
+  uint4 w0, w1;
+  philox_words_d2q9(d, site, step, w0, w1);
+  normals_from_words<R>(w0, w1, n);
+}
+
+// Collision of one site (Eqs. 5, 8, 10), in two parts.  collide_relax: the non-conserved
+// moments M^3..M^8 of Eq. 9, relaxed towards the equilibrium moments of Eq. 10 at rates
+// 1/tau^a: D[a - 3] = Delta M^a (and the sampled fields of the pre-collision state when
+// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a and the back transform
+// sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a, in place.
 template <typename R, bool DEV, bool SAMPLE>
-__device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R sum, R ux, R uy, bool noisy,
-                                             const R (&n)[6], const R (&sc)[6], R (&fld)[kMaxFields]) {
+__device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)[9], R sum, R ux, R uy, R (&D)[6],
+                                              R (&fld)[kMaxFields]) {
   const R S3 = (R)1.7320508075688772935, S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
   const R g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4], g5 = g[5], g6 = g[6], g7 = g[7], g8 = g[8];
   const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
@@ -196,9 +210,19 @@ __device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R 
     fld[10] = uy - coef<R>(d, kCoU0y);
   }
   // relaxation (Eq. 5)
-  R D3 = (E3 - M3) * coef<R>(d, kCoInvTau + 3), D4 = (E4 - M4) * coef<R>(d, kCoInvTau + 4);
-  R D5 = (E5 - M5) * coef<R>(d, kCoInvTau + 5), D6 = -M6 * coef<R>(d, kCoInvTau + 6);
-  R D7 = -M7 * coef<R>(d, kCoInvTau + 7), D8 = -M8 * coef<R>(d, kCoInvTau + 8);
+  D[0] = (E3 - M3) * coef<R>(d, kCoInvTau + 3);
+  D[1] = (E4 - M4) * coef<R>(d, kCoInvTau + 4);
+  D[2] = (E5 - M5) * coef<R>(d, kCoInvTau + 5);
+  D[3] = -M6 * coef<R>(d, kCoInvTau + 6);
+  D[4] = -M7 * coef<R>(d, kCoInvTau + 7);
+  D[5] = -M8 * coef<R>(d, kCoInvTau + 8);
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], bool noisy, const R (&n)[6],
+                                              const R (&sc)[6], const R (&Drel)[6]) {
+  const R S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
+  R D3 = Drel[0], D4 = Drel[1], D5 = Drel[2], D6 = Drel[3], D7 = Drel[4], D8 = Drel[5];
   if (noisy) {                                   // Eq. 8, scaled per moment by s
     D3 += sc[0] * coef<R>(d, kCoAmp + 3) * n[0];
     D4 += sc[1] * coef<R>(d, kCoAmp + 4) * n[1];
@@ -215,15 +239,23 @@ __device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R 
   const R p6 = S32 * D6, p7 = S32 * D7;
   const R dcom = (R)2 * (D5 + D8);                  // common to the diagonal populations
   const R q6 = S6 * D6, q7 = S6 * D7, q4 = (R)3 * D4;
-  g[0] = g0 + c0;
-  g[1] = g1 + w1 * (ax5 + hx - p6);
-  g[3] = g3 + w1 * (ax5 + hx + p6);
-  g[2] = g2 + w1 * (ax5 - hx - p7);
-  g[4] = g4 + w1 * (ax5 - hx + p7);
-  g[5] = g5 + w5 * (dcom + q4 + q6 + q7);
-  g[6] = g6 + w5 * (dcom - q4 - q6 + q7);
-  g[7] = g7 + w5 * (dcom + q4 - q6 - q7);
-  g[8] = g8 + w5 * (dcom - q4 + q6 - q7);
+  g[0] = g[0] + c0;
+  g[1] = g[1] + w1 * (ax5 + hx - p6);
+  g[3] = g[3] + w1 * (ax5 + hx + p6);
+  g[2] = g[2] + w1 * (ax5 - hx - p7);
+  g[4] = g[4] + w1 * (ax5 - hx + p7);
+  g[5] = g[5] + w5 * (dcom + q4 + q6 + q7);
+  g[6] = g[6] + w5 * (dcom - q4 - q6 + q7);
+  g[7] = g[7] + w5 * (dcom + q4 - q6 - q7);
+  g[8] = g[8] + w5 * (dcom - q4 + q6 - q7);
+}
+
+template <typename R, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R sum, R ux, R uy, bool noisy,
+                                             const R (&n)[6], const R (&sc)[6], R (&fld)[kMaxFields]) {
+  R D[6];
+  collide_relax<R, DEV, SAMPLE>(d, g, sum, ux, uy, D, fld);
+  collide_apply<R>(d, g, noisy, n, sc, D);
 }
 
 // Store the post-collision populations (and the sampled fields) of a thread's sites.

@@ -86,7 +86,7 @@ def sweep(steps=100_000, warmup=10_000, every=10):
     wl = W.sweep64()
     reps = wl["replicas"]
     sim = Sim(reps, precision="fp32")
-    vec, grid, _ = sim.autotune(3)
+    vec, grid, staged, _ = sim.autotune(3)
     _timed(sim, warmup, 0)
     sim.reset_stats()
     t = _timed(sim, steps, every)
@@ -99,7 +99,7 @@ def sweep(steps=100_000, warmup=10_000, every=10):
         rows.append(dict(r=r, n=p["nx"], u0=p["u0"][0], tau_s=p["tau"][3], max_err=mx, mean_err=mean,
                          finite=finite))
     return dict(workload="sweep64", steps=steps, sample_every=every, sites=V, wall_s=t, mlups=V * steps / t / 1e6,
-                launch=dict(vec=vec, grid=grid), replicas=rows)
+                launch=dict(vec=vec, grid=grid, staged=staged), replicas=rows)
 
 
 def learned_eval(quick=False):

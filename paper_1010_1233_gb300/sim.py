@@ -148,22 +148,24 @@ class Sim:
                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
 
     # -- launch configuration ---------------------------------------------
-    def set_step_config(self, vec, grid_blocks=0):
-        L.check(L.lib().flb_set_step_config(self._ctx, int(vec), int(grid_blocks)))
+    def set_step_config(self, vec, grid_blocks=0, staged=0):
+        L.check(L.lib().flb_set_step_config(self._ctx, int(vec), int(grid_blocks), int(staged)))
 
     def step_config(self):
-        v, g = ctypes.c_int(), ctypes.c_int()
-        L.check(L.lib().flb_get_step_config(self._ctx, ctypes.byref(v), ctypes.byref(g)))
-        return int(v.value), int(g.value)
+        """(vec, grid blocks, staged) of the step kernel."""
+        v, g, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(L.lib().flb_get_step_config(self._ctx, ctypes.byref(v), ctypes.byref(g), ctypes.byref(s)))
+        return int(v.value), int(g.value), int(s.value)
 
     def set_graphs(self, enable=True):
         L.check(L.lib().flb_set_graphs(self._ctx, int(bool(enable))))
 
     def autotune(self, trials=5):
-        """Pick the fastest step-kernel configuration; returns (vec, grid, ms per step)."""
-        v, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        L.check(L.lib().flb_autotune(self._ctx, int(trials), ctypes.byref(v), ctypes.byref(g), ctypes.byref(ms)))
-        return int(v.value), int(g.value), float(ms.value)
+        """Pick the fastest step-kernel configuration; returns (vec, grid, staged, ms per step)."""
+        v, g, s, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        L.check(L.lib().flb_autotune(self._ctx, int(trials), ctypes.byref(v), ctypes.byref(g), ctypes.byref(s),
+                                     ctypes.byref(ms)))
+        return int(v.value), int(g.value), int(s.value), float(ms.value)
 
     # -- checkpoint -------------------------------------------------------
     def save(self):

@@ -206,6 +206,41 @@ def test_mlp_scaled_noise_matches_oracle():
     assert _rel(plain.f, ref.f, ref.f - feq) > 20 * err
 
 
+STAGED = [(260, 6, 1, False), (264, 5, 2, True), (512, 4, 1, True), (64, 8, 4, False), (1032, 3, 4, True),
+          (16, 8, 2, True), (1024, 2, 4, False)]
+
+
+@pytest.mark.parametrize("nx,ny,vec,with_mlp", STAGED, ids=[f"{c[0]}x{c[1]}-v{c[2]}-{'mlp' if c[3] else 'plain'}"
+                                                           for c in STAGED])
+def test_staged_kernel_matches_oracle(nx, ny, vec, with_mlp):
+    # row tiles of 256 vec sites through shared memory: full tiles, ragged last tiles
+    # (260 = 256 + 4, 1032 = 1024 + 8), rows shorter than one warpgroup's half (16, 64),
+    # and the periodic halos at both row ends; on power-of-two lattices also the sampled
+    # fields and correlators (every 3 steps)
+    pow2 = (nx & (nx - 1)) == 0 and (ny & (ny - 1)) == 0
+    fields = (0, 9, 10) if pow2 else ()
+    p = W.replica("D2Q9", nx, ny, W.taus_d2q9(0.8, 0.7, 1.1), kT=1e-4, u0=(0.12, -0.04), seed=8,
+                  init_mode=1, fields=fields)
+    sim = Sim(p, precision="fp32")
+    ref = _oracle(p)
+    tol = FP32_TOL
+    if with_mlp:
+        wts = W.mlp_weights(3, out_scale=0.5)
+        sim.set_mlp(wts)
+        ref.p.mlp = {k: (omlp.to_bf16(v) if k.startswith("W") else v.astype(np.float64)) for k, v in wts.items()}
+        ref.p.mlp_bf16 = True
+        tol = 1e-3          # bfloat16 rounding ties, see test_mlp_scaled_noise_matches_oracle
+    sim.set_step_config(vec, 0, 1)
+    assert sim.step_config()[2] == 1
+    sim.run(12, 3 if pow2 else 0)
+    ref.run(12, 3 if pow2 else 0)
+    feq = lb.uniform_state(ref.p)
+    assert _rel(sim.populations(), ref.f, ref.f - feq) < tol
+    for a, b in spectra.pairs(fields):
+        g, o = sim.correlator(0, a, b), ref.acc.correlator(a, b)
+        assert np.abs(g - o).max() < 5 * tol * max(1.0, np.abs(o).max()), (a, b)
+
+
 def test_mlp_zero_output_is_plain_method_bitwise():
     wts = W.mlp_weights(4)
     wts["W3"][:] = 0
@@ -258,28 +293,29 @@ def test_step_configs_and_autotune(with_mlp):
                   fields=(0, 9, 10))
     wts = W.mlp_weights(5, out_scale=0.3)
     ref = None
-    for vec, grid in [(4, 0), (1, 0), (2, 3), (4, 1), (1, 100000)]:
+    for vec, grid, staged in [(4, 0, 0), (1, 0, 0), (2, 3, 0), (4, 1, 0), (1, 100000, 0),
+                              (1, 0, 1), (2, 0, 1), (4, 0, 1), (2, 1, 1)]:
         sim = Sim(p, precision="fp32")
         if with_mlp:
             sim.set_mlp(wts)
-        sim.set_step_config(vec, grid)
-        assert sim.step_config()[0] == vec
+        sim.set_step_config(vec, grid, staged)
+        assert sim.step_config()[0] == vec and sim.step_config()[2] == staged
         sim.run(12, 4)
         out = (sim.populations(), sim.correlator(0, 0, 9))
         if ref is None:
             ref = out
             feq = lb.uniform_state(lb.Params(**p))
         else:
-            assert _rel(out[0], ref[0], ref[0] - feq) < 1e-5, (vec, grid)
-            assert np.abs(out[1] - ref[1]).max() < 1e-4 * np.abs(ref[1]).max(), (vec, grid)
+            assert _rel(out[0], ref[0], ref[0] - feq) < 1e-5, (vec, grid, staged)
+            assert np.abs(out[1] - ref[1]).max() < 1e-4 * np.abs(ref[1]).max(), (vec, grid, staged)
     # the autotuner's timing launches leave the state and the step counter unchanged
     sim = Sim(p, precision="fp32")
     if with_mlp:
         sim.set_mlp(wts)
     sim.run(6, 4)
     before, step = sim.populations(), sim.step
-    vec, grid, ms = sim.autotune(trials=3)
-    assert vec in (1, 2, 4) and grid > 0 and ms > 0
+    vec, grid, staged, ms = sim.autotune(trials=3)
+    assert vec in (1, 2, 4) and grid > 0 and staged in (0, 1) and ms > 0
     assert np.array_equal(sim.populations(), before) and sim.step == step
     sim.run(6, 4)
     assert _rel(sim.populations(), ref[0], ref[0] - feq) < 1e-5
