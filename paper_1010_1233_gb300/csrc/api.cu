@@ -206,20 +206,32 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
     fill_desc(precision, reps[r], d);
-    const int64_t V = (int64_t)d.nx * d.ny;
-    d.off_pop[0] = off; off = align256(off + L.q * V * rs);
-    d.off_pop[1] = off; off = align256(off + L.q * V * rs);
     if (d.n_fields) {
       L.any_fields = true;
       maxF = std::max(maxF, (int)d.n_fields);
       maxlen = std::max(maxlen, std::max(1 << d.log2n1, d.ny >> d.log2n1));
       maxnx = std::max(maxnx, d.nx);
+    }
+  }
+  // column tile width of the sampling passes (it fixes the blocked layout of the pair sums)
+  if (L.any_fields) {
+    L.ncol = kColsMax;
+    while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
+  }
+  for (int r = 0; r < n; ++r) {
+    ReplicaDesc& d = L.desc[r];
+    const int64_t V = (int64_t)d.nx * d.ny;
+    d.off_pop[0] = off; off = align256(off + L.q * V * rs);
+    d.off_pop[1] = off; off = align256(off + L.q * V * rs);
+    if (d.n_fields) {
       d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs);
       d.off_spec = off; off = align256(off + (int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
+      d.acc_ncol = L.ncol;
+      const int64_t padded_kx = (d.half_nx + L.ncol - 1) / L.ncol * L.ncol;
       for (int pr = 0; pr < d.n_pairs; ++pr) {
         d.pair_off[pr] = off;
         const int64_t el = d.pair_a[pr] == d.pair_b[pr] ? 8 : 16;
-        off = align256(off + (int64_t)d.ny * d.half_nx * el);
+        off = align256(off + (int64_t)d.ny * padded_kx * el);
       }
       d.off_mean0 = off; off = align256(off + 8 * (int64_t)d.n_fields);
       d.off_tw_x = off; off = align256(off + (int64_t)(d.nx / 2) * 2 * rs + 16);
@@ -229,9 +241,6 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   // virtual-block prefixes of the three launches
   L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
   if (L.any_fields) {
-    const int cs = precision == FLB_FP64 ? 16 : 8;
-    L.ncol = 16;
-    while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
     L.rows_smem = fft_rows_smem(precision, maxnx);
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
@@ -550,7 +559,9 @@ int flb_get_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out
   for (int k = 0; k < d.n_pairs; ++k) if (d.pair_a[k] == lo && d.pair_b[k] == hi) pr = k;
   const int nx = d.nx, ny = d.ny, hn = d.half_nx;
   const bool autoc = lo == hi;
-  std::vector<double> acc((size_t)ny * hn * (autoc ? 1 : 2));
+  const int bc = d.acc_ncol;                              // blocked layout (see ReplicaDesc)
+  const int n1 = 1 << d.log2n1, n2 = ny >> d.log2n1, tiles = (hn + bc - 1) / bc;
+  std::vector<double> acc((size_t)ny * tiles * bc * (autoc ? 1 : 2));
   rc = cuda_check(cudaMemcpy(acc.data(), c->ws + d.pair_off[pr], acc.size() * 8, cudaMemcpyDeviceToHost), "read sums");
   if (rc) return rc;
   std::vector<double> m0(d.n_fields);
@@ -567,7 +578,7 @@ int flb_get_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out
       int hy = ky, hx = kx;
       bool conj = false;
       if (kx > nx / 2) { hx = nx - kx; hy = (ny - ky) % ny; conj = true; }
-      const size_t idx = (size_t)hy * hn + hx;
+      const size_t idx = ((size_t)((hy & (n1 - 1)) * tiles + hx / bc) * n2 + (hy >> d.log2n1)) * bc + hx % bc;
       if (autoc) { re = acc[idx]; im = 0.0; }
       else { re = acc[2 * idx]; im = acc[2 * idx + 1]; }
       if (conj) im = -im;

@@ -51,6 +51,9 @@ struct ReplicaDesc {
   int32_t half_nx;                  // nx / 2 + 1
   int32_t wpitch;                   // pitch (complex elements) of spec rows
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
+  int32_t acc_ncol;                 // pair-sum layout: 0 = [ky][kx]; c > 0 = blocked in the order
+                                    // the column pass produces the points: [k1][kx / c][k2][kx % c]
+                                    // (ky = k1 + N1 k2; kx padded to a multiple of c)
   // the per-replica coefficients in the arithmetic type of the path (host-filled),
   // so the FP32 kernels never convert from FP64: [kCoRho0], [kCoU0x], [kCoU0y],
   // [kCoInvTau + a], [kCoAmp + a], [kCoMref + field]
@@ -139,6 +142,10 @@ struct StepLaunch {
 // N1 = 2^floor(log2(ny)/2) (four-step).
 constexpr int kColsSmemBudget = 200 * 1024;
 constexpr int kColsBlock = 256;
+#ifndef FLB_COLS_MAX
+#define FLB_COLS_MAX 16
+#endif
+constexpr int kColsMax = FLB_COLS_MAX;   // widest column tile (halved until it fits the budget)
 inline int column_split(int precision, int F, int ny) {
   const int cs = precision == FLB_FP64 ? 16 : 8;
   if ((int64_t)F * (ny + 1) * 4 * cs <= kColsSmemBudget) return 0;

@@ -22,35 +22,90 @@ template <typename R> __device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
   C<R> r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
 
+// w * exp(-2 pi i u / 2^(st+1)) for st <= 2 (u < 2^st): multiplication by an eighth
+// root of unity (exact for 1 and -i)
+template <typename R>
+__device__ __forceinline__ C<R> rot8(C<R> w, int st, int u) {
+  const int e = u << (2 - st);                        // exponent in units of -2 pi i / 8
+  C<R> r = w;
+  if (e == 2) { r.x = w.y; r.y = -w.x; }              // * (-i)
+  else if (e == 1 || e == 3) {
+    const R h = (R)0.70710678118654752440;            // * (1 - i)/sqrt2, * (-1 - i)/sqrt2
+    if (e == 1) { r.x = h * (w.x + w.y); r.y = h * (w.y - w.x); }
+    else { r.x = h * (w.y - w.x); r.y = -h * (w.x + w.y); }
+  }
+  return r;
+}
+
+// The butterflies of RS consecutive radix-2 decimation-in-time stages s .. s + RS - 1
+// on a group of 2^RS elements held in registers: v[t] is element i0 + t 2^s of the
+// sequence, where i0 has bits s .. s+RS-1 clear and low = i0 mod 2^s.  Stage S = s + st
+// pairs t with t + 2^st and multiplies by exp(-2 pi i pos / 2^(S+1)),
+// pos = low + (t mod 2^st) 2^s, i.e. the base twiddle exp(-2 pi i low / 2^(S+1)) (one
+// table read per stage) times an eighth root of unity.
+template <typename R, int RS>
+__device__ __forceinline__ void dit_group(C<R> (&v)[1 << RS], int logn, int s, int low,
+                                          const C<R>* __restrict__ tw, int tw_stride) {
+#pragma unroll
+  for (int st = 0; st < RS; ++st) {
+    const C<R> base = __ldg(&tw[(low << (logn - 1 - s - st)) * tw_stride]);
+#pragma unroll
+    for (int t = 0; t < (1 << RS); ++t) {
+      if (t & (1 << st)) continue;
+      const C<R> w = rot8<R>(base, st, t & ((1 << st) - 1));
+      const C<R> a = v[t];
+      const C<R> tt = cmul<R>(v[t + (1 << st)], w);
+      v[t].x = a.x + tt.x; v[t].y = a.y + tt.y;
+      v[t + (1 << st)].x = a.x - tt.x; v[t + (1 << st)].y = a.y - tt.y;
+    }
+  }
+}
+
+// RS consecutive stages in one pass through shared memory: each thread takes groups of
+// 2^RS elements closed under those stages, keeps them in registers through the RS stages
+// and writes them back (one barrier per RS stages).
+template <typename R, int RS>
+__device__ __forceinline__ void dit_pass(C<R>* data, int logn, int n_fft, int seq_stride,
+                                         const C<R>* __restrict__ tw, int tw_stride, int pad_shift, int s) {
+  constexpr int G = 1 << RS;
+  const int lg = logn - RS;                          // log2 of the groups per sequence
+  const int total = n_fft << lg;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    const int k = g >> lg;
+    const int q = g & ((1 << lg) - 1);
+    const int low = q & ((1 << s) - 1);
+    const int i0 = ((q >> s) << (s + RS)) | low;
+    C<R>* d = data + k * seq_stride;
+    C<R> v[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int e = i0 + (t << s);
+      v[t] = d[e + (e >> pad_shift)];
+    }
+    dit_group<R, RS>(v, logn, s, low, tw, tw_stride);
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int e = i0 + (t << s);
+      d[e + (e >> pad_shift)] = v[t];
+    }
+  }
+}
+
 // In-place radix-2 decimation-in-time FFTs on n_fft sequences of length 2^logn in
 // shared memory, sequence k at data + k * seq_stride, already in bit-reversed order.
 // tw[m * tw_stride] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  Element i of a sequence is
 // stored at i + (i >> pad_shift) (one pad slot per 2^pad_shift elements, so that the
-// bit-reversed scatter does not hit one bank).  All threads of the block call it.
+// bit-reversed scatter does not hit one bank).  Stages s0 .. logn - 1 run three at a
+// time (dit_pass).  All threads of the block call it.
 template <typename R>
 __device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C<R>* __restrict__ tw,
-                        int tw_stride, int pad_shift = 31) {
-  if (logn == 0) return;
-  const int half_n = 1 << (logn - 1);
-  const int total = n_fft * half_n;
-  for (int s = 0; s < logn; ++s) {
-    const int half = 1 << s;
-    const int tshift = logn - 1 - s;
-    for (int b = threadIdx.x; b < total; b += blockDim.x) {
-      const int k = b >> (logn - 1);
-      const int j = b & (half_n - 1);
-      const int pos = j & (half - 1);
-      const int i0 = ((j >> s) << (s + 1)) + pos;
-      C<R>* d = data + k * seq_stride;
-      const C<R> w = tw[(pos << tshift) * tw_stride];
-      const int p0 = i0 + (i0 >> pad_shift), p1 = i0 + half + ((i0 + half) >> pad_shift);
-      const C<R> a = d[p0];
-      const C<R> t = cmul<R>(d[p1], w);
-      C<R> u, v;
-      u.x = a.x + t.x; u.y = a.y + t.y;
-      v.x = a.x - t.x; v.y = a.y - t.y;
-      d[p0] = u; d[p1] = v;
-    }
+                        int tw_stride, int pad_shift = 31, int s0 = 0) {
+  for (int s = s0; s < logn;) {
+    const int rs = logn - s >= 3 ? 3 : logn - s;
+    if (rs == 3) dit_pass<R, 3>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
+    else if (rs == 2) dit_pass<R, 2>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
+    else dit_pass<R, 1>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
+    s += rs;
     __syncthreads();
   }
 }
@@ -78,8 +133,8 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
     const int64_t local = vb - vb_begin[r];
-    const int y = (int)(local % d.ny);
-    const int p = (int)(local / d.ny);
+    const int y = (int)(local & (d.ny - 1));              // ny is a power of two
+    const int p = (int)(local >> d.log2ny);
     const int fa = 2 * p, fb = 2 * p + 1;
     const bool has_b = fb < (int)d.n_fields;
     const int nx = d.nx, logn = d.log2nx;
@@ -88,13 +143,36 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
     const R* xa = fields + fa * plane + (int64_t)y * nx;
     const R* xb = fields + fb * plane + (int64_t)y * nx;
     const int ps = logn > 5 ? logn - 5 : 31;        // 32 pad slots per row
-    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-      C<R> v; v.x = xa[x]; v.y = has_b ? xb[x] : (R)0;
-      const int i = brev(x, logn);
-      z[i + (i >> ps)] = v;
+    const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_x);
+    if (logn >= 3) {
+      // thread x0 < nx/8 loads x0 + j nx/8 (j < 8, coalesced): after bit reversal these are
+      // elements t = brev3(j) of the group m = brev(x0) of the first three stages, which
+      // run in registers before the group is stored
+      const int n8 = nx >> 3;
+      for (int x0 = threadIdx.x; x0 < n8; x0 += blockDim.x) {
+        C<R> v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int x = x0 + (((t & 1) << 2) | (t & 2) | ((t >> 2) & 1)) * n8;
+          v[t].x = xa[x];
+          v[t].y = has_b ? xb[x] : (R)0;
+        }
+        dit_group<R, 3>(v, logn, 0, 0, tw, 1);
+        const int i0 = brev(x0, logn - 3) << 3;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) z[i0 + t + ((i0 + t) >> ps)] = v[t];
+      }
+      __syncthreads();
+      dit_fft<R>(z, logn, 1, 0, tw, 1, ps, 3);
+    } else {
+      for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        C<R> v; v.x = xa[x]; v.y = has_b ? xb[x] : (R)0;
+        const int i = brev(x, logn);
+        z[i + (i >> ps)] = v;
+      }
+      __syncthreads();
+      dit_fft<R>(z, logn, 1, 0, tw, 1, ps);
     }
-    __syncthreads();
-    dit_fft<R>(z, logn, 1, 0, reinterpret_cast<const C<R>*>(ws + d.off_tw_x), 1, ps);
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     C<R>* ra = spec + fa * fplane + (int64_t)y * d.wpitch;
@@ -124,31 +202,41 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
-    const int tiles = (d.half_nx + ncol - 1) / ncol;
+    const int lc = 31 - __clz(ncol);                    // ncol is a power of two
+    const int tiles = (d.half_nx + ncol - 1) >> lc;
     const int64_t local = vb - vb_begin[r];
     const int y2 = (int)(local / tiles);
-    const int kx0 = (int)(local % tiles) * ncol;
+    const int kx0 = (int)(local - (int64_t)y2 * tiles) << lc;
     const int ncl = min(ncol, d.half_nx - kx0);
     const int logn1 = d.log2n1, n1 = 1 << logn1, n2 = d.ny >> logn1, F = (int)d.n_fields;
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     const int total = F * n1 * ncol;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int c = i % ncol;
-      const int y1 = (i / ncol) % n1;
-      const int f = i / (ncol * n1);
-      C<R> v; v.x = (R)0; v.y = (R)0;
-      if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
-      s[(f * ncol + c) * (n1 + 1) + brev(y1, logn1)] = v;
+    // gather, four loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+      C<R> v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int c = i & (ncol - 1), y1 = (i >> lc) & (n1 - 1), f = i >> (lc + logn1);
+        v[u].x = (R)0; v[u].y = (R)0;
+        if (i < total && c < ncl) v[u] = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int c = i & (ncol - 1), y1 = (i >> lc) & (n1 - 1), f = i >> (lc + logn1);
+        if (i < total) s[(f * ncol + c) * (n1 + 1) + brev(y1, logn1)] = v[u];
+      }
     }
     __syncthreads();
     const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_y);
     dit_fft<R>(s, logn1, F * ncol, n1 + 1, tw, n2);
     const int hn = d.ny >> 1;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int c = i % ncol;
-      const int k1 = (i / ncol) % n1;
-      const int f = i / (ncol * n1);
+      const int c = i & (ncol - 1);
+      const int k1 = (i >> lc) & (n1 - 1);
+      const int f = i >> (lc + logn1);
       if (c >= ncl) continue;
       const int e = y2 * k1;                       // < ny
       C<R> w = tw[e < hn ? e : e - hn];
@@ -169,56 +257,89 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
-    const int tiles = (d.half_nx + ncol - 1) / ncol;
+    const int lc = 31 - __clz(ncol);                    // ncol is a power of two
+    const int tiles = (d.half_nx + ncol - 1) >> lc;
     const int64_t local = vb - vb_begin[r];
     const int k1 = (int)(local / tiles);
-    const int kx0 = (int)(local % tiles) * ncol;
+    const int kx0 = (int)(local - (int64_t)k1 * tiles) << lc;
     const int logn1 = d.log2n1, n1 = 1 << logn1, logn2 = d.log2ny - logn1, n2 = d.ny >> logn1;
     const int F = (int)d.n_fields;
     const int ncl = min(ncol, d.half_nx - kx0);
     const C<R>* spec = reinterpret_cast<const C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
+    // blocked pair sums: this block's sums of every pair are one contiguous range, pulled
+    // into L2 by bulk prefetches while the columns are loaded and transformed
+    if (d.acc_ncol && threadIdx.x < d.n_pairs) {
+      const int pr = threadIdx.x;
+      const int64_t el = d.pair_a[pr] == d.pair_b[pr] ? 8 : 16;
+      const int64_t first = (int64_t)(k1 * tiles + (kx0 >> lc)) * n2 * ncol;
+      const char* base = ws + d.pair_off[pr] + first * el;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(base), "r"((uint32_t)(n2 * ncol * el)) : "memory");
+    }
     // smem layout: [field][column][n2]
     const int total = F * n2 * ncol;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int c = i % ncol;
-      const int y2 = (i / ncol) % n2;
-      const int f = i / (ncol * n2);
-      C<R> v; v.x = (R)0; v.y = (R)0;
-      if (c < ncl) v = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
-      s[(f * ncol + c) * (n2 + 1) + brev(y2, logn2)] = v;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {   // four loads in flight
+      C<R> v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int c = i & (ncol - 1), y2 = (i >> lc) & (n2 - 1), f = i >> (lc + logn2);
+        v[u].x = (R)0; v[u].y = (R)0;
+        if (i < total && c < ncl) v[u] = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int c = i & (ncol - 1), y2 = (i >> lc) & (n2 - 1), f = i >> (lc + logn2);
+        if (i < total) s[(f * ncol + c) * (n2 + 1) + brev(y2, logn2)] = v[u];
+      }
     }
     __syncthreads();
     dit_fft<R>(s, logn2, F * ncol, n2 + 1, reinterpret_cast<const C<R>*>(ws + d.off_tw_y), n1);
-    // accumulate pair products in FP64; k = 0 sums for the mean subtraction
-    const int npts = n2 * ncol;
-    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
-      const int c = i % ncol;
-      const int k2 = i / ncol;
-      if (c >= ncl) continue;
-      const int kx = kx0 + c;
-      const int ky = k1 + n1 * k2;
-      const int64_t pt = (int64_t)ky * d.half_nx + kx;
-      for (int pr = 0; pr < d.n_pairs; ++pr) {
+    // accumulate pair products in FP64: one work item per (pair, point) of the block,
+    // pair-major so that a warp works on one pair (uniform auto/cross branch) and 32
+    // consecutive points; four items per thread are loaded before any is stored
+    const int lp = lc + logn2, npts = 1 << lp;
+    const int items = d.n_pairs << lp;
+    for (int it0 = threadIdx.x; it0 < items; it0 += 4 * blockDim.x) {
+      double2 acc[4];
+      int64_t pt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int it = it0 + u * blockDim.x;
+        const int pr = it >> lp, i = it & (npts - 1);
+        const int c = i & (ncol - 1), k2 = i >> lc;
+        pt[u] = -1;
+        if (it >= items || c >= ncl) continue;
+        pt[u] = d.acc_ncol ? ((int64_t)(k1 * tiles + (kx0 >> lc)) * n2 + k2) * ncol + c   // contiguous per block
+                           : (int64_t)(k1 + n1 * k2) * d.half_nx + kx0 + c;
+        if (d.pair_a[pr] == d.pair_b[pr]) acc[u].x = reinterpret_cast<const double*>(ws + d.pair_off[pr])[pt[u]];
+        else acc[u] = reinterpret_cast<const double2*>(ws + d.pair_off[pr])[pt[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (pt[u] < 0) continue;
+        const int it = it0 + u * blockDim.x;
+        const int pr = it >> lp, i = it & (npts - 1);
+        const int c = i & (ncol - 1), k2 = i >> lc;
         const int a = d.pair_a[pr], b = d.pair_b[pr];
         const C<R> Xa = s[(a * ncol + c) * (n2 + 1) + k2];
         const C<R> Xb = s[(b * ncol + c) * (n2 + 1) + k2];
         // the product in the transform's precision (exact to its rounding), the sum in FP64
         if (a == b) {
-          double* acc = reinterpret_cast<double*>(ws + d.pair_off[pr]);
-          acc[pt] += (double)(Xa.x * Xa.x + Xa.y * Xa.y);
+          acc[u].x += (double)(Xa.x * Xa.x + Xa.y * Xa.y);
+          reinterpret_cast<double*>(ws + d.pair_off[pr])[pt[u]] = acc[u].x;
         } else {
-          double2* acc = reinterpret_cast<double2*>(ws + d.pair_off[pr]);
-          double2 v = acc[pt];
-          v.x += (double)(Xa.x * Xb.x + Xa.y * Xb.y);          // X_a X_b^*
-          v.y += (double)(Xa.y * Xb.x - Xa.x * Xb.y);
-          acc[pt] = v;
+          acc[u].x += (double)(Xa.x * Xb.x + Xa.y * Xb.y);     // X_a X_b^*
+          acc[u].y += (double)(Xa.y * Xb.x - Xa.x * Xb.y);
+          reinterpret_cast<double2*>(ws + d.pair_off[pr])[pt[u]] = acc[u];
         }
       }
-      if (kx == 0 && ky == 0) {
-        double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
-        for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol + c) * (n2 + 1)].x;
-      }
+    }
+    // k = 0 sums for the mean subtraction
+    if (k1 == 0 && kx0 == 0 && threadIdx.x == 0) {
+      double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
+      for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol) * (n2 + 1)].x;
     }
     __syncthreads();
   }

@@ -51,7 +51,7 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   d.half_nx = nx / 2 + 1;
   d.wpitch = (d.half_nx + 1) & ~1;
   d.log2n1 = l1;
-  P.ncol = 16;
+  P.ncol = kColsMax;
   while (P.ncol > 1 && fft_cols_smem(precision, F, len, P.ncol) > kColsSmemBudget) P.ncol >>= 1;
   P.rows_smem = fft_rows_smem(precision, nx);
   P.rows_block = std::max(32, std::min(512, nx / 2));
