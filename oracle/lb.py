@@ -24,6 +24,9 @@ Readings where the paper is silent or unit-specific:
 * Fields are sampled on the pre-collision state of step t (after streaming).
 * s_a = 1 unless a per-site noise-scale network is given (learned extension,
   not in the paper): s_a = 1 + o_a(u_x, u_y, rho - rho0), see ``oracle.mlp``.
+* noise_mode = 1 (extension the paper points to after Eq. 7): the noise on the
+  non-conserved moments is correlated, xi = s * (R N) with R from
+  ``oracle.correlated`` (Eq. 6 with the covariance of Eq. 7 at f^0(rho0, u0)).
 
 Normals come from ``oracle.philox`` with counter (site, t, call | tag << 8,
 stream); D2Q9 uses normals 0..5 for moments 3..8, D1Q3 normal 0 for moment 2.
@@ -37,6 +40,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
+from . import correlated as _corr
 from . import lattice as _lat
 from . import philox as _rng
 from . import spectra as _spec
@@ -61,6 +65,7 @@ class Params:
     fields: Sequence[int] = field(default_factory=list)
     mlp: Optional[dict] = None               # {"W1","b1","W2","b2","W3","b3"} FP64 arrays
     mlp_bf16: bool = False                   # round network operands to bfloat16 (tensor-core precision)
+    noise_mode: int = 0                      # 0: independent noise (Eq. 8); 1: correlated (oracle.correlated)
 
     @property
     def lat(self):
@@ -191,10 +196,16 @@ def collide(p, f, t, return_parts=False, sites=None):
         n_normals = 6 if lat.name == "D2Q9" else 1
         N = _rng.site_normals(n_normals, sites, t, 0, p.stream, p.seed)
         s = noise_scale(p, rho, u)
-        for c, a in enumerate(lat.nonconserved):
-            if (mask >> a) & 1:
-                amp = np.sqrt(p.mu * p.rho0 * (2.0 * tau[a] - 1.0)) / tau[a]   # Eq. 8
-                xi[a] = s[a] * amp * N[c]
+        if p.noise_mode == 1:                                          # xi = R N (Eqs. 6-7 at u0)
+            R, _, _ = _corr.noise_root(lat, tau, p.rho0, p.kT, p.u0_vec(), mask)
+            Z = np.tensordot(R, N[: len(lat.nonconserved)], axes=(1, 0))
+            for c, a in enumerate(lat.nonconserved):
+                xi[a] = s[a] * Z[c]
+        else:
+            for c, a in enumerate(lat.nonconserved):
+                if (mask >> a) & 1:
+                    amp = np.sqrt(p.mu * p.rho0 * (2.0 * tau[a] - 1.0)) / tau[a]   # Eq. 8
+                    xi[a] = s[a] * amp * N[c]
     Mp = M.copy()
     for a in lat.nonconserved:
         Mp[a] = M[a] - (M[a] - Meq[a]) / tau[a] + xi[a]                # Eq. 5

@@ -12,7 +12,8 @@ derivative of the collision (Eq. 5) with respect to the pre-collision f,
     F_ij = d f_i^0 / d f_j of Eq. 2 at (rho0, u0),
 
 (M = m_i^a of Eq. 9, N = n_i^a = w_i m_i^a), and xi is white noise with per-site
-variances sigma_a^2 = s_a^2 mu rho0 (2 tau^a - 1) / tau_a^2 (Eq. 8).  The
+variances sigma_a^2 = s_a^2 mu rho0 (2 tau^a - 1) / tau_a^2 (Eq. 8), or with the
+covariance of the correlated scheme (``noise_matrix``).  The
 stationary equal-time covariance per unit volume C_k = <df(k) df(k)^H> / V then
 solves the discrete Lyapunov equation
 
@@ -38,6 +39,7 @@ measured spectra agree within statistical error).
 import numpy as np
 import scipy.linalg as sla
 
+from . import correlated as _corr
 from . import lattice as _lat
 
 
@@ -69,6 +71,22 @@ def noise_variances(lat, tau, rho0, kT, mask, scale=None):
             s = 1.0 if scale is None else float(scale[c])
             s2[a] = s * s * mu * rho0 * (2.0 * tau[a] - 1.0) / tau[a] ** 2
     return s2
+
+
+def noise_matrix(p, scale=None):
+    """Covariance of the moment noise xi (q x q): diag(sigma^2) of Eq. 8, or for
+    p.noise_mode == 1 the positive part of Eq. 6 at u0 (oracle.correlated); the
+    per-moment scales s multiply rows and columns."""
+    lat = p.lat
+    tau = np.asarray(p.tau, dtype=np.float64)
+    if getattr(p, "noise_mode", 0) != 1:
+        return np.diag(noise_variances(lat, tau, p.rho0, p.kT, p.mask(), scale))
+    _, _, Xp = _corr.noise_root(lat, tau, p.rho0, p.kT, p.u0_vec(), p.mask())
+    s = np.ones(lat.q)
+    if scale is not None:
+        for c, a in enumerate(lat.nonconserved):
+            s[a] = float(scale[c])
+    return s[:, None] * Xp * s[None, :]
 
 
 def wavevectors(nx, ny):
@@ -113,8 +131,7 @@ def theory_spectra(p, fields, scale=None, tol=1e-9):
     nx = p.nx
     tau = np.asarray(p.tau, dtype=np.float64)
     J = collision_jacobian(lat, tau, p.rho0, p.u0_vec())
-    sig2 = noise_variances(lat, tau, p.rho0, p.kT, p.mask(), scale)
-    Qf = lat.n @ np.diag(sig2) @ lat.n.T
+    Qf = lat.n @ noise_matrix(p, scale) @ lat.n.T
     L = field_rows(p, fields)
     var = np.array([field_variance(p, f) for f in fields])
     kx, ky = wavevectors(nx, ny)

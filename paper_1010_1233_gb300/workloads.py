@@ -40,14 +40,18 @@ def taus_d1q3(tau):
 
 
 def replica(lattice=D2Q9, nx=16, ny=16, tau=None, rho0=1.0, kT=1e-4, u0=(0.0, 0.0),
-            seed=0, stream=0, noise_mask=None, init_mode=0, fields=()):
-    """One replica's parameters as a plain dict (keys shared by both sides)."""
+            seed=0, stream=0, noise_mask=None, init_mode=0, fields=(), noise_mode=0):
+    """One replica's parameters as a plain dict (keys shared by both sides).
+
+    noise_mode 0: independent noise per non-conserved moment; 1: correlated noise
+    for the mean velocity u0."""
     if tau is None:
         tau = taus_d2q9(1.0) if lattice == D2Q9 else taus_d1q3(1.0)
     return dict(lattice=lattice, nx=int(nx), ny=int(ny if lattice == D2Q9 else 1),
                 tau=[float(t) for t in tau], rho0=float(rho0), kT=float(kT),
                 u0=(float(u0[0]), float(u0[1])), seed=int(seed), stream=int(stream),
-                noise_mask=noise_mask, init_mode=int(init_mode), fields=list(fields))
+                noise_mask=noise_mask, init_mode=int(init_mode), fields=list(fields),
+                noise_mode=int(noise_mode))
 
 
 def d1q3_L64():
