@@ -75,6 +75,15 @@ typedef struct {
   uint32_t init_mode;   /* 0: f^0(rho0, u0) on every site; 1: thermal (moment
                            fluctuations N(0, mu rho0), mean of rho and j removed) */
   uint32_t field_mask;  /* fields to sample (see above); 0 = no sampling         */
+  uint32_t noise_mode;  /* 0: independent noise per non-conserved moment (Eq. 8).
+                           1: correlated noise for a fluid moving at u0 (the
+                           extension the paper points to after Eq. 7): the
+                           noise covariance of Eq. 6 with the moment covariance
+                           mu sum_i m_i^a m_i^b f^0_i(rho0, u0) of Eq. 7 on the
+                           masked non-conserved moments; xi = R N with R the
+                           principal square root of its positive part (computed
+                           once per replica on the host).  At u0 = 0 it equals
+                           mode 0                                               */
 } flb_replica;
 
 typedef struct flb_ctx flb_ctx;

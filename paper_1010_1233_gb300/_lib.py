@@ -26,7 +26,7 @@ class flb_replica(ctypes.Structure):
     _fields_ = [("lattice", c_int32), ("nx", c_int32), ("ny", c_int32), ("tau", c_double * 9),
                 ("rho0", c_double), ("kT", c_double), ("u0", c_double * 2), ("seed", c_uint64),
                 ("stream", c_uint32), ("noise_mask", c_uint32), ("init_mode", c_uint32),
-                ("field_mask", c_uint32)]
+                ("field_mask", c_uint32), ("noise_mode", c_uint32)]
 
 
 _SIGS = {

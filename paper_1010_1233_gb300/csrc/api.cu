@@ -104,6 +104,7 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.noise_mask & ((1u << nc0) - 1)) return set_error(FLB_EINVAL, "replica %d: noise on a conserved moment", r);
     if (p.noise_mask >> q) return set_error(FLB_EINVAL, "replica %d: noise_mask has bits beyond moment %d", r, q - 1);
     if (p.init_mode > 1) return set_error(FLB_EINVAL, "replica %d: init_mode must be 0 or 1", r);
+    if (p.noise_mode > 1) return set_error(FLB_EINVAL, "replica %d: noise_mode must be 0 or 1", r);
     for (int f = 0; f < 32; ++f)
       if (((p.field_mask >> f) & 1) && !field_valid(lat, f))
         return set_error(FLB_EINVAL, "replica %d: field %d not available on this lattice", r, f);
@@ -119,6 +120,100 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.init_mode == 1 && p.kT > 0 && (int64_t)p.nx * p.ny < 2) return set_error(FLB_EINVAL, "thermal init needs V >= 2");
   }
   return FLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Correlated noise (noise_mode 1).  Moment rows of Eq. 9 (D2Q9) and of the D1Q3
+// projection, the discrete Maxwellian of Eq. 2, the moment covariance of Eq. 7 at
+// f^0(rho0, u0), the noise covariance of Eq. 6, and the principal square root of its
+// positive part.
+
+static double moment_row(bool d2, int a, double vx, double vy) {
+  const double v2 = vx * vx + vy * vy, s3 = std::sqrt(3.0);
+  if (!d2) {
+    const double m[3] = {1.0, s3 * vx, (3.0 * vx * vx - 1.0) / std::sqrt(2.0)};
+    return m[a];
+  }
+  switch (a) {
+    case 0: return 1.0;
+    case 1: return s3 * vx;
+    case 2: return s3 * vy;
+    case 3: return 1.5 * (vx * vx - vy * vy);
+    case 4: return 3.0 * vx * vy;
+    case 5: return 1.5 * v2 - 1.0;
+    case 6: return std::sqrt(1.5) * vx * (3.0 * v2 - 4.0);
+    case 7: return std::sqrt(1.5) * vy * (3.0 * v2 - 4.0);
+    default: return 2.25 * v2 * v2 - 3.75 * v2 + 0.5;
+  }
+}
+
+// Eigen-decomposition of a symmetric n x n matrix (n <= 6) by cyclic Jacobi rotations
+// (Golub & Van Loan, Matrix Computations, Sec. 8.5): A = V diag(w) V^T.
+static void jacobi_eigen(int n, double A[6][6], double V[6][6], double w[6]) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) { tot += A[i][j] * A[i][j]; if (i != j) off += A[i][j] * A[i][j]; }
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (A[p][q] == 0.0) continue;
+        // rotation that zeroes A[p][q]: t = tan(theta), theta = (A_qq - A_pp) / (2 A_pq)
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {            // A <- A J (columns p, q)
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {            // A <- J^T A (rows p, q)
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {            // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) w[i] = A[i][i];
+}
+
+// R (n_nc x n_nc, row-major in out) for replica p; returns n_nc.
+static int correlated_root(const flb_replica& p, double* out) {
+  const bool d2 = p.lattice == FLB_D2Q9;
+  const int q = d2 ? 9 : 3, nc0 = d2 ? 3 : 2, n = q - nc0;
+  const double mu = 3.0 * p.kT, ux = p.u0[0], uy = d2 ? p.u0[1] : 0.0, uu = ux * ux + uy * uy;
+  double C[9][9] = {};
+  for (int i = 0; i < q; ++i) {
+    const double vx = d2 ? kVx9[i] : kVx3[i], vy = d2 ? kVy9[i] : 0.0, w = d2 ? kW9[i] : kW3[i];
+    const double vu = vx * ux + vy * uy;
+    const double f0 = w * p.rho0 * (1.0 + 3.0 * vu + 4.5 * vu * vu - 1.5 * uu);     // Eq. 2
+    double m[9];
+    for (int a = 0; a < q; ++a) m[a] = moment_row(d2, a, vx, vy);
+    for (int a = 0; a < q; ++a)
+      for (int b = 0; b < q; ++b) C[a][b] += mu * m[a] * m[b] * f0;             // Eq. 7 at u0
+  }
+  double A[6][6] = {}, V[6][6], w[6];
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) {
+      const int ma = nc0 + a, mc = nc0 + c;
+      if (!((p.noise_mask >> ma) & 1) || !((p.noise_mask >> mc) & 1)) continue;
+      A[a][c] = (p.tau[ma] + p.tau[mc] - 1.0) / (p.tau[ma] * p.tau[mc]) * C[ma][mc];   // Eq. 6
+    }
+  jacobi_eigen(n, A, V, w);
+  for (int a = 0; a < n; ++a)
+    for (int c = 0; c < n; ++c) {
+      double r = 0.0;
+      for (int k = 0; k < n; ++k) r += V[a][k] * std::sqrt(w[k] > 0.0 ? w[k] : 0.0) * V[c][k];
+      out[a * n + c] = r;
+    }
+  return n;
 }
 
 static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
@@ -156,6 +251,18 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   d.half_nx = p.nx / 2 + 1;
   d.wpitch = (d.half_nx + 1) & ~1;
   d.log2n1 = F ? column_split(precision, F, p.ny) : 0;
+  d.noise_mode = (int32_t)p.noise_mode;
+  if (p.noise_mode == 1) {
+    double R[36];
+    const int nr = correlated_root(p, R);
+    if (d2) {
+      for (int i = 0; i < 36; ++i) d.dco[kCoNoiseR + i] = R[i];
+    } else {
+      d.amp[2] = R[0];            // one non-conserved moment: the root is its amplitude
+      d.noise_mode = 0;
+    }
+    (void)nr;
+  }
   d.dco[kCoRho0] = d.rho0; d.dco[kCoU0x] = d.u0x; d.dco[kCoU0y] = d.u0y;
   for (int a = 0; a < 9; ++a) { d.dco[kCoInvTau + a] = d.inv_tau[a]; d.dco[kCoAmp + a] = d.amp[a]; }
   for (int f = 0; f < kMaxFields; ++f) d.dco[kCoMref + f] = d.mref[f];

@@ -21,7 +21,8 @@ constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut *
 constexpr int kMlpBiases = kMlpHidden + kMlpHidden + kMlpOut;                               // 70
 
 constexpr int kCoRho0 = 0, kCoU0x = 1, kCoU0y = 2, kCoInvTau = 3, kCoAmp = 12, kCoMref = 21;
-constexpr int kNumCoef = kCoMref + 11;
+constexpr int kCoNoiseR = kCoMref + 11;      // 6 x 6 correlated-noise root (noise_mode 1), row-major
+constexpr int kNumCoef = kCoNoiseR + 36;
 
 // Per-replica description, resident in device memory (one array per context).
 // Offsets are byte offsets from the workspace base.
@@ -34,6 +35,7 @@ struct ReplicaDesc {
   int64_t n_units;              // units_per_row * ny
   int64_t block_begin;          // first virtual block of this replica in the step launch
   uint32_t seed_lo, seed_hi, stream, noise_mask;
+  int32_t noise_mode;           // 0: independent noise (Eq. 8); 1: correlated (root in kCoNoiseR)
   uint32_t field_mask, n_fields;
   int32_t field_id[kMaxFields];     // slot -> field id
   int32_t n_pairs;
@@ -56,7 +58,8 @@ struct ReplicaDesc {
                                     // (ky = k1 + N1 k2; kx padded to a multiple of c)
   // the per-replica coefficients in the arithmetic type of the path (host-filled),
   // so the FP32 kernels never convert from FP64: [kCoRho0], [kCoU0x], [kCoU0y],
-  // [kCoInvTau + a], [kCoAmp + a], [kCoMref + field]
+  // [kCoInvTau + a], [kCoAmp + a], [kCoMref + field], [kCoNoiseR + 6 c + c'] (c, c' index
+  // the non-conserved moments 3..8)
   float fco[kNumCoef];
   double dco[kNumCoef];
 };

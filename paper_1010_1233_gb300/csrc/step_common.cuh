@@ -180,7 +180,8 @@ __device__ __forceinline__ void normals_d2q9(const ReplicaDesc& d, uint32_t site
 // Collision of one site (Eqs. 5, 8, 10), in two parts.  collide_relax: the non-conserved
 // moments M^3..M^8 of Eq. 9, relaxed towards the equilibrium moments of Eq. 10 at rates
 // 1/tau^a: D[a - 3] = Delta M^a (and the sampled fields of the pre-collision state when
-// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a and the back transform
+// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a (or, for correlated noise,
+// xi^a = s_a sum_c R_ac N^c) and the back transform
 // sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a, in place.
 template <typename R, bool DEV, bool SAMPLE>
 __device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)[9], R sum, R ux, R uy, R (&D)[6],
@@ -223,7 +224,22 @@ __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], b
                                               const R (&sc)[6], const R (&Drel)[6]) {
   const R S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
   R D3 = Drel[0], D4 = Drel[1], D5 = Drel[2], D6 = Drel[3], D7 = Drel[4], D8 = Drel[5];
-  if (noisy) {                                   // Eq. 8, scaled per moment by s
+  if (noisy && d.noise_mode) {                   // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
+    R z[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      R acc = coef<R>(d, kCoNoiseR + 6 * c) * n[0];
+#pragma unroll
+      for (int e = 1; e < 6; ++e) acc += coef<R>(d, kCoNoiseR + 6 * c + e) * n[e];
+      z[c] = acc;
+    }
+    D3 += sc[0] * z[0];
+    D4 += sc[1] * z[1];
+    D5 += sc[2] * z[2];
+    D6 += sc[3] * z[3];
+    D7 += sc[4] * z[4];
+    D8 += sc[5] * z[5];
+  } else if (noisy) {                            // Eq. 8, scaled per moment by s
     D3 += sc[0] * coef<R>(d, kCoAmp + 3) * n[0];
     D4 += sc[1] * coef<R>(d, kCoAmp + 4) * n[1];
     D5 += sc[2] * coef<R>(d, kCoAmp + 5) * n[2];

@@ -185,9 +185,11 @@ def experiment(n=128, n_train=16, u_max=0.3, heldout=(0.07, 0.17, 0.2, 0.27), st
     km = included_k(n, n)
     for u in heldout:
         res = {}
-        for name, mlp in (("plain", None), ("learned", w)):
+        # the plain method, the learned per-site scales, and (for comparison) the correlated
+        # noise of the moving equilibrium (noise_mode 1), which needs no training
+        for name, mlp, mode in (("plain", None, 0), ("learned", w, 0), ("correlated", None, 1)):
             p = W.replica("D2Q9", n, n, W.taus_d2q9(0.8, 0.8, 1.0), kT=1e-4, u0=(u, 0.0), seed=999,
-                          init_mode=1, fields=HYDRO_FIELDS)
+                          init_mode=1, fields=HYDRO_FIELDS, noise_mode=mode)
             sim = run_spectra([p], steps, warmup, sample_every, mlp=mlp)
             S = hydro_matrix(sim, 0, km)
             sim.close()

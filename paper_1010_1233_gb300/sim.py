@@ -33,6 +33,7 @@ def replica_struct(p):
     s.noise_mask = sum(1 << a for a in _NONCONSERVED[p["lattice"]]) if nm is None else int(nm)
     s.init_mode = int(p.get("init_mode", 0))
     s.field_mask = sum(1 << f for f in p.get("fields", ()))
+    s.noise_mode = int(p.get("noise_mode", 0))
     return s
 
 
