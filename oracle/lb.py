@@ -216,13 +216,15 @@ def collide(p, f, t, return_parts=False, sites=None):
 
 
 class Run:
-    """State (post-collision f*), global step counter and correlator sums."""
+    """State (post-collision f*), global step counter and correlator sums; optional
+    time correlators at selected wave vectors (``tacc``, spectra.TimeAccumulator)."""
 
-    def __init__(self, p: Params, fstar=None):
+    def __init__(self, p: Params, fstar=None, time_k=None, n_lags=0):
         self.p = p
         self.f = initial_state(p) if fstar is None else np.array(fstar, dtype=np.float64)
         self.t = 0
         self.acc = _spec.Accumulator(p) if p.fields else None
+        self.tacc = _spec.TimeAccumulator(p, time_k, n_lags) if (time_k and p.fields) else None
 
     def run(self, n_steps, sample_every=0):
         p = self.p
@@ -230,7 +232,10 @@ class Run:
             f = stream(p.lat, self.f)
             if sample_every and self.acc is not None and self.t % sample_every == 0:
                 rho, _, u = macroscopic(p.lat, f)
-                self.acc.add(sample_fields(p, f, rho, u))
+                fl = sample_fields(p, f, rho, u)
+                self.acc.add(fl)
+                if self.tacc is not None:
+                    self.tacc.add(fl)
             self.f = collide(p, f, self.t)
             self.t += 1
         return self

@@ -113,3 +113,49 @@ class PointAccumulator:
                 c[i] -= m_a * m_b
         V = p.nx * (p.ny if p.lat.d == 2 else 1)
         return c / (V * np.sqrt(field_variance(p, a) * field_variance(p, b)))
+
+
+class TimeAccumulator:
+    """Time correlators at a list of wave vectors (an extension the paper leaves to
+    future work, Sec. 3: its correlators are equal-time ones).
+
+    For samples s = 0, 1, ... (every sample_every steps) and lag tau = 0 .. n_lags - 1
+    (in samples), with every ordered field pair (a, b):
+
+        F_ab(k, tau) = N^{ab} (1 / n_tau) sum_{s >= tau} X_a(k, s) X_b(k, s - tau)^*,
+
+    n_tau = n - tau pairs of samples, N^{ab} the normalisation of the equal-time
+    correlators (so F_ab(k, 0) = C_ab(k) away from k = 0; k = 0 is not allowed, there
+    the mean would have to be removed).  X(k) is the direct sum of Eq. 11.
+    """
+
+    def __init__(self, p, kpoints, n_lags):
+        self.p = p
+        self.fields = list(p.fields)
+        self.k = [tuple(k) for k in kpoints]
+        if any(kx == 0 and ky == 0 for ky, kx in self.k):
+            raise ValueError("k = 0 is not supported")
+        self.T = int(n_lags)
+        self.hist = []                                   # last T samples: {fid: (n_k,) complex}
+        self.n = 0
+        self.sum = {(a, b): np.zeros((self.T, len(self.k)), complex) for a in self.fields for b in self.fields}
+
+    def add(self, fields):
+        ny = self.p.ny if self.p.lat.d == 2 else 1
+        X = {fid: np.array([dft_at(np.asarray(v).reshape(ny, self.p.nx), kx, ky) for ky, kx in self.k])
+             for fid, v in fields.items()}
+        self.hist.insert(0, X)                           # hist[tau] = sample s - tau
+        del self.hist[self.T:]
+        for (a, b), acc in self.sum.items():
+            for tau, Y in enumerate(self.hist):
+                acc[tau] += X[a] * np.conj(Y[b])
+        self.n += 1
+
+    def correlator(self, a, b):
+        """Normalised F_ab(k, tau), shape (n_lags, n_k); lags without pairs are NaN."""
+        p = self.p
+        V = p.nx * (p.ny if p.lat.d == 2 else 1)
+        norm = 1.0 / (V * np.sqrt(field_variance(p, a) * field_variance(p, b)))
+        n_tau = np.array([self.n - t for t in range(self.T)], float)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return np.where(n_tau[:, None] > 0, self.sum[(a, b)] / n_tau[:, None], np.nan) * norm

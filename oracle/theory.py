@@ -168,3 +168,35 @@ def spectral_radius(p):
             P = streaming_phase(lat, np.array([kx[ix], ky[iy]]))
             r = max(r, np.abs(np.linalg.eigvals(P[:, None] * J)).max())
     return r
+
+
+def time_correlators(p, fields, kpoints, n_lags, every, scale=None):
+    """Predicted normalised F_ab(k, tau) = <X_a(k, s) X_b(k, s - tau)^*> (time
+    correlators of spectra.TimeAccumulator) for lags of tau * every steps:
+    the stationary covariance C_k propagated by the one-step operator,
+    <df(k, t + m) df(k, t)^H> / V = A_k^m C_k.  Returns {(a, b): (n_lags, n_k)}."""
+    from .spectra import field_variance
+    lat = p.lat
+    tau_m = np.asarray(p.tau, dtype=np.float64)
+    J = collision_jacobian(lat, tau_m, p.rho0, p.u0_vec())
+    Qf = lat.n @ noise_matrix(p, scale) @ lat.n.T
+    L = field_rows(p, fields)
+    var = np.array([field_variance(p, f) for f in fields])
+    ny = p.ny if lat.d == 2 else 1
+    out = {(a, b): np.zeros((n_lags, len(kpoints)), complex) for a in fields for b in fields}
+    for j, (ky, kx) in enumerate(kpoints):
+        kvec = np.array([2 * np.pi * kx / p.nx, 2 * np.pi * ky / ny])
+        P = streaming_phase(lat, kvec)
+        A = P[:, None] * J
+        Q = (P[:, None] * Qf) * np.conj(P)[None, :]
+        C = sla.solve_discrete_lyapunov(A, Q)
+        Ae = np.linalg.matrix_power(A, int(every))
+        G = C
+        for t in range(n_lags):
+            H = L @ G @ L.conj().T
+            for ia, a in enumerate(fields):
+                for ib, b in enumerate(fields):
+                    out[(a, b)][t, j] = H[ia, ib] / np.sqrt(var[ia] * var[ib])
+            G = Ae @ G
+    return out
+
