@@ -164,6 +164,27 @@ int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int e
 int flb_save(flb_ctx* ctx, void* host_buf, size_t* bytes_inout);
 int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 
+/* Time correlators at selected wave vectors (an extension: the paper's correlators
+ * are equal-time ones, Sec. 3, Eqs. 11-12):
+ *   F_ab(k, tau) = N^ab (1/n_tau) sum_s X_a(k, s) X_b(k, s - tau)^*
+ * over the samples s taken by flb_run (every sample_every steps), lags
+ * tau = 0 .. n_lags-1 in samples, n_tau = n_samples - tau, every ordered pair of
+ * the sampled fields, with the normalisation N^ab of flb_get_correlator (so
+ * F_ab(k, 0) = C_ab(k)).  The same n_k wave vectors for every replica: 0 <= kx_j
+ * <= nx/2, 0 <= ky_j < ny, k != 0; every replica must sample fields.
+ * flb_time_correlator_bytes: size of the caller-owned device buffer.
+ * flb_set_time_correlator: buf_dev 256-B aligned, at least that size, kept alive
+ * while enabled; zeroes the time-correlator sums (flb_reset_stats does too);
+ * n_lags = 0 switches them off.  Synchronises; captured graphs are dropped.
+ * flb_get_time_correlator: host_out [n_lags][n_k] complex (re, im), NaN for lags
+ * without a pair of samples; n_samples (may be NULL) the samples taken.  The
+ * time-correlator state is not part of flb_save checkpoints. */
+int flb_time_correlator_bytes(flb_ctx* ctx, int n_lags, int n_k, size_t* bytes_out);
+int flb_set_time_correlator(flb_ctx* ctx, int n_lags, int n_k, const int32_t* kx, const int32_t* ky,
+                            void* buf_dev, size_t bytes);
+int flb_get_time_correlator(flb_ctx* ctx, int replica, int field_a, int field_b, double* host_out,
+                            uint64_t* n_samples);
+
 /* Launch configuration of the step kernel.  staged = 0: direct kernels, vec
  * consecutive sites per thread (1, 2 or 4; > 1 only on the FP32 D2Q9 path,
  * every nx a multiple of vec), grid_blocks persistent blocks (0 = 16 per SM).

@@ -48,6 +48,9 @@ _SIGS = {
                                    c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_size_t, c_void_p]),
     "flb_get_step": (c_int, [c_void_p, POINTER(c_uint64)]),
+    "flb_time_correlator_bytes": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
+    "flb_set_time_correlator": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_size_t]),
+    "flb_get_time_correlator": (c_int, [c_void_p, c_int, c_int, c_int, POINTER(c_double), POINTER(c_uint64)]),
     "flb_set_mlp": (c_int, [c_void_p, POINTER(c_uint16), POINTER(c_float), c_int]),
     "flb_save": (c_int, [c_void_p, c_void_p, POINTER(c_size_t)]),
     "flb_load": (c_int, [c_void_p, c_void_p, c_size_t]),

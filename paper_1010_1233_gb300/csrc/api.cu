@@ -31,7 +31,9 @@ cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                     const TimeCorr& tc);
+void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
 
@@ -402,6 +404,8 @@ struct flb_ctx {
   struct Graph { uint32_t len; bool sample; cudaGraphExec_t exec; };
   std::vector<Graph> graphs;
   std::vector<float> mlp_host;
+  TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
+  int64_t tc_off_sums0 = 0, tc_bytes = 0;      // start of the sums (first replica) and buffer size
 };
 
 static ReplicaDesc* descs_dev(flb_ctx* c) { return reinterpret_cast<ReplicaDesc*>(c->ws + c->L.off_descs); }
@@ -431,11 +435,128 @@ static int reset_stats_async(flb_ctx* c) {
     int rc = cuda_check(cudaMemsetAsync(c->ws + a0, 0, a1 - a0, c->stream), "reset stats");
     if (rc) return rc;
   }
+  if (c->tc.base) {            // time-correlator sample counts and sums (the rings need no reset)
+    int rc = cuda_check(cudaMemsetAsync(c->tc.count, 0, 8 * (size_t)c->n, c->stream), "reset stats");
+    if (!rc) rc = cuda_check(cudaMemsetAsync(c->tc.base + c->tc_off_sums0, 0, (size_t)(c->tc_bytes - c->tc_off_sums0),
+                                             c->stream), "reset stats");
+    if (rc) return rc;
+  }
   c->n_samples = 0;
   return FLB_OK;
 }
 
+// Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | rings of every
+// replica | sums of every replica (contiguous, so a reset is one memset).
+static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vector<int64_t>* ring,
+                                std::vector<int64_t>* sums, int64_t* sums0) {
+  int64_t off = align256(8 * (int64_t)c->n);
+  off = align256(off + 4 * (int64_t)n_k);
+  off = align256(off + 4 * (int64_t)n_k);
+  for (int r = 0; r < c->n; ++r) {
+    if (ring) (*ring)[r] = off;
+    off = align256(off + 16 * (int64_t)n_lags * c->L.desc[r].n_fields * n_k);
+  }
+  if (sums0) *sums0 = off;
+  for (int r = 0; r < c->n; ++r) {
+    const int64_t F = c->L.desc[r].n_fields;
+    if (sums) (*sums)[r] = off;
+    off = align256(off + 16 * (int64_t)n_lags * F * F * n_k);
+  }
+  return off;
+}
+
 extern "C" {
+
+static void drop_graphs(flb_ctx* c);
+
+int flb_time_correlator_bytes(flb_ctx* c, int n_lags, int n_k, size_t* bytes_out) {
+  if (!c || !bytes_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (n_lags < 1 || n_k < 1) return set_error(FLB_EINVAL, "n_lags and n_k must be >= 1");
+  *bytes_out = (size_t)time_corr_layout(c, n_lags, n_k, nullptr, nullptr, nullptr);
+  return FLB_OK;
+}
+
+int flb_set_time_correlator(flb_ctx* c, int n_lags, int n_k, const int32_t* kx, const int32_t* ky, void* buf_dev,
+                            size_t bytes) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "time correlator");
+  if (rc) return rc;
+  drop_graphs(c);
+  if (n_lags == 0) {                           // off
+    c->tc = TimeCorr{};
+    return FLB_OK;
+  }
+  if (n_lags < 1 || n_lags > 65536) return set_error(FLB_EINVAL, "n_lags must be in 1..65536 (0 = off)");
+  if (n_k < 1 || n_k > 4096 || !kx || !ky) return set_error(FLB_EINVAL, "need 1..4096 wave vectors");
+  if (!buf_dev || (reinterpret_cast<uintptr_t>(buf_dev) & 255)) return set_error(FLB_EINVAL, "buf_dev must be 256-B aligned");
+  for (int r = 0; r < c->n; ++r) {
+    const ReplicaDesc& d = c->L.desc[r];
+    if (!d.n_fields) return set_error(FLB_EINVAL, "replica %d samples no fields", r);
+    for (int j = 0; j < n_k; ++j) {
+      if (kx[j] < 0 || kx[j] > d.nx / 2 || ky[j] < 0 || ky[j] >= d.ny)
+        return set_error(FLB_EINVAL, "wave vector %d = (%d, %d) outside replica %d's half spectrum", j, kx[j], ky[j], r);
+      if (kx[j] == 0 && ky[j] == 0) return set_error(FLB_EINVAL, "wave vector %d is k = 0", j);
+    }
+  }
+  std::vector<int64_t> ring(c->n), sums(c->n);
+  int64_t sums0 = 0;
+  const int64_t need = time_corr_layout(c, n_lags, n_k, &ring, &sums, &sums0);
+  if ((int64_t)bytes < need) return set_error(FLB_EINVAL, "buffer of %zu bytes, need %lld", bytes, (long long)need);
+  char* base = static_cast<char*>(buf_dev);
+  const int64_t okx = align256(8 * (int64_t)c->n), oky = align256(okx + 4 * (int64_t)n_k);
+  rc = cuda_check(cudaMemcpy(base + okx, kx, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
+  if (!rc) rc = cuda_check(cudaMemcpy(base + oky, ky, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
+  if (!rc) rc = cuda_check(cudaMemset(base, 0, 8 * (size_t)c->n), "zero counts");
+  if (!rc) rc = cuda_check(cudaMemset(base + sums0, 0, (size_t)(need - sums0)), "zero sums");
+  if (rc) return rc;
+  for (int r = 0; r < c->n; ++r) { c->L.desc[r].off_tc_ring = ring[r]; c->L.desc[r].off_tc_sums = sums[r]; }
+  rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
+                             cudaMemcpyHostToDevice), "copy descriptors");
+  if (rc) return rc;
+  c->tc.base = base;
+  c->tc.n_lags = n_lags;
+  c->tc.n_k = n_k;
+  c->tc.kx = reinterpret_cast<const int32_t*>(base + okx);
+  c->tc.ky = reinterpret_cast<const int32_t*>(base + oky);
+  c->tc.count = reinterpret_cast<uint64_t*>(base);
+  c->tc_off_sums0 = sums0;
+  c->tc_bytes = need;
+  return FLB_OK;
+}
+
+int flb_get_time_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out, uint64_t* n_samples) {
+  if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (!c->tc.base) return set_error(FLB_ESTATE, "time correlators are off");
+  if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
+  const ReplicaDesc& d = c->L.desc[replica];
+  int sa = -1, sb = -1;
+  for (int s = 0; s < (int)d.n_fields; ++s) { if (d.field_id[s] == fa) sa = s; if (d.field_id[s] == fb) sb = s; }
+  if (sa < 0 || sb < 0) return set_error(FLB_EINVAL, "fields %d, %d are not both sampled", fa, fb);
+  int rc = flb_sync(c);
+  if (rc) return rc;
+  uint64_t cnt = 0;
+  rc = cuda_check(cudaMemcpy(&cnt, c->tc.count + replica, 8, cudaMemcpyDeviceToHost), "read count");
+  if (rc) return rc;
+  const int T = c->tc.n_lags, nk = c->tc.n_k, F = (int)d.n_fields;
+  std::vector<double> sums((size_t)T * F * F * nk * 2);
+  rc = cuda_check(cudaMemcpy(sums.data(), c->tc.base + d.off_tc_sums, sums.size() * 8, cudaMemcpyDeviceToHost),
+                  "read sums");
+  if (rc) return rc;
+  auto var = [&](int f) { return f < 9 ? d.mu * d.rho0 : d.kT / d.rho0; };
+  const double vv = var(fa) * var(fb);
+  const double V = (double)d.nx * d.ny;
+  const double norm = vv > 0 ? 1.0 / (V * std::sqrt(vv)) : 1.0 / V;
+  for (int tau = 0; tau < T; ++tau)
+    for (int j = 0; j < nk; ++j) {
+      const size_t i = (((size_t)tau * F + sa) * F + sb) * nk + j;
+      const double n_tau = cnt > (uint64_t)tau ? (double)(cnt - (uint64_t)tau) : 0.0;
+      host_out[2 * ((size_t)tau * nk + j)] = n_tau > 0 ? sums[2 * i] / n_tau * norm : NAN;
+      host_out[2 * ((size_t)tau * nk + j) + 1] = n_tau > 0 ? sums[2 * i + 1] / n_tau * norm : NAN;
+    }
+  if (n_samples) *n_samples = cnt;
+  return FLB_OK;
+}
+
 
 const char* flb_last_error(void) { return g_last_error.c_str(); }
 
@@ -520,7 +641,12 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
       launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
                         L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st);
     launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
-                    L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st);
+                    L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st, c->tc);
+    if (c->tc.base) {
+      int maxF = 0;
+      for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
+      launch_time_corr(S.descs, c->n, maxF, c->tc, st);
+    }
   }
 }
 

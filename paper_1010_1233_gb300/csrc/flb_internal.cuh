@@ -53,6 +53,7 @@ struct ReplicaDesc {
   int32_t half_nx;                  // nx / 2 + 1
   int32_t wpitch;                   // pitch (complex elements) of spec rows
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
+  int64_t off_tc_ring, off_tc_sums; // time correlators: offsets in the TimeCorr buffer (see TimeCorr)
   int32_t acc_ncol;                 // pair-sum layout: 0 = [ky][kx]; c > 0 = blocked in the order
                                     // the column pass produces the points: [k1][kx / c][k2][kx % c]
                                     // (ky = k1 + N1 k2; kx padded to a multiple of c)
@@ -129,6 +130,18 @@ template <typename T> struct cplx { T x, y; };
 template <typename T> struct vec2_of;
 template <> struct vec2_of<float> { using type = float2; };
 template <> struct vec2_of<double> { using type = double2; };
+
+// Time correlators at selected wave vectors (caller-owned device buffer; base = nullptr
+// when off).  Per replica r with F sampled fields: the last n_lags samples of X_f(k_j)
+// in a ring [n_lags][F][n_k] (double2) at base + off_tc_ring, slot = sample % n_lags, and
+// the sums of X_a(k, s) X_b(k, s - tau)^* at base + off_tc_sums, [n_lags][F][F][n_k].
+struct TimeCorr {
+  char* base = nullptr;
+  int n_lags = 0, n_k = 0;
+  const int32_t* kx = nullptr;      // [n_k], 0 <= kx <= nx/2
+  const int32_t* ky = nullptr;      // [n_k], 0 <= ky < ny
+  uint64_t* count = nullptr;        // [n_replicas]: samples written so far
+};
 
 // Arguments of one step launch (lb_step.cu).
 struct StepLaunch {

@@ -12,6 +12,7 @@
 // ky = k1 + N1 k2:  X(ky) = sum_y2 W_N2^(y2 k2) W_N^(y2 k1) sum_y1 W_N1^(y1 k1) x(y);
 // pass 2a does the inner length-N1 transforms and the W_N^(y2 k1) twiddle in
 // place (rows N2 y1 + y2 -> N2 k1 + y2), pass 2b the outer length-N2 transforms.
+#include <algorithm>
 #include "flb_internal.cuh"
 
 namespace flb {
@@ -251,7 +252,7 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
 // One-pass columns are the case N1 = 1.
 template <typename R>
 __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
-                               int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol) {
+                               int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol, TimeCorr tc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* s = reinterpret_cast<C<R>*>(smem_raw);
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
@@ -336,6 +337,18 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
         }
       }
     }
+    // time correlators: this sample's X_f(k_j) of the selected wave vectors in this tile
+    if (tc.base) {
+      const int slot = (int)(tc.count[r] % (uint64_t)tc.n_lags);
+      double2* ring = reinterpret_cast<double2*>(tc.base + d.off_tc_ring);
+      for (int i = threadIdx.x; i < tc.n_k * F; i += blockDim.x) {
+        const int j = i % tc.n_k, f = i / tc.n_k;
+        const int kx = tc.kx[j], ky = tc.ky[j];
+        if ((ky & (n1 - 1)) != k1 || kx < kx0 || kx >= kx0 + ncl) continue;
+        const C<R> X = s[(f * ncol + (kx - kx0)) * (n2 + 1) + (ky >> logn1)];
+        ring[((int64_t)slot * F + f) * tc.n_k + j] = make_double2((double)X.x, (double)X.y);
+      }
+    }
     // k = 0 sums for the mean subtraction
     if (k1 == 0 && kx0 == 0 && threadIdx.x == 0) {
       double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
@@ -343,6 +356,39 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
     }
     __syncthreads();
   }
+}
+
+// Time correlators, after the column pass of a sample: sums[tau][a][b][j] +=
+// X_a(k_j, s) X_b(k_j, s - tau)^* for every lag with a sample s - tau in the ring
+// (s = count), then (k_time_corr_advance) count += 1.  One item per (tau, a, b, j);
+// blockIdx.y is the replica.
+__global__ void k_time_corr(const ReplicaDesc* __restrict__ descs, TimeCorr tc) {
+  const int r = blockIdx.y;
+  const ReplicaDesc& d = descs[r];
+  const int F = (int)d.n_fields, T = tc.n_lags, nk = tc.n_k;
+  const uint64_t cnt = tc.count[r];
+  const int slot = (int)(cnt % (uint64_t)T);
+  const double2* ring = reinterpret_cast<const double2*>(tc.base + d.off_tc_ring);
+  double2* sums = reinterpret_cast<double2*>(tc.base + d.off_tc_sums);
+  const int64_t items = (int64_t)T * F * F * nk;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(it % nk);
+    const int64_t rest = it / nk;
+    const int b = (int)(rest % F), a = (int)((rest / F) % F), tau = (int)(rest / ((int64_t)F * F));
+    if ((uint64_t)tau > cnt) continue;                         // no sample s - tau yet
+    const int old = (slot - tau + T) % T;
+    const double2 xa = ring[((int64_t)slot * F + a) * nk + j];
+    const double2 xb = ring[((int64_t)old * F + b) * nk + j];
+    double2 v = sums[it];
+    v.x += xa.x * xb.x + xa.y * xb.y;                          // X_a X_b^*
+    v.y += xa.y * xb.x - xa.x * xb.y;
+    sums[it] = v;
+  }
+}
+
+__global__ void k_time_corr_advance(TimeCorr tc, int n_reps) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n_reps) tc.count[r] += 1;
 }
 
 template <typename R>
@@ -396,11 +442,19 @@ void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* v
 }
 
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st) {
+                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                     const TimeCorr& tc) {
   if (precision == FLB_FP64)
-    k_fft_cols_acc<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
+    k_fft_cols_acc<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
   else
-    k_fft_cols_acc<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
+    k_fft_cols_acc<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
+}
+
+void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st) {
+  const int64_t items = (int64_t)tc.n_lags * max_fields * max_fields * tc.n_k;
+  const int gx = (int)std::min<int64_t>((items + 255) / 256, 4096);
+  k_time_corr<<<dim3(gx, n_reps), 256, 0, st>>>(descs, tc);
+  k_time_corr_advance<<<(n_reps + 127) / 128, 128, 0, st>>>(tc, n_reps);
 }
 
 }  // namespace flb

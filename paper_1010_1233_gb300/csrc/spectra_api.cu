@@ -17,7 +17,8 @@ cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+                     int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                     const TimeCorr& tc);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
 
@@ -114,7 +115,8 @@ int spectra_launch(int precision, SpectraPlan& P, char* scratch, const void* fie
     launch_fft_cols_a(precision, ddesc, vb + 1, 1, P.n_vb_cols_a, scratch, P.ncol, ga, kColsBlock, P.cols_smem, st);
   }
   const int gc = (int)std::min<int64_t>(P.n_vb_cols, (int64_t)sms * 8);
-  launch_fft_cols(precision, ddesc, vb + 2, 1, P.n_vb_cols, scratch, P.ncol, gc, kColsBlock, P.cols_smem, st);
+  launch_fft_cols(precision, ddesc, vb + 2, 1, P.n_vb_cols, scratch, P.ncol, gc, kColsBlock, P.cols_smem, st,
+                  TimeCorr{});
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FLB_ECUDA, "spectra launch: %s", cudaGetErrorString(e));
   return FLB_OK;

@@ -60,6 +60,7 @@ class Sim:
         self.device = torch.device(device or "cuda")
         self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device=self.device)
         self.stream = stream or torch.cuda.current_stream(self.device)
+        self._tc = None                      # time-correlator buffer (set_time_correlator)
         ctx = ctypes.c_void_p()
         L.check(lib.flb_create(_PREC[precision], arr, n, ctypes.c_void_p(self.workspace.data_ptr()),
                                self.workspace.numel(), ctypes.c_void_p(self.stream.cuda_stream),
@@ -147,6 +148,36 @@ class Sim:
         b = np.ascontiguousarray(b, dtype=np.float32)
         L.check(lib.flb_set_mlp(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
                                 b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    # -- time correlators -------------------------------------------------
+    def set_time_correlator(self, kpoints, n_lags):
+        """Accumulate F_ab(k, tau) at the wave vectors kpoints = [(ky, kx), ...] for lags
+        0..n_lags-1 (samples); n_lags = 0 switches them off."""
+        lib = L.lib()
+        if n_lags == 0:
+            L.check(lib.flb_set_time_correlator(self._ctx, 0, 0, None, None, None, 0))
+            self._tc = None
+            return
+        ky = np.ascontiguousarray([k[0] for k in kpoints], dtype=np.int32)
+        kx = np.ascontiguousarray([k[1] for k in kpoints], dtype=np.int32)
+        n = ctypes.c_size_t()
+        L.check(lib.flb_time_correlator_bytes(self._ctx, int(n_lags), len(kx), ctypes.byref(n)))
+        buf = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
+        off = (-buf.data_ptr()) % 256
+        L.check(lib.flb_set_time_correlator(self._ctx, int(n_lags), len(kx), kx.ctypes.data, ky.ctypes.data,
+                                            ctypes.c_void_p(buf.data_ptr() + off), int(n.value)))
+        self._tc = (buf, int(n_lags), len(kx))
+
+    def time_correlator(self, r, a, b, with_count=False):
+        """Normalised F_ab(k, tau) of replica r, complex (n_lags, n_k)."""
+        _, T, nk = self._tc
+        out = np.empty(2 * T * nk)
+        cnt = ctypes.c_uint64()
+        L.check(L.lib().flb_get_time_correlator(self._ctx, int(r), int(a), int(b),
+                                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                ctypes.byref(cnt)))
+        v = out[0::2].reshape(T, nk) + 1j * out[1::2].reshape(T, nk)
+        return (v, int(cnt.value)) if with_count else v
 
     # -- launch configuration ---------------------------------------------
     def set_step_config(self, vec, grid_blocks=0, staged=0):
