@@ -20,7 +20,8 @@ Readings where the paper is silent or unit-specific:
 * Temperature: Eq. 8 is written in units with k_B T = c_s^2 = 1/3.  With a
   general k_B T the equal-time moment covariance of Eq. 7 is mu rho0 delta^ab
   with mu = 3 k_B T, so the amplitude becomes (1/tau) sqrt(mu rho0 (2 tau - 1)).
-* rho-bar in Eq. 8 is the fixed mean density rho0.
+* rho-bar in Eq. 8 is the fixed mean density rho0 (noise_mode 2: the site's own
+  density rho(x), the local form of the amplitude).
 * Fields are sampled on the pre-collision state of step t (after streaming).
 * s_a = 1 unless a per-site noise-scale network is given (learned extension,
   not in the paper): s_a = 1 + o_a(u_x, u_y, rho - rho0), see ``oracle.mlp``.
@@ -65,7 +66,7 @@ class Params:
     fields: Sequence[int] = field(default_factory=list)
     mlp: Optional[dict] = None               # {"W1","b1","W2","b2","W3","b3"} FP64 arrays
     mlp_bf16: bool = False                   # round network operands to bfloat16 (tensor-core precision)
-    noise_mode: int = 0                      # 0: independent noise (Eq. 8); 1: correlated (oracle.correlated)
+    noise_mode: int = 0                      # 0: Eq. 8; 1: correlated (oracle.correlated); 2: Eq. 8 with the local rho
 
     @property
     def lat(self):
@@ -202,9 +203,11 @@ def collide(p, f, t, return_parts=False, sites=None):
             for c, a in enumerate(lat.nonconserved):
                 xi[a] = s[a] * Z[c]
         else:
+            # Eq. 8 with rho-bar = rho0, or with the local density (noise_mode 2)
+            rho_n = rho if p.noise_mode == 2 else p.rho0
             for c, a in enumerate(lat.nonconserved):
                 if (mask >> a) & 1:
-                    amp = np.sqrt(p.mu * p.rho0 * (2.0 * tau[a] - 1.0)) / tau[a]   # Eq. 8
+                    amp = np.sqrt(p.mu * rho_n * (2.0 * tau[a] - 1.0)) / tau[a]   # Eq. 8
                     xi[a] = s[a] * amp * N[c]
     Mp = M.copy()
     for a in lat.nonconserved:

@@ -43,8 +43,8 @@ def replica(lattice=D2Q9, nx=16, ny=16, tau=None, rho0=1.0, kT=1e-4, u0=(0.0, 0.
             seed=0, stream=0, noise_mask=None, init_mode=0, fields=(), noise_mode=0):
     """One replica's parameters as a plain dict (keys shared by both sides).
 
-    noise_mode 0: independent noise per non-conserved moment; 1: correlated noise
-    for the mean velocity u0."""
+    noise_mode 0: independent noise per non-conserved moment (Eq. 8); 1: correlated
+    noise for the mean velocity u0; 2: Eq. 8 with the local density."""
     if tau is None:
         tau = taus_d2q9(1.0) if lattice == D2Q9 else taus_d1q3(1.0)
     return dict(lattice=lattice, nx=int(nx), ny=int(ny if lattice == D2Q9 else 1),
