@@ -83,7 +83,9 @@ typedef struct {
                            masked non-conserved moments; xi = R N with R the
                            principal square root of its positive part (computed
                            once per replica on the host).  At u0 = 0 it equals
-                           mode 0                                               */
+                           mode 0.
+                           2: Eq. 8 with the local density rho(x) of the site in
+                           place of rho-bar (the amplitude times sqrt(rho/rho0)) */
 } flb_replica;
 
 typedef struct flb_ctx flb_ctx;

@@ -106,7 +106,7 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.noise_mask & ((1u << nc0) - 1)) return set_error(FLB_EINVAL, "replica %d: noise on a conserved moment", r);
     if (p.noise_mask >> q) return set_error(FLB_EINVAL, "replica %d: noise_mask has bits beyond moment %d", r, q - 1);
     if (p.init_mode > 1) return set_error(FLB_EINVAL, "replica %d: init_mode must be 0 or 1", r);
-    if (p.noise_mode > 1) return set_error(FLB_EINVAL, "replica %d: noise_mode must be 0 or 1", r);
+    if (p.noise_mode > 2) return set_error(FLB_EINVAL, "replica %d: noise_mode must be 0, 1 or 2", r);
     for (int f = 0; f < 32; ++f)
       if (((p.field_mask >> f) & 1) && !field_valid(lat, f))
         return set_error(FLB_EINVAL, "replica %d: field %d not available on this lattice", r, f);

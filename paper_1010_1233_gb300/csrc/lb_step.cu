@@ -113,6 +113,7 @@ k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
       const uint4 w = philox4x32_10((uint32_t)x, step, 0u, d.stream, d.seed_lo, d.seed_hi);
       R n0, n1;
       box_muller(w.x, w.y, n0, n1);
+      if (d.noise_mode == 2) n0 *= sqrt(rho / coef<R>(d, kCoRho0));    // local density in Eq. 8
       D2 += coef<R>(d, kCoAmp + 2) * n0;
     }
     dst[x] = g0 - (R)(2.0 / 3.0) * IS2 * D2;

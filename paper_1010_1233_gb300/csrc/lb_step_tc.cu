@@ -130,7 +130,7 @@ k_step_d2q9_tc(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Re
       R g[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = f[i][v];
-      collide_apply<R>(d, g, noisy, nrm[v], sc[v], Drel[v]);
+      collide_apply<R, DEV>(d, g, sum[v], noisy, nrm[v], sc[v], Drel[v]);
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i][v] = g[i];
     }

@@ -180,8 +180,9 @@ __device__ __forceinline__ void normals_d2q9(const ReplicaDesc& d, uint32_t site
 // Collision of one site (Eqs. 5, 8, 10), in two parts.  collide_relax: the non-conserved
 // moments M^3..M^8 of Eq. 9, relaxed towards the equilibrium moments of Eq. 10 at rates
 // 1/tau^a: D[a - 3] = Delta M^a (and the sampled fields of the pre-collision state when
-// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a (or, for correlated noise,
-// xi^a = s_a sum_c R_ac N^c) and the back transform
+// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a (noise mode 2: amp_a with the local
+// density rho in place of rho0; mode 1, correlated noise: xi^a = s_a sum_c R_ac N^c) and
+// the back transform
 // sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a, in place.
 template <typename R, bool DEV, bool SAMPLE>
 __device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)[9], R sum, R ux, R uy, R (&D)[6],
@@ -219,12 +220,12 @@ __device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)
   D[5] = -M8 * coef<R>(d, kCoInvTau + 8);
 }
 
-template <typename R>
-__device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], bool noisy, const R (&n)[6],
+template <typename R, bool DEV>
+__device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], R sum, bool noisy, const R (&n)[6],
                                               const R (&sc)[6], const R (&Drel)[6]) {
   const R S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
   R D3 = Drel[0], D4 = Drel[1], D5 = Drel[2], D6 = Drel[3], D7 = Drel[4], D8 = Drel[5];
-  if (noisy && d.noise_mode) {                   // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
+  if (noisy && d.noise_mode == 1) {              // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
     R z[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -240,12 +241,18 @@ __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], b
     D7 += sc[4] * z[4];
     D8 += sc[5] * z[5];
   } else if (noisy) {                            // Eq. 8, scaled per moment by s
-    D3 += sc[0] * coef<R>(d, kCoAmp + 3) * n[0];
-    D4 += sc[1] * coef<R>(d, kCoAmp + 4) * n[1];
-    D5 += sc[2] * coef<R>(d, kCoAmp + 5) * n[2];
-    D6 += sc[3] * coef<R>(d, kCoAmp + 6) * n[3];
-    D7 += sc[4] * coef<R>(d, kCoAmp + 7) * n[4];
-    D8 += sc[5] * coef<R>(d, kCoAmp + 8) * n[5];
+    R s0 = sc[0], s1 = sc[1], s2 = sc[2], s3 = sc[3], s4 = sc[4], s5 = sc[5];
+    if (d.noise_mode == 2) {                     // local density in Eq. 8: amp * sqrt(rho / rho0)
+      const R rho0 = coef<R>(d, kCoRho0);
+      const R fac = sqrt((DEV ? rho0 + sum : sum) / rho0);
+      s0 *= fac; s1 *= fac; s2 *= fac; s3 *= fac; s4 *= fac; s5 *= fac;
+    }
+    D3 += s0 * coef<R>(d, kCoAmp + 3) * n[0];
+    D4 += s1 * coef<R>(d, kCoAmp + 4) * n[1];
+    D5 += s2 * coef<R>(d, kCoAmp + 5) * n[2];
+    D6 += s3 * coef<R>(d, kCoAmp + 6) * n[3];
+    D7 += s4 * coef<R>(d, kCoAmp + 7) * n[4];
+    D8 += s5 * coef<R>(d, kCoAmp + 8) * n[5];
   }
   // back transform of the moment change, n_i^a = w_i m_i^a
   const R w1 = (R)1 / (R)9, w5 = (R)1 / (R)36;
@@ -271,7 +278,7 @@ __device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R 
                                              const R (&n)[6], const R (&sc)[6], R (&fld)[kMaxFields]) {
   R D[6];
   collide_relax<R, DEV, SAMPLE>(d, g, sum, ux, uy, D, fld);
-  collide_apply<R>(d, g, noisy, n, sc, D);
+  collide_apply<R, DEV>(d, g, sum, noisy, n, sc, D);
 }
 
 // Store the post-collision populations (and the sampled fields) of a thread's sites.
