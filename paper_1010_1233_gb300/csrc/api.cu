@@ -666,6 +666,7 @@ static StepLaunch step_launch(flb_ctx* c) {
   S.status = status_dev(c);
   S.sms = c->sms;
   S.desc0 = &L.desc[0];
+  for (const ReplicaDesc& d : L.desc) S.noise_general = S.noise_general || d.noise_mode != 0;
   return S;
 }
 
@@ -1102,6 +1103,7 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
       S.status = status_dev(c);
       S.sms = c->sms;
       S.desc0 = &c->L.desc[0];
+      for (const ReplicaDesc& d : c->L.desc) S.noise_general = S.noise_general || d.noise_mode != 0;
       auto launch = [&] {
         if (staged) launch_step_bulk(vec, S, false, c->mlp_on, c->stream);
         else launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);

@@ -151,7 +151,12 @@ struct StepLaunch {
   DevStatus* status = nullptr;          // where a kernel reports a bounded wait that gave up
   int sms = 0;                          // multiprocessors of the device
   const ReplicaDesc* desc0 = nullptr;   // host copy of descs[0] (kernel argument of one-replica launches)
+  bool noise_general = false;           // some replica uses noise mode 1 or 2
+  // kernel flavour: 0 = one replica, noise mode 0; 1 = one replica, any mode; 2 = batched
+  int flavor() const { return n_reps > 1 ? 2 : (noise_general ? 1 : 0); }
 };
+// flavour -> (descriptor in the constant bank, noise modes 1/2 compiled)
+template <int FL> struct Flavor { static constexpr bool kOne = FL != 2, kGen = FL != 0; };
 
 // Shared-memory budget of the column transforms and their split rule: one pass of
 // length ny when F columns of 4 fit the budget, else ny = N1 * N2 with

@@ -23,11 +23,12 @@ namespace flb {
 // a persistent grid loops over virtual blocks of kStepThreads units, each within one replica.
 // ONE: a single replica, whose description is the kernel argument `one` (read through
 // the constant bank) instead of descs[0] in global memory.
-template <typename R, bool DEV, int VEC, bool SAMPLE, bool ONE>
+template <typename R, bool DEV, int VEC, bool SAMPLE, int FL>
 __global__ void __launch_bounds__(kStepThreads, FLB_STEP_MINB_PLAIN)
 k_step_d2q9(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
             const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_vblocks, char* __restrict__ ws, int parity,
             uint32_t step, const uint64_t* __restrict__ step_dev) {
+  constexpr bool ONE = Flavor<FL>::kOne;
   if (step_dev) {                  // graph replay: step = device base + offset
     const uint64_t t = *step_dev + step;
     step = (uint32_t)t;
@@ -56,7 +57,7 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repli
       const R one[6] = {(R)1, (R)1, (R)1, (R)1, (R)1, (R)1};
       if (noisy) normals_d2q9<R>(d, (uint32_t)u.y * (uint32_t)d.nx + (uint32_t)(u.x0 + s), step, n);
       R fl[kMaxFields];
-      collide_d2q9<R, DEV, SAMPLE>(d, g, sum, ux, uy, noisy, n, one, fl);
+      collide_d2q9<R, DEV, SAMPLE, Flavor<FL>::kGen>(d, g, sum, ux, uy, noisy, n, one, fl);
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i][s] = g[i];
       if constexpr (SAMPLE) {
@@ -288,10 +289,12 @@ static void launch_d2q9_vec(const StepLaunch& L, bool sample, bool mlp, cudaStre
   if constexpr (sizeof(R) == 4) {
     if (mlp) { launch_step_tc(VEC, L, sample, st); return; }
   }
-#define FLB_L(S, O) k_step_d2q9<R, DEV, VEC, S, O><<<L.grid, kStepThreads, 0, st>>>( \
+#define FLB_L(S, F) k_step_d2q9<R, DEV, VEC, S, F><<<L.grid, kStepThreads, 0, st>>>( \
       L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, L.step_dev)
-  if (L.n_reps == 1) { if (sample) FLB_L(true, true); else FLB_L(false, true); }
-  else { if (sample) FLB_L(true, false); else FLB_L(false, false); }
+#define FLB_LF(F) { if (sample) FLB_L(true, F); else FLB_L(false, F); }
+  const int fl = L.flavor();
+  if (fl == 0) FLB_LF(0) else if (fl == 1) FLB_LF(1) else FLB_LF(2)
+#undef FLB_LF
 #undef FLB_L
 }
 

@@ -114,7 +114,7 @@ __device__ __forceinline__ void issue_tile(const ReplicaDesc& d, const TilePos& 
   }
 }
 
-template <int VEC, bool SAMPLE, bool ONE, bool NET>
+template <int VEC, bool SAMPLE, int FL, bool NET>
 __global__ void __launch_bounds__(kStepThreads, (BulkOcc<VEC, NET>::kBlocks))
 k_step_d2q9_bulk(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
                  const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_tiles, char* __restrict__ ws,
@@ -122,6 +122,7 @@ k_step_d2q9_bulk(const ReplicaDesc* __restrict__ descs, const __grid_constant__ 
                  const uint64_t* __restrict__ step_dev, DevStatus* status) {
   using G = BulkGeom<VEC>;
   using R = float;
+  constexpr bool ONE = Flavor<FL>::kOne;
   static_assert(kStepThreads == 256, "two warpgroups per block");
   constexpr uint32_t kCols = 2 * VEC * kTileCols;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -242,7 +243,7 @@ k_step_d2q9_bulk(const ReplicaDesc* __restrict__ descs, const __grid_constant__ 
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = f[i][v];
       R fl[kMaxFields];
-      collide_d2q9<R, true, SAMPLE>(d, g, sum[v], ux[v], uy[v], noisy, nrm[v], sc[v], fl);
+      collide_d2q9<R, true, SAMPLE, Flavor<FL>::kGen>(d, g, sum[v], ux[v], uy[v], noisy, nrm[v], sc[v], fl);
 #pragma unroll
       for (int i = 0; i < 9; ++i) out[i * G::HALF + 128 * v + tw] = g[i];
       if constexpr (SAMPLE) {
@@ -289,20 +290,21 @@ static void launch_bulk_vec(const StepLaunch& L, bool sample, cudaStream_t st) {
   using G = BulkGeom<VEC>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_step_d2q9_bulk<VEC, false, false, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
-    cudaFuncSetAttribute(k_step_d2q9_bulk<VEC, true, false, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
-    cudaFuncSetAttribute(k_step_d2q9_bulk<VEC, false, true, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
-    cudaFuncSetAttribute(k_step_d2q9_bulk<VEC, true, true, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem);
+#define FLB_A(S, F) cudaFuncSetAttribute(k_step_d2q9_bulk<VEC, S, F, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmem)
+    FLB_A(false, 0); FLB_A(true, 0); FLB_A(false, 1); FLB_A(true, 1); FLB_A(false, 2); FLB_A(true, 2);
+#undef FLB_A
     attr = true;
   }
   // a persistent grid of resident blocks
   int grid = L.grid;
   if (L.sms > 0) grid = (int)std::min<int64_t>((int64_t)grid, (int64_t)L.sms * BulkOcc<VEC, NET>::kBlocks);
   auto w = reinterpret_cast<const MlpWeights*>(L.mlp);
-#define FLB_L(S, O) k_step_d2q9_bulk<VEC, S, O, NET><<<grid, kStepThreads, G::kSmem, st>>>( \
+#define FLB_L(S, F) k_step_d2q9_bulk<VEC, S, F, NET><<<grid, kStepThreads, G::kSmem, st>>>( \
       L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, w, L.step_dev, L.status)
-  if (L.n_reps == 1) { if (sample) FLB_L(true, true); else FLB_L(false, true); }
-  else { if (sample) FLB_L(true, false); else FLB_L(false, false); }
+#define FLB_LF(F) { if (sample) FLB_L(true, F); else FLB_L(false, F); }
+  const int fl = L.flavor();
+  if (fl == 0) FLB_LF(0) else if (fl == 1) FLB_LF(1) else FLB_LF(2)
+#undef FLB_LF
 #undef FLB_L
 }
 

@@ -20,14 +20,14 @@ namespace flb {
 
 // ONE: a single replica, whose description is the kernel argument `one` (read through
 // the constant bank) instead of descs[0] in global memory.
-template <int VEC, bool SAMPLE, bool ONE>
+template <int VEC, bool SAMPLE, int FL>
 __global__ void __launch_bounds__(kStepThreads, TcOcc<VEC>::kMinBlocks)
 k_step_d2q9_tc(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
                const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_vblocks, char* __restrict__ ws, int parity,
                uint32_t step, const MlpWeights* __restrict__ mlp_w, const uint64_t* __restrict__ step_dev,
                DevStatus* status) {
   using R = float;
-  constexpr bool DEV = true;
+  constexpr bool DEV = true, ONE = Flavor<FL>::kOne;
   static_assert(kStepThreads == 256, "two warpgroups per block");
   constexpr uint32_t kCols = 2 * VEC * kTileCols;                    // 128, 256 or 512 columns
   __shared__ __align__(128) unsigned char sb[kBBytes];
@@ -130,7 +130,7 @@ k_step_d2q9_tc(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Re
       R g[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = f[i][v];
-      collide_apply<R, DEV>(d, g, sum[v], noisy, nrm[v], sc[v], Drel[v]);
+      collide_apply<R, DEV, Flavor<FL>::kGen>(d, g, sum[v], noisy, nrm[v], sc[v], Drel[v]);
 #pragma unroll
       for (int i = 0; i < 9; ++i) f[i][v] = g[i];
     }
@@ -150,10 +150,12 @@ static void launch_tc_vec(const StepLaunch& L, bool sample, cudaStream_t st) {
   int grid = L.grid;
   if (L.sms > 0) grid = (int)std::min<int64_t>((int64_t)grid, (int64_t)L.sms * TcOcc<VEC>::kBlocks);
   auto w = reinterpret_cast<const MlpWeights*>(L.mlp);
-#define FLB_L(S, O) k_step_d2q9_tc<VEC, S, O><<<grid, kStepThreads, 0, st>>>( \
+#define FLB_L(S, F) k_step_d2q9_tc<VEC, S, F><<<grid, kStepThreads, 0, st>>>( \
       L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, w, L.step_dev, L.status)
-  if (L.n_reps == 1) { if (sample) FLB_L(true, true); else FLB_L(false, true); }
-  else { if (sample) FLB_L(true, false); else FLB_L(false, false); }
+#define FLB_LF(F) { if (sample) FLB_L(true, F); else FLB_L(false, F); }
+  const int fl = L.flavor();
+  if (fl == 0) FLB_LF(0) else if (fl == 1) FLB_LF(1) else FLB_LF(2)
+#undef FLB_LF
 #undef FLB_L
 }
 

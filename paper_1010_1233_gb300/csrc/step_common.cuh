@@ -220,12 +220,14 @@ __device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)
   D[5] = -M8 * coef<R>(d, kCoInvTau + 8);
 }
 
-template <typename R, bool DEV>
+// GEN: the replica may use noise modes 1 and 2 (branch on d.noise_mode); without it only
+// mode 0 is compiled (the common case keeps its registers and instruction count).
+template <typename R, bool DEV, bool GEN>
 __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], R sum, bool noisy, const R (&n)[6],
                                               const R (&sc)[6], const R (&Drel)[6]) {
   const R S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
   R D3 = Drel[0], D4 = Drel[1], D5 = Drel[2], D6 = Drel[3], D7 = Drel[4], D8 = Drel[5];
-  if (noisy && d.noise_mode == 1) {              // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
+  if (GEN && noisy && d.noise_mode == 1) {              // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
     R z[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -242,7 +244,7 @@ __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], R
     D8 += sc[5] * z[5];
   } else if (noisy) {                            // Eq. 8, scaled per moment by s
     R s0 = sc[0], s1 = sc[1], s2 = sc[2], s3 = sc[3], s4 = sc[4], s5 = sc[5];
-    if (d.noise_mode == 2) {                     // local density in Eq. 8: amp * sqrt(rho / rho0)
+    if (GEN && d.noise_mode == 2) {              // local density in Eq. 8: amp * sqrt(rho / rho0)
       const R rho0 = coef<R>(d, kCoRho0);
       const R fac = sqrt((DEV ? rho0 + sum : sum) / rho0);
       s0 *= fac; s1 *= fac; s2 *= fac; s3 *= fac; s4 *= fac; s5 *= fac;
@@ -273,12 +275,12 @@ __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], R
   g[8] = g[8] + w5 * (dcom - q4 + q6 - q7);
 }
 
-template <typename R, bool DEV, bool SAMPLE>
+template <typename R, bool DEV, bool SAMPLE, bool GEN>
 __device__ __forceinline__ void collide_d2q9(const ReplicaDesc& d, R (&g)[9], R sum, R ux, R uy, bool noisy,
                                              const R (&n)[6], const R (&sc)[6], R (&fld)[kMaxFields]) {
   R D[6];
   collide_relax<R, DEV, SAMPLE>(d, g, sum, ux, uy, D, fld);
-  collide_apply<R, DEV>(d, g, sum, noisy, n, sc, D);
+  collide_apply<R, DEV, GEN>(d, g, sum, noisy, n, sc, D);
 }
 
 // Store the post-collision populations (and the sampled fields) of a thread's sites.
