@@ -32,9 +32,9 @@ ALG_BYTES_PER_SITE = 72          # FP32 deviation storage: 9 reads + 9 writes of
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per site of one launch of the dominant kernel in the tuned
 # launch configuration (direct tensor-core step kernel, vec 2): ncu capture of
-# k_step_d2q9_tc<2,0,1> on the 4096^2 case (profiles/k_step_d2q9_tc_fp32_mlp_4096.md),
+# k_step_d2q9_tc<2,0,0> on the 4096^2 case (profiles/k_step_d2q9_tc_fp32_mlp_4096.md),
 # scaled by the site count; None for any other configuration.
-TRAFFIC_PER_SITE = {(2, 0): (604066560 + 559978240) / 4096**2}
+TRAFFIC_PER_SITE = {(2, 0): (604170240 + 559957248) / 4096**2}
 
 
 def parse():
@@ -313,7 +313,8 @@ def run_ours(args):
                          "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_step_d2q9_tc (fused pull-stream/collide/noise, network on tcgen05)",
                          "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms,
-                         "launch": {"vec": tuned[0], "grid": tuned[1], "staged": tuned[2], "block": 256}},
+                         "launch": {"vec": tuned[0], "grid_blocks_requested": tuned[1], "staged": tuned[2],
+                                    "block": 256}},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,

@@ -58,6 +58,8 @@ def test_workspace_size_grows_with_lattice(lib):
     dict(fields=(0,), nx=24),                       # sampling needs powers of two
     dict(fields=(11,)),                             # unknown field
     dict(init_mode=3),
+    dict(noise_mode=3),                             # unknown noise mode
+    dict(nx=65536, ny=65536),                       # 2^32 sites
 ])
 def test_invalid_parameters_rejected(lib, bad):
     p = W.replica(nx=16, ny=16)
@@ -80,3 +82,8 @@ def test_d1q3_needs_single_row(lib):
     arr = (L.flb_replica * 1)(s)
     n = ctypes.c_size_t()
     assert lib.flb_workspace_bytes(L.FLB_FP64, arr, 1, ctypes.byref(n)) == L.FLB_EINVAL
+
+
+def test_empty_replica_list_rejected(lib):
+    n = ctypes.c_size_t()
+    assert lib.flb_workspace_bytes(L.FLB_FP32_DEV, None, 0, ctypes.byref(n)) == L.FLB_EINVAL
