@@ -19,6 +19,23 @@ namespace flb {
 
 template <typename R> using C = typename vec2_of<R>::type;
 
+// Exact widening to FP64 with integer operations (GB300's FP64 pipe is slow, and the
+// column pass is bound by it): a normal float's sign, exponent (rebiased by 1023 - 127)
+// and significand placed in the double's fields; zero and subnormal floats give a signed
+// zero (a subnormal product is below 1.2e-38 and cannot change an FP64 sum of such
+// correlators), infinities and NaN stay infinities and NaN.
+__device__ __forceinline__ double widen(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(b >> 31) << 63;
+  uint64_t bits;
+  if (e == 0u) bits = sign;
+  else if (e == 0xFFu) bits = sign | (0x7FFull << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  else bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 template <typename R> __device__ __forceinline__ C<R> cmul(C<R> a, C<R> b) {
   C<R> r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
@@ -328,11 +345,11 @@ __global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int6
         const C<R> Xb = s[(b * ncol + c) * (n2 + 1) + k2];
         // the product in the transform's precision (exact to its rounding), the sum in FP64
         if (a == b) {
-          acc[u].x += (double)(Xa.x * Xa.x + Xa.y * Xa.y);
+          acc[u].x += widen(Xa.x * Xa.x + Xa.y * Xa.y);
           reinterpret_cast<double*>(ws + d.pair_off[pr])[pt[u]] = acc[u].x;
         } else {
-          acc[u].x += (double)(Xa.x * Xb.x + Xa.y * Xb.y);     // X_a X_b^*
-          acc[u].y += (double)(Xa.y * Xb.x - Xa.x * Xb.y);
+          acc[u].x += widen(Xa.x * Xb.x + Xa.y * Xb.y);       // X_a X_b^*
+          acc[u].y += widen(Xa.y * Xb.x - Xa.x * Xb.y);
           reinterpret_cast<double2*>(ws + d.pair_off[pr])[pt[u]] = acc[u];
         }
       }
