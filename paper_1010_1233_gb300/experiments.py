@@ -56,16 +56,51 @@ def spectra_errors(sim, r, fields):
     return worst, float(np.mean(mean))
 
 
+def batched_errors(sim, steps, every, fields, batches=10, replicas=None):
+    """Run `steps` in `batches` equal batches (statistics reset in between) and return
+    (seconds, {r: (max |S - delta|, k-mean |S - delta|, max z)}) with the batch-means
+    standard error sigma_k per point: z = |mean - delta| / sigma_k over the included k
+    and all sampled pairs.  At u0 = 0, where Eq. 7 makes delta the exact answer, the z
+    values measure the method against its statistical noise."""
+    reps = range(len(sim.params)) if replicas is None else replicas
+    per = max(1, steps // batches)
+    samples = {r: {} for r in reps}
+    t = 0.0
+    for _ in range(batches):
+        sim.reset_stats()
+        t += _timed(sim, per, every)
+        for r in reps:
+            p = sim.params[r]
+            ny = p["ny"] if p["lattice"] == "D2Q9" else 1
+            km = _mask(p["lattice"], p["nx"], ny)
+            for i, a in enumerate(fields):
+                for b in fields[i:]:
+                    samples[r].setdefault((a, b), []).append(sim.correlator(r, a, b)[km])
+    out = {}
+    for r in reps:
+        worst, mean, zmax = 0.0, [], 0.0
+        for (a, b), v in samples[r].items():
+            v = np.array(v)
+            m = v.mean(0)
+            se = v.std(0, ddof=1) / np.sqrt(len(v))
+            same = (a == b) or ({a, b} == {1, 9}) or ({a, b} == {2, 10})
+            d = np.abs(m - (1.0 if same else 0.0))
+            worst = max(worst, float(d.max()))
+            mean.append(float(d.mean()))
+            zmax = max(zmax, float((d / np.maximum(se, 1e-12)).max()))
+        out[r] = (worst, float(np.mean(mean)), zmax)
+    return t, out
+
+
 def d1q3(steps=100_000, warmup=10_000, precision="fp64"):
     wl = W.d1q3_L64()
     p = wl["replicas"][0]
     sim = Sim(p, precision=precision)
     t_w = _timed(sim, warmup, 0)
-    sim.reset_stats()
-    t = _timed(sim, steps, 1)
-    mx, mean = spectra_errors(sim, 0, list(p["fields"]))
+    t, errs = batched_errors(sim, steps, 1, list(p["fields"]))
+    mx, mean, z = errs[0]
     return dict(workload="d1q3_L64", precision=precision, steps=steps, warmup=warmup, wall_s=t + t_w,
-                mlups=p["nx"] * steps / t / 1e6, max_err=mx, mean_err=mean)
+                mlups=p["nx"] * steps / t / 1e6, max_err=mx, mean_err=mean, max_z=z, batches=10)
 
 
 def d2q9_256(steps=200_000, warmup=10_000, precision="fp32", every=10):
@@ -74,12 +109,12 @@ def d2q9_256(steps=200_000, warmup=10_000, precision="fp32", every=10):
     sim = Sim(p, precision=precision)
     sim.autotune(3)
     _timed(sim, warmup, 0)
-    sim.reset_stats()
-    t = _timed(sim, steps, every)
-    mx, mean = spectra_errors(sim, 0, list(p["fields"]))
+    t, errs = batched_errors(sim, steps, every, list(p["fields"]))
+    mx, mean, z = errs[0]
     V = p["nx"] * p["ny"]
     return dict(workload="d2q9_256", precision=precision, steps=steps, sample_every=every, wall_s=t,
-                mlups=V * steps / t / 1e6, samples=steps // every, max_err=mx, mean_err=mean)
+                mlups=V * steps / t / 1e6, samples=steps // every, max_err=mx, mean_err=mean, max_z=z,
+                batches=10)
 
 
 def sweep(steps=100_000, warmup=10_000, every=10):
@@ -88,16 +123,16 @@ def sweep(steps=100_000, warmup=10_000, every=10):
     sim = Sim(reps, precision="fp32")
     vec, grid, staged, _ = sim.autotune(3)
     _timed(sim, warmup, 0)
-    sim.reset_stats()
-    t = _timed(sim, steps, every)
+    fields = list(reps[0]["fields"])
+    t, errs = batched_errors(sim, steps, every, fields)
     V = sum(p["nx"] * p["ny"] for p in reps)
     rows = []
     for r, p in enumerate(reps):
         c = sim.conserved(r)
         finite = bool(np.all(np.isfinite(c)))
-        mx, mean = spectra_errors(sim, r, list(p["fields"])) if finite else (float("nan"), float("nan"))
+        mx, mean, z = errs[r] if finite else (float("nan"),) * 3
         rows.append(dict(r=r, n=p["nx"], u0=p["u0"][0], tau_s=p["tau"][3], max_err=mx, mean_err=mean,
-                         finite=finite))
+                         max_z=z, finite=finite))
     return dict(workload="sweep64", steps=steps, sample_every=every, sites=V, wall_s=t, mlups=V * steps / t / 1e6,
                 launch=dict(vec=vec, grid=grid, staged=staged), replicas=rows)
 
