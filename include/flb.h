@@ -44,14 +44,27 @@ extern "C" {
 /* ---- lattices and storage precisions --------------------------------- */
 #define FLB_D1Q3 1          /* v = (0, +1, -1); moments rho, sqrt3 j, (3v^2-1)/sqrt2 */
 #define FLB_D2Q9 2          /* Sec. 3 velocity set and the moment matrix of Eq. 9   */
+#define FLB_D3Q15 3         /* tested in Sec. 3, tables not printed: standard D3Q15
+                               velocities and weights (2/9, 1/9, 1/72) and the
+                               orthonormal basis (Eq. 4) obtained by Gram-Schmidt of
+                               1, vx, vy, vz, vx^2 - vy^2, vx^2 + vy^2 - 2 vz^2,
+                               vx vy, vy vz, vz vx, v^2, vx v^2, vy v^2, vz v^2,
+                               vx vy vz, v^4 (moments 0-3 conserved, 4-8 shear,
+                               9 bulk, 10-14 ghosts).  Velocity order: rest,
+                               +x, -x, +y, -y, +z, -z, (1,1,1), (-1,-1,-1),
+                               (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1),
+                               (1,-1,-1).  Noise normals 0..10 (Philox calls 0..2)
+                               drive moments 4..14.                                  */
 #define FLB_FP64     0      /* full f_i in FP64, all arithmetic FP64                 */
 #define FLB_FP32_DEV 1      /* f_i - w_i rho0 stored and processed in FP32;
                                correlators accumulated in FP64                      */
 
 /* ---- sampled fields (bit f of flb_replica.field_mask) -----------------
  * f = 0..q-1 : moment M^a - M^{a,0}(rho0, u0)   (M^0 = rho, M^1,2 = sqrt3 j)
- * f = 9, 10  : u_x - u0_x, u_y - u0_y           (u = j / rho)
- * Fields are taken from the pre-collision (post-streaming) state.            */
+ * f = 9, 10  : u_x - u0_x, u_y - u0_y           (u = j / rho; not for D3Q15)
+ * Fields are taken from the pre-collision (post-streaming) state.  D3Q15
+ * samples moments only and accumulates correlators at chosen wave vectors
+ * (flb_set_time_correlator3), not on the full FFT grid.                    */
 #define FLB_FIELD_UX 9
 #define FLB_FIELD_UY 10
 #define FLB_MAX_FIELDS 11
@@ -59,14 +72,15 @@ extern "C" {
 /* One independent periodic lattice (a replica).  Several replicas with the
  * same lattice type and precision can run in one context (batched launch). */
 typedef struct {
-  int32_t  lattice;     /* FLB_D1Q3 or FLB_D2Q9                                  */
+  int32_t  lattice;     /* FLB_D1Q3, FLB_D2Q9 or FLB_D3Q15                       */
   int32_t  nx, ny;      /* lattice size; ny = 1 for D1Q3.  nx even.  Sampling
                            needs powers of two: 2 <= nx <= 16384, ny <= 16384  */
-  double   tau[9];      /* relaxation time per moment a (Eq. 5); entries of the
-                           conserved moments are ignored, the others must be > 1/2 */
+  double   tau[16];     /* relaxation time per moment a (Eq. 5), a < q; entries of
+                           the conserved moments are ignored, the others must be
+                           > 1/2                                                 */
   double   rho0;        /* mean density rho-bar (> 0)                            */
   double   kT;          /* temperature; mu = 3 kT scales the noise of Eq. 8      */
-  double   u0[2];       /* mean velocity of the initial state                    */
+  double   u0[3];       /* mean velocity of the initial state (u0[2]: D3Q15)     */
   uint64_t seed;        /* Philox key                                            */
   uint32_t stream;      /* Philox counter word 3 (replica stream id)             */
   uint32_t noise_mask;  /* bit a = noise on moment a; bits of conserved moments
@@ -85,7 +99,11 @@ typedef struct {
                            once per replica on the host).  At u0 = 0 it equals
                            mode 0.
                            2: Eq. 8 with the local density rho(x) of the site in
-                           place of rho-bar (the amplitude times sqrt(rho/rho0)) */
+                           place of rho-bar (the amplitude times sqrt(rho/rho0)).
+                           D3Q15: mode 0 only                                   */
+  int32_t  nz;          /* D3Q15: lattice depth (>= 1); 0 or 1 otherwise.  The
+                           populations are [q][nz][ny][nx], site index
+                           (z ny + y) nx + x                                    */
 } flb_replica;
 
 typedef struct flb_ctx flb_ctx;
@@ -143,9 +161,9 @@ int flb_get_populations_window(flb_ctx* ctx, int replica, int x0, int y0, int w,
  * FLB_ESTATE before the first sample.  Synchronises. */
 int flb_get_fields(flb_ctx* ctx, int replica, double* host_out);
 
-/* FP64 sums over the lattice of rho, j_x, j_y (j_y = 0 for D1Q3) of the stored
- * state; out[3].  Synchronises. */
-int flb_get_conserved(flb_ctx* ctx, int replica, double* out3);
+/* FP64 sums over the lattice of rho, j_x, j_y, j_z (zero for the components
+ * a lattice does not have) of the stored state; out[4].  Synchronises. */
+int flb_get_conserved(flb_ctx* ctx, int replica, double* out4);
 
 /* Global step counter (number of steps taken). */
 int flb_get_step(flb_ctx* ctx, uint64_t* step_out);
@@ -184,6 +202,12 @@ int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 int flb_time_correlator_bytes(flb_ctx* ctx, int n_lags, int n_k, size_t* bytes_out);
 int flb_set_time_correlator(flb_ctx* ctx, int n_lags, int n_k, const int32_t* kx, const int32_t* ky,
                             void* buf_dev, size_t bytes);
+/* Same with a third component kz (0 <= kz < nz) for D3Q15, whose transforms are
+ * direct sums over the lattice at the chosen wave vectors (no FFT grid); for
+ * D1Q3 / D2Q9 kz must be 0.  With n_lags = 1 these are the equal-time correlators
+ * C_ab(k) of Eqs. 11-12. */
+int flb_set_time_correlator3(flb_ctx* ctx, int n_lags, int n_k, const int32_t* kx, const int32_t* ky,
+                             const int32_t* kz, void* buf_dev, size_t bytes);
 int flb_get_time_correlator(flb_ctx* ctx, int replica, int field_a, int field_b, double* host_out,
                             uint64_t* n_samples);
 

@@ -36,6 +36,16 @@ void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+// D3Q15 (lb_d3q15.cu)
+void launch_step3(int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st);
+void launch_init3(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+                  double* sums, double* partial, int64_t V, cudaStream_t st);
+void launch_conserved3(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
+                       double* partial, DevStatus* status, int64_t V, cudaStream_t st);
+size_t point_dft_smem(int precision, int nx, int ny, int nz, int items);
+cudaError_t set_point_dft_smem(int precision, size_t bytes);
+void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int max_items, const char* ws,
+                      const TimeCorr& tc, size_t smem, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 
@@ -63,6 +73,20 @@ static const int kVx9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int kVy9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double kW3[3] = {2.0 / 3, 1.0 / 6, 1.0 / 6};
 static const int kVx3[3] = {0, 1, -1};
+// D3Q15: rest, +-x, +-y, +-z, then the corners in +- pairs (1,1,1), (1,1,-1), (1,-1,1), (-1,1,1)
+static const int kVx15[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+static const int kVy15[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
+static const int kVz15[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, 1, -1};
+static double lattice_weight(int q, int i) {
+  if (q == 9) return kW9[i];
+  if (q == 3) return kW3[i];
+  return i == 0 ? 2.0 / 9 : (i < 7 ? 1.0 / 9 : 1.0 / 72);
+}
+static inline int64_t volume(const ReplicaDesc& d) { return (int64_t)d.nx * d.ny * d.nz; }
+static inline int lattice_q(int lat) { return lat == FLB_D3Q15 ? 15 : (lat == FLB_D2Q9 ? 9 : 3); }
+static inline int first_nonconserved(int lat) { return lat == FLB_D3Q15 ? 4 : (lat == FLB_D2Q9 ? 3 : 2); }
+static constexpr int kMaxPointItems = 2048;    // D3Q15 direct transforms: fields x wave vectors
+static constexpr int kFeqStride = 32;          // doubles per replica: f^0_i(rho0, u0) at i, w_i rho0 at 16 + i
 
 static constexpr int kStepBlock = 256;
 
@@ -79,6 +103,7 @@ struct Layout {
 };
 
 static int field_valid(int lattice, int f) {
+  if (lattice == FLB_D3Q15) return f >= 0 && f < 15;
   if (lattice == FLB_D2Q9) return f >= 0 && f <= 10;
   return f == 0 || f == 1 || f == 2 || f == FLB_FIELD_UX;
 }
@@ -87,19 +112,25 @@ static int validate(int precision, const flb_replica* reps, int n) {
   if (precision != FLB_FP64 && precision != FLB_FP32_DEV) return set_error(FLB_EINVAL, "unknown precision %d", precision);
   if (!reps || n <= 0) return set_error(FLB_EINVAL, "need at least one replica");
   const int lat = reps[0].lattice;
-  if (lat != FLB_D1Q3 && lat != FLB_D2Q9) return set_error(FLB_EINVAL, "unknown lattice %d", lat);
+  if (lat != FLB_D1Q3 && lat != FLB_D2Q9 && lat != FLB_D3Q15) return set_error(FLB_EINVAL, "unknown lattice %d", lat);
   for (int r = 0; r < n; ++r) {
     const flb_replica& p = reps[r];
     if (p.lattice != lat) return set_error(FLB_EINVAL, "replica %d: all replicas must share the lattice type", r);
-    const int q = lat == FLB_D2Q9 ? 9 : 3;
+    const int q = lattice_q(lat);
     if (p.nx < 2 || p.nx % 2) return set_error(FLB_EINVAL, "replica %d: nx must be even and >= 2", r);
     if (lat == FLB_D1Q3 && p.ny != 1) return set_error(FLB_EINVAL, "replica %d: D1Q3 needs ny = 1", r);
-    if (lat == FLB_D2Q9 && p.ny < 1) return set_error(FLB_EINVAL, "replica %d: ny must be >= 1", r);
-    if ((int64_t)p.nx * p.ny >= (int64_t(1) << 32)) return set_error(FLB_EINVAL, "replica %d: lattice too large", r);
+    if (lat != FLB_D1Q3 && p.ny < 1) return set_error(FLB_EINVAL, "replica %d: ny must be >= 1", r);
+    if (lat == FLB_D3Q15 ? p.nz < 1 : (p.nz < 0 || p.nz > 1))
+      return set_error(FLB_EINVAL, "replica %d: nz = %d (D3Q15: >= 1; otherwise 0 or 1)", r, p.nz);
+    const int64_t V = (int64_t)p.nx * p.ny * (lat == FLB_D3Q15 ? p.nz : 1);
+    if (V >= (int64_t(1) << 32)) return set_error(FLB_EINVAL, "replica %d: lattice too large", r);
+    if (precision == FLB_FP64 && V >= (int64_t(1) << 31))
+      return set_error(FLB_EINVAL, "replica %d: lattice too large for the FP64 path", r);
     if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return set_error(FLB_EINVAL, "replica %d: rho0 must be > 0", r);
     if (!(p.kT >= 0) || !std::isfinite(p.kT)) return set_error(FLB_EINVAL, "replica %d: kT must be >= 0", r);
-    if (!std::isfinite(p.u0[0]) || !std::isfinite(p.u0[1])) return set_error(FLB_EINVAL, "replica %d: u0 not finite", r);
-    const int nc0 = lat == FLB_D2Q9 ? 3 : 2;
+    if (!std::isfinite(p.u0[0]) || !std::isfinite(p.u0[1]) || !std::isfinite(p.u0[2]))
+      return set_error(FLB_EINVAL, "replica %d: u0 not finite", r);
+    const int nc0 = first_nonconserved(lat);
     for (int a = nc0; a < q; ++a)
       if (!(p.tau[a] > 0.5) || !std::isfinite(p.tau[a]))
         return set_error(FLB_EINVAL, "replica %d: tau[%d] = %g must be > 1/2", r, a, p.tau[a]);
@@ -107,10 +138,16 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.noise_mask >> q) return set_error(FLB_EINVAL, "replica %d: noise_mask has bits beyond moment %d", r, q - 1);
     if (p.init_mode > 1) return set_error(FLB_EINVAL, "replica %d: init_mode must be 0 or 1", r);
     if (p.noise_mode > 2) return set_error(FLB_EINVAL, "replica %d: noise_mode must be 0, 1 or 2", r);
+    if (lat == FLB_D3Q15 && p.noise_mode != 0) return set_error(FLB_EINVAL, "replica %d: D3Q15 has noise_mode 0 only", r);
     for (int f = 0; f < 32; ++f)
       if (((p.field_mask >> f) & 1) && !field_valid(lat, f))
         return set_error(FLB_EINVAL, "replica %d: field %d not available on this lattice", r, f);
-    if (p.field_mask) {
+    if (p.field_mask && lat == FLB_D3Q15) {
+      if (__builtin_popcount(p.field_mask) > kMaxFields)
+        return set_error(FLB_EINVAL, "replica %d: at most %d sampled fields", r, kMaxFields);
+      if (p.nx > 4096 || p.ny > 4096 || p.nz > 4096)
+        return set_error(FLB_EINVAL, "replica %d: sampling needs nx, ny, nz <= 4096", r);
+    } else if (p.field_mask) {
       if (!is_pow2(p.nx) || !is_pow2(p.ny)) return set_error(FLB_EINVAL, "replica %d: sampling needs power-of-two nx, ny", r);
       if (fft_rows_smem(precision, p.nx) > 227 * 1024) return set_error(FLB_EINVAL, "replica %d: nx too large for the row FFT", r);
       const int F = __builtin_popcount(p.field_mask);
@@ -119,7 +156,7 @@ static int validate(int precision, const flb_replica* reps, int n) {
       if (fft_cols_smem(precision, F, len, 1) > kColsSmemBudget)
         return set_error(FLB_EINVAL, "replica %d: ny = %d too long for the column FFT with %d fields", r, p.ny, F);
     }
-    if (p.init_mode == 1 && p.kT > 0 && (int64_t)p.nx * p.ny < 2) return set_error(FLB_EINVAL, "thermal init needs V >= 2");
+    if (p.init_mode == 1 && p.kT > 0 && V < 2) return set_error(FLB_EINVAL, "thermal init needs V >= 2");
   }
   return FLB_OK;
 }
@@ -220,21 +257,29 @@ static int correlated_root(const flb_replica& p, double* out) {
 
 static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   memset(&d, 0, sizeof d);
-  const bool d2 = p.lattice == FLB_D2Q9;
+  const bool d2 = p.lattice == FLB_D2Q9, d3 = p.lattice == FLB_D3Q15;
   d.nx = p.nx; d.ny = p.ny; d.log2nx = ilog2(p.nx); d.log2ny = ilog2(p.ny);
-  d.q = d2 ? 9 : 3;
+  d.nz = d3 ? p.nz : 1;
+  d.q = lattice_q(p.lattice);
   d.seed_lo = (uint32_t)p.seed; d.seed_hi = (uint32_t)(p.seed >> 32);
   d.stream = p.stream; d.noise_mask = p.noise_mask; d.field_mask = p.field_mask;
-  d.rho0 = p.rho0; d.kT = p.kT; d.mu = 3.0 * p.kT; d.u0x = p.u0[0]; d.u0y = d2 ? p.u0[1] : 0.0;
-  const int nc0 = d2 ? 3 : 2;
+  d.rho0 = p.rho0; d.kT = p.kT; d.mu = 3.0 * p.kT; d.u0x = p.u0[0]; d.u0y = (d2 || d3) ? p.u0[1] : 0.0;
+  d.u0z = d3 ? p.u0[2] : 0.0;
+  const int nc0 = first_nonconserved(p.lattice);
   for (int a = nc0; a < d.q; ++a) {
     d.inv_tau[a] = 1.0 / p.tau[a];
     d.amp[a] = ((p.noise_mask >> a) & 1) ? std::sqrt(d.mu * p.rho0 * (2.0 * p.tau[a] - 1.0)) / p.tau[a] : 0.0;
   }
   // field reference values M^{a,0}(rho0, u0) (Eq. 10), minus rho0 on the density
   // moment in deviation storage, where the stored moment is that of f - w rho0
-  const double ux = d.u0x, uy = d.u0y, r0 = p.rho0, s3 = std::sqrt(3.0);
-  if (d2) {
+  const double ux = d.u0x, uy = d.u0y, uz = d.u0z, r0 = p.rho0, s3 = std::sqrt(3.0);
+  if (d3) {
+    // the equilibrium moments of the D3Q15 basis (lb_d3q15.cu) at (rho0, u0); ghosts 0
+    const double m[10] = {r0, s3 * r0 * ux, s3 * r0 * uy, s3 * r0 * uz, 1.5 * r0 * (ux * ux - uy * uy),
+                          0.5 * s3 * r0 * (ux * ux + uy * uy - 2 * uz * uz), 3 * r0 * ux * uy, 3 * r0 * uy * uz,
+                          3 * r0 * uz * ux, 0.5 * std::sqrt(6.0) * r0 * (ux * ux + uy * uy + uz * uz)};
+    for (int a = 0; a < 10; ++a) d.mref[a] = m[a];
+  } else if (d2) {
     const double m[9] = {r0, s3 * r0 * ux, s3 * r0 * uy, 1.5 * r0 * (ux * ux - uy * uy), 3 * r0 * ux * uy,
                          1.5 * r0 * (ux * ux + uy * uy), 0, 0, 0};
     for (int a = 0; a < 9; ++a) d.mref[a] = m[a];
@@ -243,16 +288,17 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   }
   if (precision == FLB_FP32_DEV) d.mref[0] -= r0;
   int F = 0;
-  for (int f = 0; f < kMaxFields; ++f)
+  for (int f = 0; f < 32 && F < kMaxFields; ++f)
     if ((p.field_mask >> f) & 1) d.field_id[F++] = f;
   d.n_fields = F;
   int np = 0;
-  for (int a = 0; a < F; ++a)
-    for (int b = a; b < F; ++b) { d.pair_a[np] = a; d.pair_b[np] = b; ++np; }
+  if (!d3)                     // pair sums on the FFT grid (D1Q3, D2Q9)
+    for (int a = 0; a < F; ++a)
+      for (int b = a; b < F; ++b) { d.pair_a[np] = a; d.pair_b[np] = b; ++np; }
   d.n_pairs = np;
   d.half_nx = p.nx / 2 + 1;
   d.wpitch = (d.half_nx + 1) & ~1;
-  d.log2n1 = F ? column_split(precision, F, p.ny) : 0;
+  d.log2n1 = (F && !d3) ? column_split(precision, F, p.ny) : 0;
   d.noise_mode = (int32_t)p.noise_mode;
   if (p.noise_mode == 1) {
     double R[36];
@@ -265,9 +311,9 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
     }
     (void)nr;
   }
-  d.dco[kCoRho0] = d.rho0; d.dco[kCoU0x] = d.u0x; d.dco[kCoU0y] = d.u0y;
-  for (int a = 0; a < 9; ++a) { d.dco[kCoInvTau + a] = d.inv_tau[a]; d.dco[kCoAmp + a] = d.amp[a]; }
-  for (int f = 0; f < kMaxFields; ++f) d.dco[kCoMref + f] = d.mref[f];
+  d.dco[kCoRho0] = d.rho0; d.dco[kCoU0x] = d.u0x; d.dco[kCoU0y] = d.u0y; d.dco[kCoU0z] = d.u0z;
+  for (int a = 0; a < kMaxQ; ++a) { d.dco[kCoInvTau + a] = d.inv_tau[a]; d.dco[kCoAmp + a] = d.amp[a]; }
+  for (int f = 0; f < kMaxQ; ++f) d.dco[kCoMref + f] = d.mref[f];
   for (int i = 0; i < kNumCoef; ++i) d.fco[i] = (float)d.dco[i];
 }
 
@@ -282,14 +328,14 @@ static void plan_step(int lattice, int vec, int staged, Layout& L) {
   for (size_t r = 0; r < L.desc.size(); ++r) {
     ReplicaDesc& d = L.desc[r];
     const int tile = kStepBlock * vec;
-    d.units_per_row = staged ? (d.nx + tile - 1) / tile : d.nx / (lattice == FLB_D2Q9 ? vec : 1);
+    d.units_per_row = staged ? (d.nx + tile - 1) / tile : d.nx / (lattice == FLB_D1Q3 ? 1 : vec);
     // m = ceil(2^(31+l) / upr), l = ceil(log2 upr): floor(u m / 2^(31+l)) = floor(u / upr) for u < 2^31
     int l = 0;
     while ((1LL << l) < d.units_per_row) ++l;
     const uint64_t p2 = 1ULL << (31 + l);
     d.upr_magic = (uint32_t)((p2 + (uint64_t)d.units_per_row - 1) / (uint64_t)d.units_per_row);
     d.upr_shift = 31 + l;
-    d.n_units = (int64_t)d.units_per_row * d.ny;
+    d.n_units = (int64_t)d.units_per_row * d.ny * d.nz;      // rows (y, z)
     L.vb_step[r] = L.n_vb_step;
     d.block_begin = L.n_vb_step;
     L.n_vb_step += staged ? d.n_units : (d.n_units + kStepBlock - 1) / kStepBlock;
@@ -301,13 +347,15 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   if (rc) return rc;
   const int lat = reps[0].lattice;
   const int64_t rs = precision == FLB_FP64 ? 8 : 4;
-  L.q = lat == FLB_D2Q9 ? 9 : 3;
+  L.q = lattice_q(lat);
   // vector width of the step kernel: all replicas share one launch
   L.vec = 1;
   if (precision == FLB_FP32_DEV && lat == FLB_D2Q9) {
     bool all4 = true;
     for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
     L.vec = all4 ? 4 : 2;
+  } else if (precision == FLB_FP32_DEV && lat == FLB_D3Q15) {
+    L.vec = 2;                                   // nx is even
   }
   L.desc.resize(n);
   int64_t off = 0;
@@ -315,25 +363,25 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
     fill_desc(precision, reps[r], d);
-    if (d.n_fields) {
-      L.any_fields = true;
+    if (d.n_fields) L.any_fields = true;
+    if (d.n_pairs) {
       maxF = std::max(maxF, (int)d.n_fields);
       maxlen = std::max(maxlen, std::max(1 << d.log2n1, d.ny >> d.log2n1));
       maxnx = std::max(maxnx, d.nx);
     }
   }
   // column tile width of the sampling passes (it fixes the blocked layout of the pair sums)
-  if (L.any_fields) {
+  if (maxF) {
     L.ncol = kColsMax;
     while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
   }
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
-    const int64_t V = (int64_t)d.nx * d.ny;
+    const int64_t V = volume(d);
     d.off_pop[0] = off; off = align256(off + L.q * V * rs);
     d.off_pop[1] = off; off = align256(off + L.q * V * rs);
-    if (d.n_fields) {
-      d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs);
+    if (d.n_fields) { d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs); }
+    if (d.n_pairs) {
       d.off_spec = off; off = align256(off + (int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
       d.acc_ncol = L.ncol;
       const int64_t padded_kx = (d.half_nx + L.ncol - 1) / L.ncol * L.ncol;
@@ -349,7 +397,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   }
   // virtual-block prefixes of the three launches
   L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
-  if (L.any_fields) {
+  if (maxF) {
     L.rows_smem = fft_rows_smem(precision, maxnx);
     L.rows_block = std::max(32, std::min(512, maxnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
@@ -360,7 +408,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.vb_rows[r] = L.n_vb_rows;
     L.vb_cols[r] = L.n_vb_cols;
     L.vb_cols_a[r] = L.n_vb_cols_a;
-    if (d.n_fields) {
+    if (d.n_pairs) {
       const int64_t tiles = (d.half_nx + L.ncol - 1) / L.ncol;
       L.n_vb_rows += (int64_t)((d.n_fields + 1) / 2) * d.ny;
       L.n_vb_cols += tiles << d.log2n1;                       // (k1, tile)
@@ -373,9 +421,9 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   L.off_vb_cols = off; off = align256(off + 8 * (int64_t)n);
   L.off_vb_cols_a = off; off = align256(off + 8 * (int64_t)n);
   L.off_status = off; off = align256(off + (int64_t)sizeof(DevStatus));
-  L.off_sums = off; off = align256(off + 8 * 3 * (int64_t)n);
-  L.off_partial = off; off = align256(off + 8 * 3 * (int64_t)kReduceBlocks);
-  L.off_feq0 = off; off = align256(off + 8 * 18 * (int64_t)n);
+  L.off_sums = off; off = align256(off + 8 * 4 * (int64_t)n);
+  L.off_partial = off; off = align256(off + 8 * 4 * (int64_t)kReduceBlocks);
+  L.off_feq0 = off; off = align256(off + 8 * kFeqStride * (int64_t)n);
   L.off_mlp = off; off = align256(off + (int64_t)mlp_weights_bytes());
   L.off_stepdev = off; off = align256(off + 8);
   L.total = off;
@@ -406,30 +454,31 @@ struct flb_ctx {
   std::vector<float> mlp_host;
   TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
   int64_t tc_off_sums0 = 0, tc_bytes = 0;      // start of the sums (first replica) and buffer size
+  size_t tc_smem = 0;                          // D3Q15 direct transforms: dynamic shared memory
 };
 
 static ReplicaDesc* descs_dev(flb_ctx* c) { return reinterpret_cast<ReplicaDesc*>(c->ws + c->L.off_descs); }
 static DevStatus* status_dev(flb_ctx* c) { return reinterpret_cast<DevStatus*>(c->ws + c->L.off_status); }
 
-static void feq0_host(const flb_replica& p, int precision, double out[18]) {
-  // Eq. 2 (c = 1) at (rho0, u0), and w_i rho0
-  const bool d2 = p.lattice == FLB_D2Q9;
-  const int q = d2 ? 9 : 3;
-  const double ux = p.u0[0], uy = d2 ? p.u0[1] : 0.0;
-  for (int i = 0; i < 18; ++i) out[i] = 0.0;
+static void feq0_host(const flb_replica& p, double out[kFeqStride]) {
+  // Eq. 2 (c = 1) at (rho0, u0) at [i], and w_i rho0 at [16 + i]
+  const bool d2 = p.lattice == FLB_D2Q9, d3 = p.lattice == FLB_D3Q15;
+  const int q = lattice_q(p.lattice);
+  const double ux = p.u0[0], uy = (d2 || d3) ? p.u0[1] : 0.0, uz = d3 ? p.u0[2] : 0.0;
+  for (int i = 0; i < kFeqStride; ++i) out[i] = 0.0;
   for (int i = 0; i < q; ++i) {
-    const double w = d2 ? kW9[i] : kW3[i];
-    const double cu = d2 ? kVx9[i] * ux + kVy9[i] * uy : kVx3[i] * ux;
-    out[i] = p.rho0 * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
-    out[9 + i] = w * p.rho0;
+    const double w = lattice_weight(q, i);
+    const double cu = d3 ? kVx15[i] * ux + kVy15[i] * uy + kVz15[i] * uz
+                         : (d2 ? kVx9[i] * ux + kVy9[i] * uy : kVx3[i] * ux);
+    out[i] = p.rho0 * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy + uz * uz));
+    out[16 + i] = w * p.rho0;
   }
-  (void)precision;
 }
 
 static int reset_stats_async(flb_ctx* c) {
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
-    if (!d.n_fields) continue;
+    if (!d.n_pairs) continue;
     const int64_t a0 = d.pair_off[0];
     const int64_t a1 = d.off_mean0 + 8 * (int64_t)d.n_fields;
     int rc = cuda_check(cudaMemsetAsync(c->ws + a0, 0, a1 - a0, c->stream), "reset stats");
@@ -445,16 +494,38 @@ static int reset_stats_async(flb_ctx* c) {
   return FLB_OK;
 }
 
-// Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | rings of every
-// replica | sums of every replica (contiguous, so a reset is one memset).
+// Blocks of the D3Q15 direct transforms: two per SM at most, no more than the rows, and
+// partial sums of at most 64 MB per replica.
+static int point_blocks(const flb_ctx* c, int n_k) {
+  int64_t rows = 1, maxF = 1;
+  for (const ReplicaDesc& d : c->L.desc) {
+    rows = std::max<int64_t>(rows, (int64_t)d.ny * d.nz);
+    maxF = std::max<int64_t>(maxF, d.n_fields);
+  }
+  int64_t g = std::min<int64_t>(2 * (int64_t)c->sms, rows);
+  g = std::min<int64_t>(g, std::max<int64_t>(1, (int64_t(1) << 22) / (maxF * n_k)));
+  return (int)std::max<int64_t>(g, 1);
+}
+
+// Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | kz [n_k] | rings
+// of every replica | D3Q15 block partials of every replica | sums of every replica
+// (contiguous, so a reset is one memset).
 static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vector<int64_t>* ring,
-                                std::vector<int64_t>* sums, int64_t* sums0) {
+                                std::vector<int64_t>* sums, int64_t* sums0, std::vector<int64_t>* part = nullptr) {
   int64_t off = align256(8 * (int64_t)c->n);
+  off = align256(off + 4 * (int64_t)n_k);
   off = align256(off + 4 * (int64_t)n_k);
   off = align256(off + 4 * (int64_t)n_k);
   for (int r = 0; r < c->n; ++r) {
     if (ring) (*ring)[r] = off;
     off = align256(off + 16 * (int64_t)n_lags * c->L.desc[r].n_fields * n_k);
+  }
+  if (c->lattice == FLB_D3Q15) {
+    const int G = point_blocks(c, n_k);
+    for (int r = 0; r < c->n; ++r) {
+      if (part) (*part)[r] = off;
+      off = align256(off + 16 * (int64_t)G * c->L.desc[r].n_fields * n_k);
+    }
   }
   if (sums0) *sums0 = off;
   for (int r = 0; r < c->n; ++r) {
@@ -478,6 +549,11 @@ int flb_time_correlator_bytes(flb_ctx* c, int n_lags, int n_k, size_t* bytes_out
 
 int flb_set_time_correlator(flb_ctx* c, int n_lags, int n_k, const int32_t* kx, const int32_t* ky, void* buf_dev,
                             size_t bytes) {
+  return flb_set_time_correlator3(c, n_lags, n_k, kx, ky, nullptr, buf_dev, bytes);
+}
+
+int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx, const int32_t* ky,
+                             const int32_t* kz, void* buf_dev, size_t bytes) {
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   int rc = cuda_check(cudaStreamSynchronize(c->stream), "time correlator");
   if (rc) return rc;
@@ -489,27 +565,56 @@ int flb_set_time_correlator(flb_ctx* c, int n_lags, int n_k, const int32_t* kx, 
   if (n_lags < 1 || n_lags > 65536) return set_error(FLB_EINVAL, "n_lags must be in 1..65536 (0 = off)");
   if (n_k < 1 || n_k > 4096 || !kx || !ky) return set_error(FLB_EINVAL, "need 1..4096 wave vectors");
   if (!buf_dev || (reinterpret_cast<uintptr_t>(buf_dev) & 255)) return set_error(FLB_EINVAL, "buf_dev must be 256-B aligned");
+  const bool d3 = c->lattice == FLB_D3Q15;
+  std::vector<int32_t> kzv(n_k, 0);
+  if (kz) kzv.assign(kz, kz + n_k);
+  size_t smem = 0;
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
     if (!d.n_fields) return set_error(FLB_EINVAL, "replica %d samples no fields", r);
     for (int j = 0; j < n_k; ++j) {
-      if (kx[j] < 0 || kx[j] > d.nx / 2 || ky[j] < 0 || ky[j] >= d.ny)
-        return set_error(FLB_EINVAL, "wave vector %d = (%d, %d) outside replica %d's half spectrum", j, kx[j], ky[j], r);
-      if (kx[j] == 0 && ky[j] == 0) return set_error(FLB_EINVAL, "wave vector %d is k = 0", j);
+      if (d3) {
+        if (kx[j] < 0 || kx[j] >= d.nx || ky[j] < 0 || ky[j] >= d.ny || kzv[j] < 0 || kzv[j] >= d.nz)
+          return set_error(FLB_EINVAL, "wave vector %d = (%d, %d, %d) outside replica %d's lattice", j, kx[j], ky[j],
+                           kzv[j], r);
+      } else {
+        if (kx[j] < 0 || kx[j] > d.nx / 2 || ky[j] < 0 || ky[j] >= d.ny)
+          return set_error(FLB_EINVAL, "wave vector %d = (%d, %d) outside replica %d's half spectrum", j, kx[j], ky[j], r);
+        if (kzv[j] != 0) return set_error(FLB_EINVAL, "wave vector %d: kz = %d on a lattice without z", j, kzv[j]);
+      }
+      if (kx[j] == 0 && ky[j] == 0 && kzv[j] == 0) return set_error(FLB_EINVAL, "wave vector %d is k = 0", j);
+    }
+    if (d3) {
+      const int items = (int)d.n_fields * n_k;
+      if (items > kMaxPointItems)
+        return set_error(FLB_EINVAL, "fields x wave vectors = %d > %d", items, kMaxPointItems);
+      smem = std::max(smem, point_dft_smem(c->precision, d.nx, d.ny, d.nz, items));
     }
   }
-  std::vector<int64_t> ring(c->n), sums(c->n);
+  if (d3) {
+    if (smem > 200 * 1024) return set_error(FLB_EINVAL, "direct transform needs %zu bytes of shared memory", smem);
+    rc = cuda_check(set_point_dft_smem(c->precision, smem), "transform smem");
+    if (rc) return rc;
+  }
+  std::vector<int64_t> ring(c->n), sums(c->n), part(c->n);
   int64_t sums0 = 0;
-  const int64_t need = time_corr_layout(c, n_lags, n_k, &ring, &sums, &sums0);
+  const int64_t need = time_corr_layout(c, n_lags, n_k, &ring, &sums, &sums0, &part);
   if ((int64_t)bytes < need) return set_error(FLB_EINVAL, "buffer of %zu bytes, need %lld", bytes, (long long)need);
   char* base = static_cast<char*>(buf_dev);
   const int64_t okx = align256(8 * (int64_t)c->n), oky = align256(okx + 4 * (int64_t)n_k);
+  const int64_t okz = align256(oky + 4 * (int64_t)n_k);
   rc = cuda_check(cudaMemcpy(base + okx, kx, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
   if (!rc) rc = cuda_check(cudaMemcpy(base + oky, ky, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
+  if (!rc) rc = cuda_check(cudaMemcpy(base + okz, kzv.data(), 4 * (size_t)n_k, cudaMemcpyHostToDevice),
+                           "copy wave vectors");
   if (!rc) rc = cuda_check(cudaMemset(base, 0, 8 * (size_t)c->n), "zero counts");
   if (!rc) rc = cuda_check(cudaMemset(base + sums0, 0, (size_t)(need - sums0)), "zero sums");
   if (rc) return rc;
-  for (int r = 0; r < c->n; ++r) { c->L.desc[r].off_tc_ring = ring[r]; c->L.desc[r].off_tc_sums = sums[r]; }
+  for (int r = 0; r < c->n; ++r) {
+    c->L.desc[r].off_tc_ring = ring[r];
+    c->L.desc[r].off_tc_sums = sums[r];
+    c->L.desc[r].off_tc_part = d3 ? part[r] : 0;
+  }
   rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
                              cudaMemcpyHostToDevice), "copy descriptors");
   if (rc) return rc;
@@ -518,7 +623,10 @@ int flb_set_time_correlator(flb_ctx* c, int n_lags, int n_k, const int32_t* kx, 
   c->tc.n_k = n_k;
   c->tc.kx = reinterpret_cast<const int32_t*>(base + okx);
   c->tc.ky = reinterpret_cast<const int32_t*>(base + oky);
+  c->tc.kz = reinterpret_cast<const int32_t*>(base + okz);
   c->tc.count = reinterpret_cast<uint64_t*>(base);
+  c->tc.part_blocks = d3 ? point_blocks(c, n_k) : 0;
+  c->tc_smem = smem;
   c->tc_off_sums0 = sums0;
   c->tc_bytes = need;
   return FLB_OK;
@@ -542,9 +650,10 @@ int flb_get_time_correlator(flb_ctx* c, int replica, int fa, int fb, double* hos
   rc = cuda_check(cudaMemcpy(sums.data(), c->tc.base + d.off_tc_sums, sums.size() * 8, cudaMemcpyDeviceToHost),
                   "read sums");
   if (rc) return rc;
-  auto var = [&](int f) { return f < 9 ? d.mu * d.rho0 : d.kT / d.rho0; };
+  // moments: mu rho0; velocities (D2Q9, D1Q3 field ids 9, 10): kT / rho0
+  auto var = [&](int f) { return (f < 9 || c->lattice == FLB_D3Q15) ? d.mu * d.rho0 : d.kT / d.rho0; };
   const double vv = var(fa) * var(fb);
-  const double V = (double)d.nx * d.ny;
+  const double V = (double)volume(d);
   const double norm = vv > 0 ? 1.0 / (V * std::sqrt(vv)) : 1.0 / V;
   for (int tau = 0; tau < T; ++tau)
     for (int j = 0; j < nk; ++j) {
@@ -598,21 +707,22 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_rows, Lc.vb_rows.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_cols, Lc.vb_cols.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_vb_cols_a, Lc.vb_cols_a.data(), 8 * n_replicas, cudaMemcpyHostToDevice, st), "copy vb");
-  std::vector<double> feq(18 * (size_t)n_replicas);
-  for (int r = 0; r < n_replicas; ++r) feq0_host(reps[r], precision, &feq[18 * (size_t)r]);
+  std::vector<double> feq(kFeqStride * (size_t)n_replicas);
+  for (int r = 0; r < n_replicas; ++r) feq0_host(reps[r], &feq[kFeqStride * (size_t)r]);
   if (!rc) rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_feq0, feq.data(), feq.size() * 8, cudaMemcpyHostToDevice, st), "copy feq0");
   if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + Lc.off_status, 0, sizeof(DevStatus), st), "status");
   if (!rc) rc = cuda_check(cudaMemsetAsync(c->ws + Lc.off_mlp, 0, mlp_weights_bytes(), st), "mlp");
   for (int r = 0; r < n_replicas && !rc; ++r) {
     const ReplicaDesc& d = Lc.desc[r];
-    const int64_t V = (int64_t)d.nx * d.ny;
-    double* sums = reinterpret_cast<double*>(c->ws + Lc.off_sums) + 3 * r;
-    rc = cuda_check(cudaMemsetAsync(sums, 0, 24, st), "sums");
+    const int64_t V = volume(d);
+    double* sums = reinterpret_cast<double*>(c->ws + Lc.off_sums) + 4 * r;
+    rc = cuda_check(cudaMemsetAsync(sums, 0, 32, st), "sums");
     if (rc) break;
-    launch_init(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode,
-                reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + 18 * r, sums,
-                reinterpret_cast<double*>(c->ws + Lc.off_partial), V, st);
-    if (d.n_fields) {
+    const double* feq0 = reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + kFeqStride * r;
+    double* partial = reinterpret_cast<double*>(c->ws + Lc.off_partial);
+    if (c->lattice == FLB_D3Q15) launch_init3(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode, feq0, sums, partial, V, st);
+    else launch_init(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode, feq0, sums, partial, V, st);
+    if (d.n_pairs) {
       launch_twiddles(precision, c->ws + d.off_tw_x, d.nx, st);
       launch_twiddles(precision, c->ws + d.off_tw_y, d.ny, st);
     }
@@ -627,11 +737,24 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
 
 // Issue one step (and its sampling) on stream st.  With S.step_dev set, S.step is the
 // offset from the device step counter (graph capture); otherwise the absolute step.
+static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S, bool sample, cudaStream_t st) {
+  if (c->lattice == FLB_D3Q15) launch_step3(c->precision, vec, S, sample, st);
+  else if (staged) launch_step_bulk(vec, S, sample, c->mlp_on, st);
+  else launch_step(c->lattice, c->precision, vec, S, sample, c->mlp_on, st);
+}
+
 static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
   const Layout& L = c->L;
-  if (L.staged) launch_step_bulk(L.vec, S, sample, c->mlp_on, st);
-  else launch_step(c->lattice, c->precision, L.vec, S, sample, c->mlp_on, st);
-  if (sample) {
+  launch_step_any(c, L.vec, L.staged, S, sample, st);
+  if (sample && c->lattice == FLB_D3Q15) {
+    // direct transforms at the chosen wave vectors, then the time correlators
+    if (c->tc.base) {
+      int maxF = 0;
+      for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
+      launch_point_dft(c->precision, S.descs, c->n, maxF * c->tc.n_k, c->ws, c->tc, c->tc_smem, st);
+      launch_time_corr(S.descs, c->n, maxF, c->tc, st);
+    }
+  } else if (sample) {
     const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
     const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
     const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
@@ -781,6 +904,8 @@ int flb_get_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out
   if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
+  if (c->lattice == FLB_D3Q15)
+    return set_error(FLB_EINVAL, "D3Q15 correlators are taken at chosen wave vectors (flb_set_time_correlator3)");
   int sa = -1, sb = -1;
   for (int s = 0; s < (int)d.n_fields; ++s) { if (d.field_id[s] == fa) sa = s; if (d.field_id[s] == fb) sb = s; }
   if (sa < 0 || sb < 0) return set_error(FLB_EINVAL, "fields %d, %d are not both sampled", fa, fb);
@@ -832,7 +957,7 @@ int flb_get_populations(flb_ctx* c, int replica, double* host_out) {
   int rc = flb_sync(c);
   if (rc) return rc;
   const ReplicaDesc& d = c->L.desc[replica];
-  const int64_t V = (int64_t)d.nx * d.ny;
+  const int64_t V = volume(d);
   const char* src = c->ws + d.off_pop[c->step & 1];
   if (c->precision == FLB_FP64)
     return cuda_check(cudaMemcpy(host_out, src, d.q * V * 8, cudaMemcpyDeviceToHost), "read populations");
@@ -840,7 +965,7 @@ int flb_get_populations(flb_ctx* c, int replica, double* host_out) {
   rc = cuda_check(cudaMemcpy(tmp.data(), src, tmp.size() * 4, cudaMemcpyDeviceToHost), "read populations");
   if (rc) return rc;
   for (int i = 0; i < d.q; ++i) {
-    const double wr = (d.q == 9 ? kW9[i] : kW3[i]) * d.rho0;
+    const double wr = lattice_weight(d.q, i) * d.rho0;
     for (int64_t s = 0; s < V; ++s) host_out[i * V + s] = wr + (double)tmp[i * V + s];
   }
   return FLB_OK;
@@ -850,6 +975,7 @@ int flb_get_populations_window(flb_ctx* c, int replica, int x0, int y0, int w, i
   if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
+  if (c->lattice == FLB_D3Q15) return set_error(FLB_EINVAL, "windows are read from D1Q3 / D2Q9 lattices");
   if (w <= 0 || h <= 0 || x0 < 0 || y0 < 0 || x0 + w > d.nx || y0 + h > d.ny)
     return set_error(FLB_EINVAL, "window [%d,%d)x[%d,%d) outside the %dx%d lattice", x0, x0 + w, y0, y0 + h, d.nx, d.ny);
   int rc = flb_sync(c);
@@ -883,7 +1009,7 @@ int flb_get_fields(flb_ctx* c, int replica, double* host_out) {
   if (c->n_samples == 0) return set_error(FLB_ESTATE, "no samples taken");
   int rc = flb_sync(c);
   if (rc) return rc;
-  const size_t n = (size_t)d.n_fields * d.nx * d.ny;
+  const size_t n = (size_t)d.n_fields * volume(d);
   if (c->precision == FLB_FP64)
     return cuda_check(cudaMemcpy(host_out, c->ws + d.off_fields, n * 8, cudaMemcpyDeviceToHost), "read fields");
   std::vector<float> tmp(n);
@@ -899,31 +1025,35 @@ int flb_set_populations(flb_ctx* c, int replica, const double* host_in) {
   int rc = flb_sync(c);
   if (rc) return rc;
   const ReplicaDesc& d = c->L.desc[replica];
-  const int64_t V = (int64_t)d.nx * d.ny;
+  const int64_t V = volume(d);
   char* dst = c->ws + d.off_pop[c->step & 1];
   if (c->precision == FLB_FP64)
     return cuda_check(cudaMemcpy(dst, host_in, d.q * V * 8, cudaMemcpyHostToDevice), "write populations");
   std::vector<float> tmp((size_t)d.q * V);
   for (int i = 0; i < d.q; ++i) {
-    const double wr = (d.q == 9 ? kW9[i] : kW3[i]) * d.rho0;
+    const double wr = lattice_weight(d.q, i) * d.rho0;
     for (int64_t s = 0; s < V; ++s) tmp[i * V + s] = (float)(host_in[i * V + s] - wr);
   }
   return cuda_check(cudaMemcpy(dst, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice), "write populations");
 }
 
-int flb_get_conserved(flb_ctx* c, int replica, double* out3) {
-  if (!c || !out3) return set_error(FLB_EINVAL, "NULL argument");
+int flb_get_conserved(flb_ctx* c, int replica, double* out4) {
+  if (!c || !out4) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
-  double* sums = reinterpret_cast<double*>(c->ws + c->L.off_sums) + 3 * replica;
-  launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums,
-                   reinterpret_cast<double*>(c->ws + c->L.off_partial), status_dev(c), (int64_t)d.nx * d.ny,
-                   c->stream);
+  double* sums = reinterpret_cast<double*>(c->ws + c->L.off_sums) + 4 * replica;
+  double* partial = reinterpret_cast<double*>(c->ws + c->L.off_partial);
+  if (c->lattice == FLB_D3Q15)
+    launch_conserved3(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, partial, status_dev(c),
+                      volume(d), c->stream);
+  else
+    launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, partial, status_dev(c),
+                     volume(d), c->stream);
   int rc = cuda_check(cudaGetLastError(), "conserved launch");
   if (rc) return rc;
   rc = flb_sync(c);
   if (rc) return rc;
-  return cuda_check(cudaMemcpy(out3, sums, 24, cudaMemcpyDeviceToHost), "read sums");
+  return cuda_check(cudaMemcpy(out4, sums, 32, cudaMemcpyDeviceToHost), "read sums");
 }
 
 int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int enable) {
@@ -962,8 +1092,8 @@ int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
   size_t need = 64;
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
-    need += d.q * (size_t)d.nx * d.ny * rs;
-    if (d.n_fields) need += (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
+    need += d.q * (size_t)volume(d) * rs;
+    if (d.n_pairs) need += (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
   }
   if (!host_buf) { *bytes_inout = need; return FLB_OK; }
   if (*bytes_inout < need) return set_error(FLB_EINVAL, "buffer of %zu bytes < %zu", *bytes_inout, need);
@@ -976,11 +1106,11 @@ int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
   p += 64;
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
-    const size_t pb = d.q * (size_t)d.nx * d.ny * rs;
+    const size_t pb = d.q * (size_t)volume(d) * rs;
     rc = cuda_check(cudaMemcpy(p, c->ws + d.off_pop[c->step & 1], pb, cudaMemcpyDeviceToHost), "save");
     if (rc) return rc;
     p += pb;
-    if (d.n_fields) {
+    if (d.n_pairs) {
       const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
       rc = cuda_check(cudaMemcpy(p, c->ws + d.pair_off[0], ab, cudaMemcpyDeviceToHost), "save");
       if (rc) return rc;
@@ -1010,11 +1140,11 @@ int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
   const int64_t rs = c->precision == FLB_FP64 ? 8 : 4;
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
-    const size_t pb = d.q * (size_t)d.nx * d.ny * rs;
+    const size_t pb = d.q * (size_t)volume(d) * rs;
     rc = cuda_check(cudaMemcpy(c->ws + d.off_pop[step & 1], p, pb, cudaMemcpyHostToDevice), "load");
     if (rc) return rc;
     p += pb;
-    if (d.n_fields) {
+    if (d.n_pairs) {
       const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
       rc = cuda_check(cudaMemcpy(c->ws + d.pair_off[0], p, ab, cudaMemcpyHostToDevice), "load");
       if (rc) return rc;
@@ -1038,10 +1168,14 @@ int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks, int staged) {
   if (vec != 1 && vec != 2 && vec != 4) return set_error(FLB_EINVAL, "vec must be 1, 2 or 4");
   if (staged != 0 && staged != 1) return set_error(FLB_EINVAL, "staged must be 0 or 1");
   if (staged && !staged_ok(c)) return set_error(FLB_EINVAL, "the staged kernel needs the FP32 D2Q9 path, every nx a multiple of 4");
-  if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9))
-    return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9 path");
-  for (int r = 0; r < c->n && !staged; ++r)
+  if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice == FLB_D1Q3))
+    return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9 or D3Q15 path");
+  for (int r = 0; r < c->n && !staged; ++r) {
     if (c->L.desc[r].nx % vec) return set_error(FLB_EINVAL, "replica %d: nx not a multiple of vec = %d", r, vec);
+    // one thread per site: unit indices are 32-bit
+    if (vec == 1 && volume(c->L.desc[r]) >= (int64_t(1) << 31))
+      return set_error(FLB_EINVAL, "replica %d: vec = 1 needs fewer than 2^31 sites", r);
+  }
   if (grid_blocks < 0) return set_error(FLB_EINVAL, "grid_blocks must be >= 0");
   int rc = cuda_check(cudaStreamSynchronize(c->stream), "step config");
   if (rc) return rc;
@@ -1076,10 +1210,11 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
   float best = 1e30f;
   for (int cfg = 0; cfg < 6 && !rc; ++cfg) {
     const int vec = vecs[cfg % 3], staged = cfg / 3;
-    if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice != FLB_D2Q9)) continue;
+    if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice == FLB_D1Q3)) continue;
     if (staged && !staged_ok(c)) continue;
     bool ok = true;
-    for (int r = 0; r < c->n && !staged; ++r) ok = ok && c->L.desc[r].nx % vec == 0;
+    for (int r = 0; r < c->n && !staged; ++r)
+      ok = ok && c->L.desc[r].nx % vec == 0 && (vec > 1 || volume(c->L.desc[r]) < (int64_t(1) << 31));
     if (!ok) continue;
     // the staged kernel is persistent (its launcher caps the grid at the resident blocks)
     const int mults[5] = {2, 4, 8, 16, 0};
@@ -1104,10 +1239,7 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
       S.sms = c->sms;
       S.desc0 = &c->L.desc[0];
       for (const ReplicaDesc& d : c->L.desc) S.noise_general = S.noise_general || d.noise_mode != 0;
-      auto launch = [&] {
-        if (staged) launch_step_bulk(vec, S, false, c->mlp_on, c->stream);
-        else launch_step(c->lattice, c->precision, vec, S, false, c->mlp_on, c->stream);
-      };
+      auto launch = [&] { launch_step_any(c, vec, staged, S, false, c->stream); };
       launch();
       cudaEventRecord(e0, c->stream);
       for (int t = 0; t < trials; ++t) launch();

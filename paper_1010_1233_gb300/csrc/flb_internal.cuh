@@ -20,19 +20,22 @@ constexpr int kMlpOut = 6;
 constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden;  // 1312
 constexpr int kMlpBiases = kMlpHidden + kMlpHidden + kMlpOut;                               // 70
 
-constexpr int kCoRho0 = 0, kCoU0x = 1, kCoU0y = 2, kCoInvTau = 3, kCoAmp = 12, kCoMref = 21;
-constexpr int kCoNoiseR = kCoMref + 11;      // 6 x 6 correlated-noise root (noise_mode 1), row-major
+constexpr int kMaxQ = 16;                    // moments per site (D3Q15: 15)
+constexpr int kCoRho0 = 0, kCoU0x = 1, kCoU0y = 2, kCoU0z = 3;
+constexpr int kCoInvTau = 4, kCoAmp = kCoInvTau + kMaxQ, kCoMref = kCoAmp + kMaxQ;
+constexpr int kCoNoiseR = kCoMref + kMaxQ;   // 6 x 6 correlated-noise root (noise_mode 1), row-major
 constexpr int kNumCoef = kCoNoiseR + 36;
 
 // Per-replica description, resident in device memory (one array per context).
 // Offsets are byte offsets from the workspace base.
 struct ReplicaDesc {
   int32_t nx, ny, log2nx, log2ny;
+  int32_t nz;                   // D3Q15 depth (1 otherwise); a row is (y, z), row = z ny + y
   int32_t q;
   int32_t units_per_row;        // nx / VEC of the step launch
   uint32_t upr_magic;           // row of a unit u < 2^31: (u * upr_magic) >> upr_shift
   int32_t upr_shift;            //   (Granlund & Montgomery, PLDI'94, round-up multiplier)
-  int64_t n_units;              // units_per_row * ny
+  int64_t n_units;              // units_per_row * ny * nz
   int64_t block_begin;          // first virtual block of this replica in the step launch
   uint32_t seed_lo, seed_hi, stream, noise_mask;
   int32_t noise_mode;           // 0: independent noise (Eq. 8); 1: correlated (root in kCoNoiseR)
@@ -41,12 +44,12 @@ struct ReplicaDesc {
   int32_t n_pairs;
   int32_t pair_a[kMaxPairs], pair_b[kMaxPairs];   // slot indices, a <= b
   int64_t pair_off[kMaxPairs];      // byte offset of the pair's accumulator plane
-  double rho0, kT, mu, u0x, u0y;
-  double inv_tau[9];
-  double amp[9];                    // (1/tau) sqrt(mu rho0 (2 tau - 1)), 0 when masked
-  double mref[kMaxFields];          // reference value subtracted from each field id
+  double rho0, kT, mu, u0x, u0y, u0z;
+  double inv_tau[kMaxQ];
+  double amp[kMaxQ];                // (1/tau) sqrt(mu rho0 (2 tau - 1)), 0 when masked
+  double mref[kMaxQ];               // reference value subtracted from each field id
   int64_t off_pop[2];               // population buffers (ping-pong)
-  int64_t off_fields;               // [n_fields][ny][nx] Real
+  int64_t off_fields;               // [n_fields][nz][ny][nx] Real
   int64_t off_spec;                 // [n_fields][ny][wpitch] complex Real (row-transformed)
   int64_t off_mean0;                // [n_fields] double: sum over samples of X(k=0)
   int64_t off_tw_x, off_tw_y;       // twiddles exp(-2 pi i m / n), m < n/2, complex Real
@@ -54,11 +57,12 @@ struct ReplicaDesc {
   int32_t wpitch;                   // pitch (complex elements) of spec rows
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
   int64_t off_tc_ring, off_tc_sums; // time correlators: offsets in the TimeCorr buffer (see TimeCorr)
+  int64_t off_tc_part;              // D3Q15: per-block partial transforms [blocks][F][n_k] double2
   int32_t acc_ncol;                 // pair-sum layout: 0 = [ky][kx]; c > 0 = blocked in the order
                                     // the column pass produces the points: [k1][kx / c][k2][kx % c]
                                     // (ky = k1 + N1 k2; kx padded to a multiple of c)
   // the per-replica coefficients in the arithmetic type of the path (host-filled),
-  // so the FP32 kernels never convert from FP64: [kCoRho0], [kCoU0x], [kCoU0y],
+  // so the FP32 kernels never convert from FP64: [kCoRho0], [kCoU0x .. kCoU0z],
   // [kCoInvTau + a], [kCoAmp + a], [kCoMref + field], [kCoNoiseR + 6 c + c'] (c, c' index
   // the non-conserved moments 3..8)
   float fco[kNumCoef];
@@ -140,7 +144,9 @@ struct TimeCorr {
   int n_lags = 0, n_k = 0;
   const int32_t* kx = nullptr;      // [n_k], 0 <= kx <= nx/2
   const int32_t* ky = nullptr;      // [n_k], 0 <= ky < ny
+  const int32_t* kz = nullptr;      // [n_k], 0 <= kz < nz (D3Q15; 0 otherwise)
   uint64_t* count = nullptr;        // [n_replicas]: samples written so far
+  int part_blocks = 0;              // D3Q15: blocks of the direct transform (partials per replica)
 };
 
 // Arguments of one step launch (lb_step.cu).

@@ -1,0 +1,516 @@
+// D3Q15 fluctuating lattice Boltzmann: the scheme of Sec. 2 (pull streaming, Eq. 1;
+// relaxation of the non-conserved moments, Eq. 5; noise of Eq. 8 on each of them) on
+// the three-dimensional lattice that Sec. 3 reports testing without printing its tables.
+//
+// Velocities (order of the population index i): rest, +x, -x, +y, -y, +z, -z, (1,1,1),
+// (-1,-1,-1), (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); weights
+// 2/9, 1/9 (axes), 1/72 (corners), so that sum_i w_i v_i v_i = 1/3 as in Eq. 2.
+//
+// Moments: the basis orthonormal in the weighted norm of Eq. 4 that Gram-Schmidt gives
+// from the polynomials 1, vx, vy, vz, vx^2 - vy^2, vx^2 + vy^2 - 2 vz^2, vx vy, vy vz,
+// vz vx, v^2, vx v^2, vy v^2, vz v^2, vx vy vz, v^4 in that order.  Written out:
+//   m^0 = 1, m^{1,2,3} = sqrt3 v, m^4 = 3/2 (vx^2 - vy^2), m^5 = sqrt3/2 (vx^2 + vy^2 - 2 vz^2),
+//   m^6 = 3 vx vy, m^7 = 3 vy vz, m^8 = 3 vz vx, m^9 = sqrt6/2 (v^2 - 1),
+//   m^{10,11,12} = sqrt6/4 v_a (3 v^2 - 5), m^13 = 3 vx vy vz, m^14 = sqrt2/4 (3 v^4 - 9 v^2 + 4).
+// The equilibrium moments (Eq. 10 in three dimensions) are those of f^0 of Eq. 2:
+//   M^{4..9,0} = rho (3/2 (ux^2 - uy^2), sqrt3/2 (ux^2 + uy^2 - 2 uz^2), 3 ux uy, 3 uy uz,
+//                     3 uz ux, sqrt6/2 u^2), and 0 for the ghosts 10..14 (f^0 / w is a
+//   polynomial of degree 2 in v, to which the ghost rows are orthogonal).
+// Noise: normals 0..10 of Philox calls 0..2 (counter site, step, call, stream) drive
+// moments 4..14.  Site index (z ny + y) nx + x; populations [15][nz][ny][nx].
+//
+// Sampling: the step writes the moment fields (pre-collision state, minus M^{a,0}(rho0,
+// u0)); k_point_dft forms X_f(k) = sum_x X_f(x) exp(-i k.x) (Eq. 11) at the chosen wave
+// vectors by direct summation, and the time-correlator kernels of spectra.cu accumulate
+// X_a(k, s) X_b(k, s - tau)^*.
+#include <algorithm>
+#include "step_common.cuh"
+
+#ifndef FLB_STEP3_MINB
+#define FLB_STEP3_MINB 2       // minimum resident blocks of 256 threads per SM (128 registers)
+#endif
+
+namespace flb {
+
+// velocity components of population i: 2 bits per population, value + 1
+__host__ __device__ constexpr int v3x(int i) { return (int)((0x20889549u >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int v3y(int i) { return (int)((0x0a089495u >> (2 * i)) & 3u) - 1; }
+__host__ __device__ constexpr int v3z(int i) { return (int)((0x08a08955u >> (2 * i)) & 3u) - 1; }
+static_assert(v3x(7) == 1 && v3y(7) == 1 && v3z(7) == 1, "corner (1,1,1)");
+static_assert(v3x(13) == -1 && v3y(13) == 1 && v3z(13) == 1, "corner (-1,1,1)");
+static_assert(v3x(6) == 0 && v3y(6) == 0 && v3z(6) == -1, "axis -z");
+
+__host__ __device__ constexpr double w15(int i) { return i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0); }
+
+// m_i^a of the basis above at velocity (vx, vy, vz)
+__host__ __device__ inline double moment_row3(int a, int vx, int vy, int vz) {
+  const double S2 = 1.4142135623730950488, S3 = 1.7320508075688772935, S6 = 2.4494897427831780982;
+  const double v2 = vx * vx + vy * vy + vz * vz;
+  switch (a) {
+    case 0: return 1.0;
+    case 1: return S3 * vx;
+    case 2: return S3 * vy;
+    case 3: return S3 * vz;
+    case 4: return 1.5 * (vx * vx - vy * vy);
+    case 5: return 0.5 * S3 * (vx * vx + vy * vy - 2.0 * vz * vz);
+    case 6: return 3.0 * vx * vy;
+    case 7: return 3.0 * vy * vz;
+    case 8: return 3.0 * vz * vx;
+    case 9: return 0.5 * S6 * (v2 - 1.0);
+    case 10: return 0.25 * S6 * vx * (3.0 * v2 - 5.0);
+    case 11: return 0.25 * S6 * vy * (3.0 * v2 - 5.0);
+    case 12: return 0.25 * S6 * vz * (3.0 * v2 - 5.0);
+    case 13: return 3.0 * vx * vy * vz;
+    default: return 0.25 * S2 * (3.0 * v2 * v2 - 9.0 * v2 + 4.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pull streaming f_i(x) = f*_i(x - v_i) on the periodic box: the source row of population
+// i is (y - v_iy, z - v_iz); the x shift is taken by warp shuffle from the adjacent lane,
+// with one extra load at warp and row edges (as in the D2Q9 kernels).
+template <typename R, int VEC>
+__device__ __forceinline__ void pull_d3q15(const R* __restrict__ src, int64_t vol, int nx, int ny, int nz, int y,
+                                           int z, const UnitPos& u, R (&f)[15][VEC]) {
+  R v[15][VEC], e[15];
+  const int x0 = u.x0;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    int ys = y - v3y(i), zs = z - v3z(i);
+    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+    zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+    const R* row = src + i * vol + ((int64_t)zs * ny + ys) * nx;
+    VecIO<R, VEC>::ld(row + x0, v[i]);
+    e[i] = (R)0;
+    if (v3x(i) == 1) {
+      if (!u.left_in_warp) e[i] = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
+    } else if (v3x(i) == -1) {
+      if (!u.right_in_warp) e[i] = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 15; ++i) {
+    if (v3x(i) == 0) {
+#pragma unroll
+      for (int s = 0; s < VEC; ++s) f[i][s] = v[i][s];
+    } else if (v3x(i) == 1) {
+      const R left = __shfl_up_sync(0xffffffffu, v[i][VEC - 1], 1);
+      f[i][0] = u.left_in_warp ? left : e[i];
+#pragma unroll
+      for (int s = 1; s < VEC; ++s) f[i][s] = v[i][s - 1];
+    } else {
+      const R right = __shfl_down_sync(0xffffffffu, v[i][0], 1);
+#pragma unroll
+      for (int s = 0; s < VEC - 1; ++s) f[i][s] = v[i][s + 1];
+      f[i][VEC - 1] = u.right_in_warp ? right : e[i];
+    }
+  }
+}
+
+// Collision of one site in place (Eqs. 5, 8): moments in closed form, relaxation of
+// M^4..M^14 towards the equilibrium moments, noise amp_a N_{a-4}, and the back transform
+// f*_i = f_i + w_i sum_a m_i^a Delta M^a.  fld: the 15 moments minus their reference
+// values (SAMPLE).  DEV: g holds f - w rho0 (the non-conserved moments are the same).
+template <typename R, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void collide_d3q15(const ReplicaDesc& d, R (&g)[15], bool noisy, const R (&n)[11],
+                                              R (&fld)[15]) {
+  const R S2 = (R)1.4142135623730950488, S3 = (R)1.7320508075688772935, S6 = (R)2.4494897427831780982;
+  const R hS2 = (R)0.70710678118654752440, hS3 = (R)0.86602540378443864676, hS6 = (R)1.2247448713915890491;
+  // density and momentum
+  const R s1 = g[7] + g[8], s2 = g[9] + g[10], s3 = g[11] + g[12], s4 = g[13] + g[14];
+  const R d1 = g[7] - g[8], d2 = g[9] - g[10], d3 = g[11] - g[12], d4 = g[13] - g[14];
+  const R ax = g[1] + g[2], ay = g[3] + g[4], az = g[5] + g[6];
+  const R C = (s1 + s2) + (s3 + s4);
+  const R sum = g[0] + ((ax + ay) + az) + C;
+  const R cx = (d1 + d2) + (d3 - d4), cy = (d1 + d2) - (d3 - d4), cz = (d1 - d2) + (d3 + d4);
+  const R jx = (g[1] - g[2]) + cx, jy = (g[3] - g[4]) + cy, jz = (g[5] - g[6]) + cz;
+  const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
+  const R irho = (R)1 / rho;
+  const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
+  // non-conserved moments
+  const R M4 = (R)1.5 * (ax - ay);
+  const R M5 = hS3 * ((ax + ay) - (R)2 * az);
+  const R M6 = (R)3 * ((s1 + s2) - (s3 + s4));
+  const R M7 = (R)3 * ((s1 + s4) - (s2 + s3));
+  const R M8 = (R)3 * ((s1 + s3) - (s2 + s4));
+  const R M9 = S6 * (C - (R)0.5 * g[0]);
+  const R M10 = S6 * ((R)0.5 * (g[2] - g[1]) + cx);
+  const R M11 = S6 * ((R)0.5 * (g[4] - g[3]) + cy);
+  const R M12 = S6 * ((R)0.5 * (g[6] - g[5]) + cz);
+  const R M13 = (R)3 * ((d1 - d2) - (d3 + d4));
+  const R M14 = S2 * ((g[0] - (R)0.5 * ((ax + ay) + az)) + C);
+  // equilibrium moments
+  const R E4 = (R)1.5 * (jx * ux - jy * uy);
+  const R E5 = hS3 * ((jx * ux + jy * uy) - (R)2 * jz * uz);
+  const R E6 = (R)3 * jx * uy, E7 = (R)3 * jy * uz, E8 = (R)3 * jz * ux;
+  const R E9 = hS6 * ((jx * ux + jy * uy) + jz * uz);
+  if constexpr (SAMPLE) {
+    const R mom[15] = {sum, S3 * jx, S3 * jy, S3 * jz, M4, M5, M6, M7, M8, M9, M10, M11, M12, M13, M14};
+#pragma unroll
+    for (int a = 0; a < 15; ++a) fld[a] = mom[a] - coef<R>(d, kCoMref + a);
+  }
+  // relaxation (Eq. 5) and noise (Eq. 8)
+  R D[11] = {E4 - M4, E5 - M5, E6 - M6, E7 - M7, E8 - M8, E9 - M9, -M10, -M11, -M12, -M13, -M14};
+#pragma unroll
+  for (int c = 0; c < 11; ++c) {
+    D[c] *= coef<R>(d, kCoInvTau + 4 + c);
+    if (noisy) D[c] += coef<R>(d, kCoAmp + 4 + c) * n[c];
+  }
+  const R D4 = D[0], D5 = D[1], D6 = D[2], D7 = D[3], D8 = D[4], D9 = D[5];
+  const R D10 = D[6], D11 = D[7], D12 = D[8], D13 = D[9], D14 = D[10];
+  // back transform, n_i^a = w_i m_i^a
+  const R wa = (R)1 / (R)9, wc = (R)1 / (R)72;
+  g[0] = g[0] + (R)(2.0 / 9.0) * (S2 * D14 - hS6 * D9);
+  const R base = hS3 * D5 - hS2 * D14;             // common to the axis populations
+  const R hx = (R)1.5 * D4;
+  const R tx = hS6 * D10, ty = hS6 * D11, tz = hS6 * D12;
+  g[1] = g[1] + wa * ((base + hx) - tx);
+  g[2] = g[2] + wa * ((base + hx) + tx);
+  g[3] = g[3] + wa * ((base - hx) - ty);
+  g[4] = g[4] + wa * ((base - hx) + ty);
+  const R bz = -S3 * D5 - hS2 * D14;
+  g[5] = g[5] + wa * (bz - tz);
+  g[6] = g[6] + wa * (bz + tz);
+  // corners: w (G + E(v) +- O(v)), E even and O odd in v
+  const R G = S6 * D9 + S2 * D14;
+  const R p6 = (R)3 * D6, p7 = (R)3 * D7, p8 = (R)3 * D8, p13 = (R)3 * D13;
+  const R q10 = S6 * D10, q11 = S6 * D11, q12 = S6 * D12;
+  {
+    const R E = G + ((p6 + p7) + p8), O = ((q10 + q11) + q12) + p13;       // (1,1,1)
+    g[7] = g[7] + wc * (E + O);
+    g[8] = g[8] + wc * (E - O);
+  }
+  {
+    const R E = G + ((p6 - p7) - p8), O = ((q10 + q11) - q12) - p13;       // (1,1,-1)
+    g[9] = g[9] + wc * (E + O);
+    g[10] = g[10] + wc * (E - O);
+  }
+  {
+    const R E = G + ((p8 - p6) - p7), O = ((q10 - q11) + q12) - p13;       // (1,-1,1)
+    g[11] = g[11] + wc * (E + O);
+    g[12] = g[12] + wc * (E - O);
+  }
+  {
+    const R E = G + ((p7 - p6) - p8), O = ((q11 + q12) - q10) - p13;       // (-1,1,1)
+    g[13] = g[13] + wc * (E + O);
+    g[14] = g[14] + wc * (E - O);
+  }
+}
+
+// The eleven unit normals of a site (Philox calls 0..2; the twelfth is not used).
+template <typename R>
+__device__ __forceinline__ void normals_d3q15(const ReplicaDesc& d, uint32_t site, uint32_t step, R (&n)[11]) {
+  const uint4 w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
+  const uint4 w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
+  const uint4 w2 = philox4x32_10(site, step, 2u, d.stream, d.seed_lo, d.seed_hi);
+  R spare;
+  box_muller(w0.x, w0.y, n[0], n[1]);
+  box_muller(w0.z, w0.w, n[2], n[3]);
+  box_muller(w1.x, w1.y, n[4], n[5]);
+  box_muller(w1.z, w1.w, n[6], n[7]);
+  box_muller(w2.x, w2.y, n[8], n[9]);
+  box_muller(w2.z, w2.w, n[10], spare);
+  (void)spare;
+}
+
+// One thread = VEC consecutive sites of a row (y, z); a persistent grid loops over virtual
+// blocks of kStepThreads units, each within one replica.  ONE: a single replica whose
+// description is the kernel argument (constant bank).
+template <typename R, bool DEV, int VEC, bool SAMPLE, bool ONE>
+__global__ void __launch_bounds__(kStepThreads, FLB_STEP3_MINB)
+k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
+             const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_vblocks, char* __restrict__ ws, int parity,
+             uint32_t step, const uint64_t* __restrict__ step_dev) {
+  if (step_dev) {
+    const uint64_t t = *step_dev + step;
+    step = (uint32_t)t;
+    parity = (int)(t & 1);
+  }
+  for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
+    const int r = ONE ? 0 : find_replica(vb_begin, n_reps, vb);
+    const ReplicaDesc& d = ONE ? one : descs[r];
+    const UnitPos u = unit_position(d, vb, ONE ? 0 : vb_begin[r], (int)threadIdx.x, kStepThreads, VEC);
+    const int row = u.y;                       // z ny + y
+    const int z = row / d.ny, y = row - z * d.ny;
+    const int64_t vol = (int64_t)d.nx * d.ny * d.nz;
+    const R* __restrict__ src = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
+    R* __restrict__ dst = reinterpret_cast<R*>(ws + d.off_pop[parity ^ 1]);
+    R f[15][VEC];
+    pull_d3q15<R, VEC>(src, vol, d.nx, d.ny, d.nz, y, z, u, f);
+    const bool noisy = d.noise_mask != 0;
+    R fld[15][VEC];
+#pragma unroll
+    for (int s = 0; s < VEC; ++s) {
+      R g[15];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) g[i] = f[i][s];
+      R n[11];
+#pragma unroll
+      for (int c = 0; c < 11; ++c) n[c] = (R)0;
+      if (noisy) normals_d3q15<R>(d, (uint32_t)row * (uint32_t)d.nx + (uint32_t)(u.x0 + s), step, n);
+      R fl[15];
+      collide_d3q15<R, DEV, SAMPLE>(d, g, noisy, n, fl);
+#pragma unroll
+      for (int i = 0; i < 15; ++i) f[i][s] = g[i];
+      if constexpr (SAMPLE) {
+#pragma unroll
+        for (int a = 0; a < 15; ++a) fld[a][s] = fl[a];
+      }
+    }
+    if (!u.active) continue;
+    const int64_t off = (int64_t)row * d.nx + u.x0;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) VecIO<R, VEC>::st(dst + i * vol + off, f[i]);
+    if constexpr (SAMPLE) {
+      R* fields = reinterpret_cast<R*>(ws + d.off_fields);
+      for (int slot = 0; slot < (int)d.n_fields; ++slot) {
+        const int fid = d.field_id[slot];
+        R v[VEC];
+#pragma unroll
+        for (int s = 0; s < VEC; ++s) {
+          R val = fld[0][s];
+#pragma unroll
+          for (int a = 1; a < 15; ++a) val = (fid == a) ? fld[a][s] : val;
+          v[s] = val;
+        }
+        VecIO<R, VEC>::st(fields + slot * vol + off, v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state.  mode 0: f^0(rho0, u0).  mode 1: f^0 + sum_a n_i^a dM^a with dM^a =
+// sqrt(mu rho0) N_a (15 normals: Philox tag 1, step 0, calls 0..3) and the lattice mean of
+// the density and momentum fluctuations removed (k_thermal_sum3 sums them first).
+__device__ __forceinline__ void thermal_normals3(const ReplicaDesc& d, uint32_t site, double (&N)[16]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 w = philox4x32_10(site, 0u, (uint32_t)c | (1u << 8), d.stream, d.seed_lo, d.seed_hi);
+    box_muller(w.x, w.y, N[4 * c + 0], N[4 * c + 1]);
+    box_muller(w.z, w.w, N[4 * c + 2], N[4 * c + 3]);
+  }
+}
+
+__global__ void k_thermal_sum3(const ReplicaDesc* __restrict__ descs, int r, double* __restrict__ partial) {
+  const ReplicaDesc& d = descs[r];
+  const int64_t V = (int64_t)d.nx * d.ny * d.nz;
+  double acc[kNumSums] = {0, 0, 0, 0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
+    double N[16];
+    thermal_normals3(d, (uint32_t)s, N);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] += N[a];
+  }
+  block_sums(acc, partial);
+}
+
+// feq0: f^0_i(rho0, u0) at [i], w_i rho0 at [16 + i]
+template <typename R, bool DEV>
+__global__ void k_init3(const ReplicaDesc* __restrict__ descs, int r, char* __restrict__ ws, int mode,
+                        const double* __restrict__ feq0, const double* __restrict__ sums) {
+  const ReplicaDesc& d = descs[r];
+  const int64_t V = (int64_t)d.nx * d.ny * d.nz;
+  R* dst = reinterpret_cast<R*>(ws + d.off_pop[0]);
+  const double sm = sqrt(d.mu * d.rho0);
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
+    double M[15];
+    if (mode == 1) {
+      double N[16];
+      thermal_normals3(d, (uint32_t)s, N);
+#pragma unroll
+      for (int a = 0; a < 15; ++a) M[a] = sm * N[a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) M[a] -= sm * sums[a] / (double)V;
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      double v = feq0[i];
+      if (mode == 1) {
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < 15; ++a) acc += moment_row3(a, v3x(i), v3y(i), v3z(i)) * M[a];
+        v += w15(i) * acc;
+      }
+      if (DEV) v -= feq0[16 + i];
+      dst[i * V + s] = (R)v;
+    }
+  }
+}
+
+// FP64 lattice sums of rho, j_x, j_y, j_z of the stored state (per-block partials).
+template <typename R, bool DEV>
+__global__ void k_conserved3(const ReplicaDesc* __restrict__ descs, int r, const char* __restrict__ ws, int parity,
+                             double* __restrict__ partial) {
+  const ReplicaDesc& d = descs[r];
+  const int64_t V = (int64_t)d.nx * d.ny * d.nz;
+  const R* p = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
+  double acc[kNumSums] = {0, 0, 0, 0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
+    double rho = DEV ? d.rho0 : 0.0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      const double fv = (double)p[i * V + s];
+      rho += fv;
+      jx += v3x(i) * fv; jy += v3y(i) * fv; jz += v3z(i) * fv;
+    }
+    acc[0] += rho; acc[1] += jx; acc[2] += jy; acc[3] += jz;
+  }
+  block_sums(acc, partial);
+}
+
+// ---------------------------------------------------------------------------
+// Direct transforms at the time-correlator wave vectors.  Block b of replica blockIdx.y
+// takes the rows b, b + G, ... (G = gridDim.x); a thread is (item, part) with item =
+// f n_k + j: it sums x = part, part + P, ... of the row with the phase exp(-2 pi i (kx x
+// mod nx) / nx) from a table, multiplies by the row phase exp(-2 pi i (ky y / ny + kz z /
+// nz)) (FP64 tables) and accumulates in FP64.  The parts are added in order at the end
+// and the block's sums go to partial [G][F n_k].
+// Shared memory: x table (nx complex R) | y, z tables (ny + nz complex double) | sums.
+int point_dft_parts(int items) {
+  int P = 1;
+  while (items * P * 2 <= kStepThreads) P *= 2;
+  return P;
+}
+
+size_t point_dft_smem(int precision, int nx, int ny, int nz, int items) {
+  const size_t cs = precision == FLB_FP64 ? 16 : 8;
+  const size_t tabs = ((nx * cs + 15) & ~size_t(15)) + (size_t)(ny + nz) * 16;
+  const int P = point_dft_parts(items);
+  return tabs + (size_t)std::max(items * P, items) * 16;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kStepThreads)
+k_point_dft(const ReplicaDesc* __restrict__ descs, const char* __restrict__ ws, TimeCorr tc) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  const ReplicaDesc& d = descs[blockIdx.y];
+  const int F = (int)d.n_fields, nk = tc.n_k, items = F * nk;
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  const int64_t vol = (int64_t)nx * ny * nz;
+  cplx<R>* tx = reinterpret_cast<cplx<R>*>(psm);
+  double2* tyz = reinterpret_cast<double2*>(psm + ((nx * sizeof(cplx<R>) + 15) & ~size_t(15)));
+  double2* acc = tyz + ny + nz;
+  for (int m = threadIdx.x; m < nx; m += blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)nx, &s, &c);
+    tx[m].x = (R)c; tx[m].y = (R)s;
+  }
+  for (int m = threadIdx.x; m < ny + nz; m += blockDim.x) {
+    double s, c;
+    sincospi(m < ny ? -2.0 * (double)m / (double)ny : -2.0 * (double)(m - ny) / (double)nz, &s, &c);
+    tyz[m] = make_double2(c, s);
+  }
+  // parts per item (items <= blockDim / P); with more items than threads, P = 1 and a
+  // thread takes items tid, tid + blockDim, ...
+  int P = 1;
+  while (items * P * 2 <= (int)blockDim.x) P *= 2;
+  const int part = (int)threadIdx.x % P, ibase = (int)threadIdx.x / P, istride = (int)blockDim.x / P;
+  for (int it = ibase; it < items; it += istride) acc[part * items + it] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const R* fields = reinterpret_cast<const R*>(ws + d.off_fields);
+  const int rows = ny * nz;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int z = row / ny, y = row - z * ny;
+    for (int it = ibase; it < items; it += istride) {
+      const int f = it / nk, j = it - f * nk;
+      const int kx = tc.kx[j], ky = tc.ky[j], kz = tc.kz ? tc.kz[j] : 0;
+      const R* xr = fields + f * vol + (int64_t)row * nx;
+      R sr = (R)0, si = (R)0;
+      int m = (int)(((int64_t)kx * part) % nx);
+      const int dm = (int)(((int64_t)kx * P) % nx);
+      for (int x = part; x < nx; x += P) {
+        const R v = xr[x];
+        sr += v * tx[m].x;
+        si += v * tx[m].y;
+        m += dm;
+        if (m >= nx) m -= nx;
+      }
+      const double2 py = tyz[(int)(((int64_t)ky * y) % ny)];
+      const double2 pz = tyz[ny + (int)(((int64_t)kz * z) % nz)];
+      const double pr = py.x * pz.x - py.y * pz.y, pi = py.x * pz.y + py.y * pz.x;
+      double2& a = acc[part * items + it];
+      a.x += (double)sr * pr - (double)si * pi;
+      a.y += (double)sr * pi + (double)si * pr;
+    }
+  }
+  __syncthreads();
+  double2* out = reinterpret_cast<double2*>(tc.base + d.off_tc_part) + (int64_t)blockIdx.x * items;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    double2 s = acc[it];
+    for (int p = 1; p < P; ++p) { s.x += acc[p * items + it].x; s.y += acc[p * items + it].y; }
+    out[it] = s;
+  }
+}
+
+// Adds the G block partials in block order into the replica's ring slot count % n_lags.
+__global__ void k_point_finish(const ReplicaDesc* __restrict__ descs, TimeCorr tc) {
+  const int r = blockIdx.y;
+  const ReplicaDesc& d = descs[r];
+  const int items = (int)d.n_fields * tc.n_k;
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= items) return;
+  const double2* part = reinterpret_cast<const double2*>(tc.base + d.off_tc_part);
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < tc.part_blocks; ++b) { s.x += part[(int64_t)b * items + it].x; s.y += part[(int64_t)b * items + it].y; }
+  const int slot = (int)(tc.count[r] % (uint64_t)tc.n_lags);
+  reinterpret_cast<double2*>(tc.base + d.off_tc_ring)[(int64_t)slot * items + it] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (called from api.cu).
+
+void launch_finish_sums(const double* partial, int nblocks, double* sums, DevStatus* status, int r,
+                        cudaStream_t st);
+
+void launch_step3(int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st) {
+  const bool one = L.n_reps == 1;
+#define FLB_L3(R, DEV, V, S, O) k_step_d3q15<R, DEV, V, S, O><<<L.grid, kStepThreads, 0, st>>>( \
+      L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, L.step_dev)
+#define FLB_LS(R, DEV, V) { \
+    if (one) { if (sample) FLB_L3(R, DEV, V, true, true); else FLB_L3(R, DEV, V, false, true); } \
+    else { if (sample) FLB_L3(R, DEV, V, true, false); else FLB_L3(R, DEV, V, false, false); } }
+  if (precision == FLB_FP64) FLB_LS(double, false, 1)
+  else if (vec == 4) FLB_LS(float, true, 4)
+  else if (vec == 2) FLB_LS(float, true, 2)
+  else FLB_LS(float, true, 1)
+#undef FLB_LS
+#undef FLB_L3
+}
+
+void launch_init3(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+                  double* sums, double* partial, int64_t V, cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)std::min<int64_t>((V + block - 1) / block, kReduceBlocks);
+  if (mode == 1) {
+    k_thermal_sum3<<<grid, block, 0, st>>>(descs, r, partial);
+    launch_finish_sums(partial, grid, sums, nullptr, r, st);
+  }
+  if (precision == FLB_FP64) k_init3<double, false><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
+  else k_init3<float, true><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
+}
+
+void launch_conserved3(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
+                       double* partial, DevStatus* status, int64_t V, cudaStream_t st) {
+  const int block = 256;
+  const int grid = (int)std::min<int64_t>((V + block - 1) / block, kReduceBlocks);
+  if (precision == FLB_FP64) k_conserved3<double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  else k_conserved3<float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  launch_finish_sums(partial, grid, sums, status, r, st);
+}
+
+cudaError_t set_point_dft_smem(int precision, size_t bytes) {
+  if (precision == FLB_FP64)
+    return cudaFuncSetAttribute(k_point_dft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(k_point_dft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int max_items, const char* ws,
+                      const TimeCorr& tc, size_t smem, cudaStream_t st) {
+  const dim3 grid(tc.part_blocks, n_reps);
+  if (precision == FLB_FP64) k_point_dft<double><<<grid, kStepThreads, smem, st>>>(descs, ws, tc);
+  else k_point_dft<float><<<grid, kStepThreads, smem, st>>>(descs, ws, tc);
+  k_point_finish<<<dim3((max_items + 255) / 256, n_reps), 256, 0, st>>>(descs, tc);
+}
+
+}  // namespace flb

@@ -138,33 +138,13 @@ __device__ __forceinline__ void thermal_normals(const ReplicaDesc& d, uint32_t s
   }
 }
 
-// Deterministic block reduction of three sums: each block writes its partial sums
-// (fixed site set, fixed shuffle tree); k_finish_sums adds the partials in order.
-__device__ __forceinline__ void block_sum3(double (&acc)[3], double* __restrict__ partial) {
-  __shared__ double red[32][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 3; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int k = 0; k < 3; ++k) {
-      double v = 0.0;
-      for (int w = 0; w < nw; ++w) v += red[w][k];
-      partial[3 * blockIdx.x + k] = v;
-    }
-  }
-}
-
+// Adds the per-block partials of block_sums in block order.
 __global__ void k_finish_sums(const double* __restrict__ partial, int nblocks, double* __restrict__ sums,
                               DevStatus* status, int r) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kNumSums; ++k) {
     double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) v += partial[3 * b + k];
+    for (int b = 0; b < nblocks; ++b) v += partial[kNumSums * b + k];
     sums[k] = v;
     if (status && !isfinite(v) && status->error == 0) { status->error = FLB_EUNSTABLE; status->replica = r; }
   }
@@ -173,14 +153,14 @@ __global__ void k_finish_sums(const double* __restrict__ partial, int nblocks, d
 __global__ void k_thermal_sum(const ReplicaDesc* __restrict__ descs, int r, double* __restrict__ partial) {
   const ReplicaDesc& d = descs[r];
   const int64_t V = (int64_t)d.nx * d.ny;
-  double acc[3] = {0, 0, 0};
+  double acc[kNumSums] = {0, 0, 0, 0};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
     double N[12];
     thermal_normals(d, (uint32_t)s, d.q, N);
     acc[0] += N[0]; acc[1] += N[1];
     if (d.q == 9) acc[2] += N[2];
   }
-  block_sum3(acc, partial);
+  block_sums(acc, partial);
 }
 
 template <typename R, bool DEV>
@@ -224,7 +204,7 @@ __global__ void k_init(const ReplicaDesc* __restrict__ descs, int r, char* __res
     }
     for (int i = 0; i < d.q; ++i) {
       double v = f[i];
-      if (DEV) v -= feq0[9 + i];          // w_i rho0
+      if (DEV) v -= feq0[16 + i];         // w_i rho0
       dst[i * V + s] = (R)v;
     }
   }
@@ -237,7 +217,7 @@ __global__ void k_conserved(const ReplicaDesc* __restrict__ descs, int r, const 
   const ReplicaDesc& d = descs[r];
   const int64_t V = (int64_t)d.nx * d.ny;
   const R* p = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
-  double acc[3] = {0, 0, 0};
+  double acc[kNumSums] = {0, 0, 0, 0};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
     if (d.q == 9) {
       double fv[9];
@@ -253,7 +233,7 @@ __global__ void k_conserved(const ReplicaDesc* __restrict__ descs, int r, const 
       acc[1] += b - c;
     }
   }
-  block_sum3(acc, partial);
+  block_sums(acc, partial);
 }
 
 // Diagnostics: the generator exactly as the step kernels call it.
@@ -333,6 +313,11 @@ void launch_conserved(int precision, const ReplicaDesc* descs, int r, const char
   if (precision == FLB_FP64) k_conserved<double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
   else k_conserved<float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
   k_finish_sums<<<1, 32, 0, st>>>(partial, grid, sums, status, r);
+}
+
+void launch_finish_sums(const double* partial, int nblocks, double* sums, DevStatus* status, int r,
+                        cudaStream_t st) {
+  k_finish_sums<<<1, 32, 0, st>>>(partial, nblocks, sums, status, r);
 }
 
 void launch_philox(const uint32_t* site, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,

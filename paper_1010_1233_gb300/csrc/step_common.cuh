@@ -26,6 +26,30 @@ __device__ __forceinline__ int find_replica(const int64_t* vb_begin, int n_reps,
   return lo;
 }
 
+// Deterministic block reduction of kNumSums sums: each block writes its partial sums
+// (fixed site set, fixed shuffle tree) to partial[kNumSums * blockIdx.x + k]; k_finish_sums
+// (lb_step.cu) adds the partials in block order.
+constexpr int kNumSums = 4;
+__device__ __forceinline__ void block_sums(double (&acc)[kNumSums], double* __restrict__ partial) {
+  __shared__ double red[32][kNumSums];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < kNumSums; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < nw; ++w) v += red[w][k];
+      partial[kNumSums * blockIdx.x + k] = v;
+    }
+  }
+}
+
 template <typename R, int VEC> struct VecIO;
 template <> struct VecIO<float, 1> {
   static __device__ __forceinline__ void ld(const float* p, float (&v)[1]) { v[0] = __ldg(p); }

@@ -10,8 +10,9 @@ import torch
 
 from . import _lib as L
 
-_NONCONSERVED = {"D2Q9": (3, 4, 5, 6, 7, 8), "D1Q3": (2,)}
-_LATTICE = {"D2Q9": L.FLB_D2Q9, "D1Q3": L.FLB_D1Q3}
+_NONCONSERVED = {"D2Q9": (3, 4, 5, 6, 7, 8), "D1Q3": (2,), "D3Q15": tuple(range(4, 15))}
+_LATTICE = {"D2Q9": L.FLB_D2Q9, "D1Q3": L.FLB_D1Q3, "D3Q15": L.FLB_D3Q15}
+_Q = {"D1Q3": 3, "D2Q9": 9, "D3Q15": 15}
 _PREC = {"fp64": L.FLB_FP64, "fp32": L.FLB_FP32_DEV}
 
 
@@ -20,13 +21,15 @@ def replica_struct(p):
     s = L.flb_replica()
     s.lattice = _LATTICE[p["lattice"]]
     s.nx = int(p["nx"])
-    s.ny = int(p["ny"]) if p["lattice"] == "D2Q9" else 1
-    tau = list(p["tau"]) + [1.0] * (9 - len(p["tau"]))
-    for a in range(9):
+    s.ny = int(p["ny"]) if p["lattice"] != "D1Q3" else 1
+    s.nz = int(p.get("nz", 1)) if p["lattice"] == "D3Q15" else 1
+    tau = list(p["tau"]) + [1.0] * (16 - len(p["tau"]))
+    for a in range(16):
         s.tau[a] = float(tau[a])
     s.rho0 = float(p["rho0"])
     s.kT = float(p["kT"])
-    s.u0[0], s.u0[1] = float(p["u0"][0]), float(p["u0"][1])
+    u0 = list(p["u0"]) + [0.0] * (3 - len(p["u0"]))
+    s.u0[0], s.u0[1], s.u0[2] = float(u0[0]), float(u0[1]), float(u0[2])
     s.seed = int(p["seed"]) & 0xFFFFFFFFFFFFFFFF
     s.stream = int(p.get("stream", 0))
     nm = p.get("noise_mask")
@@ -92,6 +95,13 @@ class Sim:
         p = self.params[r]
         return (p["ny"] if p["lattice"] == "D2Q9" else 1, p["nx"])
 
+    def _dims(self, r):
+        """Lattice shape of replica r: (nz, ny, nx) for D3Q15, else (ny, nx)."""
+        p = self.params[r] if 0 <= r < len(self.params) else None
+        if p is not None and p["lattice"] == "D3Q15":
+            return (int(p["nz"]), int(p["ny"]), int(p["nx"]))
+        return self._shape(r)
+
     def correlator(self, r, a, b, with_count=False):
         ny, nx = self._shape(r)
         out = np.empty(ny * nx * 2)
@@ -103,9 +113,9 @@ class Sim:
         return (c, int(n.value)) if with_count else c
 
     def populations(self, r=0):
-        ny, nx = self._shape(r)
-        q = 9 if self.params[r]["lattice"] == "D2Q9" else 3
-        out = np.empty((q, ny, nx))
+        dims = self._dims(r)
+        q = _Q[self.params[r]["lattice"]]
+        out = np.empty((q,) + dims)
         L.check(L.lib().flb_get_populations(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
@@ -119,10 +129,10 @@ class Sim:
         return out
 
     def fields(self, r=0):
-        """Fields of the most recent sample, [n_fields][ny][nx] in increasing field id order."""
-        ny, nx = self._shape(r)
+        """Fields of the most recent sample, [n_fields] + lattice shape, in increasing field id order."""
+        dims = self._dims(r)
         F = len(self.params[r].get("fields", ()))
-        out = np.empty((F, ny, nx))
+        out = np.empty((F,) + dims)
         L.check(L.lib().flb_get_fields(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
@@ -131,9 +141,10 @@ class Sim:
         L.check(L.lib().flb_set_populations(self._ctx, r, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def conserved(self, r=0):
-        out = np.empty(3)
+        """Lattice sums (rho, j_x, j_y) (D3Q15: (rho, j_x, j_y, j_z)) of the stored state."""
+        out = np.empty(4)
         L.check(L.lib().flb_get_conserved(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        return out
+        return out if self.params[min(max(r, 0), len(self.params) - 1)]["lattice"] == "D3Q15" else out[:3]
 
     # -- learned noise scale ----------------------------------------------
     def set_mlp(self, weights=None):
@@ -151,21 +162,24 @@ class Sim:
 
     # -- time correlators -------------------------------------------------
     def set_time_correlator(self, kpoints, n_lags):
-        """Accumulate F_ab(k, tau) at the wave vectors kpoints = [(ky, kx), ...] for lags
-        0..n_lags-1 (samples); n_lags = 0 switches them off."""
+        """Accumulate F_ab(k, tau) at the wave vectors kpoints = [(ky, kx), ...] (D3Q15:
+        [(kz, ky, kx), ...]) for lags 0..n_lags-1 (samples); n_lags = 0 switches them off."""
         lib = L.lib()
         if n_lags == 0:
             L.check(lib.flb_set_time_correlator(self._ctx, 0, 0, None, None, None, 0))
             self._tc = None
             return
-        ky = np.ascontiguousarray([k[0] for k in kpoints], dtype=np.int32)
-        kx = np.ascontiguousarray([k[1] for k in kpoints], dtype=np.int32)
+        kp = [tuple(int(v) for v in k) for k in kpoints]
+        kp = [k if len(k) == 3 else (0,) + k for k in kp]
+        kz = np.ascontiguousarray([k[0] for k in kp], dtype=np.int32)
+        ky = np.ascontiguousarray([k[1] for k in kp], dtype=np.int32)
+        kx = np.ascontiguousarray([k[2] for k in kp], dtype=np.int32)
         n = ctypes.c_size_t()
         L.check(lib.flb_time_correlator_bytes(self._ctx, int(n_lags), len(kx), ctypes.byref(n)))
         buf = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
         off = (-buf.data_ptr()) % 256
-        L.check(lib.flb_set_time_correlator(self._ctx, int(n_lags), len(kx), kx.ctypes.data, ky.ctypes.data,
-                                            ctypes.c_void_p(buf.data_ptr() + off), int(n.value)))
+        L.check(lib.flb_set_time_correlator3(self._ctx, int(n_lags), len(kx), kx.ctypes.data, ky.ctypes.data,
+                                             kz.ctypes.data, ctypes.c_void_p(buf.data_ptr() + off), int(n.value)))
         self._tc = (buf, int(n_lags), len(kx))
 
     def time_correlator(self, r, a, b, with_count=False):

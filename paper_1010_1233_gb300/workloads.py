@@ -54,6 +54,26 @@ def replica(lattice=D2Q9, nx=16, ny=16, tau=None, rho0=1.0, kT=1e-4, u0=(0.0, 0.
                 noise_mode=int(noise_mode))
 
 
+D3Q15 = "D3Q15"
+
+
+def taus_d3q15(tau_shear, tau_bulk=None, tau_ghost=1.0):
+    """Relaxation time per D3Q15 moment (0..14): shear 4..8, bulk 9, ghosts 10..14."""
+    tb = tau_shear if tau_bulk is None else tau_bulk
+    return [1.0] * 4 + [tau_shear] * 5 + [tb] + [tau_ghost] * 5
+
+
+def replica3(nx=8, ny=8, nz=8, tau=None, rho0=1.0, kT=1e-4, u0=(0.0, 0.0, 0.0), seed=0, stream=0,
+             noise_mask=None, init_mode=0, fields=()):
+    """One D3Q15 replica's parameters (keys shared by both sides)."""
+    if tau is None:
+        tau = taus_d3q15(1.0)
+    return dict(lattice=D3Q15, nx=int(nx), ny=int(ny), nz=int(nz), tau=[float(t) for t in tau],
+                rho0=float(rho0), kT=float(kT), u0=tuple(float(v) for v in u0), seed=int(seed),
+                stream=int(stream), noise_mask=noise_mask, init_mode=int(init_mode), fields=list(fields),
+                noise_mode=0)
+
+
 def d1q3_L64():
     return dict(replicas=[replica(D1Q3, 64, 1, taus_d1q3(0.8), kT=1e-4, seed=1,
                                   fields=(0, 1))],

@@ -87,3 +87,40 @@ def test_d1q3_needs_single_row(lib):
 def test_empty_replica_list_rejected(lib):
     n = ctypes.c_size_t()
     assert lib.flb_workspace_bytes(L.FLB_FP32_DEV, None, 0, ctypes.byref(n)) == L.FLB_EINVAL
+
+
+def test_d3q15_workspace(lib):
+    rc, a = _ws([W.replica3(16, 8, 4)])
+    assert rc == 0 and a >= 2 * 15 * 16 * 8 * 4 * 4
+    rc, b = _ws([W.replica3(16, 8, 4, fields=(0, 4, 14))])
+    assert rc == 0 and b >= a + 3 * 16 * 8 * 4 * 4
+    rc, c = _ws([W.replica3(16, 8, 4)], precision=L.FLB_FP64)
+    assert rc == 0 and c >= 2 * 15 * 16 * 8 * 4 * 8
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nz=0),                                     # D3Q15 needs nz >= 1
+    dict(nx=5),                                     # odd nx
+    dict(tau=W.taus_d3q15(0.5)),                    # tau must exceed 1/2
+    dict(noise_mask=1 << 3),                        # noise on momentum z
+    dict(noise_mask=1 << 15),                       # beyond moment 14
+    dict(fields=(15,)),                             # unknown field
+    dict(fields=tuple(range(12))),                  # more than 11 fields
+    dict(noise_mode=1),                             # mode 0 only
+    dict(nx=4096, ny=4096, nz=256),                 # 2^32 sites
+    dict(nx=8192, ny=2, nz=2, fields=(0,)),         # direct transforms: nx <= 4096
+])
+def test_invalid_d3q15_parameters_rejected(lib, bad):
+    p = W.replica3(8, 8, 8)
+    p.update(bad)
+    rc, _ = _ws([p])
+    assert rc == L.FLB_EINVAL
+    assert len(lib.flb_last_error()) > 0
+
+
+def test_nz_rejected_on_2d_lattices(lib):
+    s = replica_struct(W.replica(nx=16, ny=16))
+    s.nz = 2
+    arr = (L.flb_replica * 1)(s)
+    n = ctypes.c_size_t()
+    assert lib.flb_workspace_bytes(L.FLB_FP32_DEV, arr, 1, ctypes.byref(n)) == L.FLB_EINVAL
