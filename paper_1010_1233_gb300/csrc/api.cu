@@ -43,6 +43,8 @@ void launch_init3(int precision, const ReplicaDesc* descs, int r, char* ws, int 
 void launch_conserved3(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
                        double* partial, DevStatus* status, int64_t V, cudaStream_t st);
 size_t point_dft_smem(int precision, int nx, int ny, int nz, int items);
+size_t point_tables_bytes(int precision, int nx, int ny, int nz);
+void launch_point_tables(int precision, const ReplicaDesc* descs, int n_reps, char* base, cudaStream_t st);
 cudaError_t set_point_dft_smem(int precision, size_t bytes);
 void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int max_items, const char* ws,
                       const TimeCorr& tc, size_t smem, cudaStream_t st);
@@ -355,7 +357,9 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
     L.vec = all4 ? 4 : 2;
   } else if (precision == FLB_FP32_DEV && lat == FLB_D3Q15) {
-    L.vec = 2;                                   // nx is even
+    bool all4 = true;                            // nx is even
+    for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
+    L.vec = all4 ? 4 : 2;
   }
   L.desc.resize(n);
   int64_t off = 0;
@@ -494,24 +498,28 @@ static int reset_stats_async(flb_ctx* c) {
   return FLB_OK;
 }
 
-// Blocks of the D3Q15 direct transforms: two per SM at most, no more than the rows, and
-// partial sums of at most 64 MB per replica.
+// Blocks of the D3Q15 direct transforms: FLB_POINT_BPS per SM at most, no more than the
+// rows, and partial sums of at most 64 MB per replica.
+#ifndef FLB_POINT_BPS
+#define FLB_POINT_BPS 8
+#endif
 static int point_blocks(const flb_ctx* c, int n_k) {
   int64_t rows = 1, maxF = 1;
   for (const ReplicaDesc& d : c->L.desc) {
     rows = std::max<int64_t>(rows, (int64_t)d.ny * d.nz);
     maxF = std::max<int64_t>(maxF, d.n_fields);
   }
-  int64_t g = std::min<int64_t>(2 * (int64_t)c->sms, rows);
+  int64_t g = std::min<int64_t>((int64_t)FLB_POINT_BPS * c->sms, rows);
   g = std::min<int64_t>(g, std::max<int64_t>(1, (int64_t(1) << 22) / (maxF * n_k)));
   return (int)std::max<int64_t>(g, 1);
 }
 
 // Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | kz [n_k] | rings
-// of every replica | D3Q15 block partials of every replica | sums of every replica
-// (contiguous, so a reset is one memset).
+// of every replica | D3Q15 block partials and phase tables of every replica | sums of
+// every replica (contiguous, so a reset is one memset).
 static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vector<int64_t>* ring,
-                                std::vector<int64_t>* sums, int64_t* sums0, std::vector<int64_t>* part = nullptr) {
+                                std::vector<int64_t>* sums, int64_t* sums0, std::vector<int64_t>* part = nullptr,
+                                std::vector<int64_t>* tab = nullptr) {
   int64_t off = align256(8 * (int64_t)c->n);
   off = align256(off + 4 * (int64_t)n_k);
   off = align256(off + 4 * (int64_t)n_k);
@@ -523,8 +531,11 @@ static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vect
   if (c->lattice == FLB_D3Q15) {
     const int G = point_blocks(c, n_k);
     for (int r = 0; r < c->n; ++r) {
+      const ReplicaDesc& d = c->L.desc[r];
       if (part) (*part)[r] = off;
-      off = align256(off + 16 * (int64_t)G * c->L.desc[r].n_fields * n_k);
+      off = align256(off + 16 * (int64_t)G * d.n_fields * n_k);
+      if (tab) (*tab)[r] = off;
+      off = align256(off + (int64_t)point_tables_bytes(c->precision, d.nx, d.ny, d.nz));
     }
   }
   if (sums0) *sums0 = off;
@@ -596,9 +607,9 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
     rc = cuda_check(set_point_dft_smem(c->precision, smem), "transform smem");
     if (rc) return rc;
   }
-  std::vector<int64_t> ring(c->n), sums(c->n), part(c->n);
+  std::vector<int64_t> ring(c->n), sums(c->n), part(c->n), tab(c->n);
   int64_t sums0 = 0;
-  const int64_t need = time_corr_layout(c, n_lags, n_k, &ring, &sums, &sums0, &part);
+  const int64_t need = time_corr_layout(c, n_lags, n_k, &ring, &sums, &sums0, &part, &tab);
   if ((int64_t)bytes < need) return set_error(FLB_EINVAL, "buffer of %zu bytes, need %lld", bytes, (long long)need);
   char* base = static_cast<char*>(buf_dev);
   const int64_t okx = align256(8 * (int64_t)c->n), oky = align256(okx + 4 * (int64_t)n_k);
@@ -614,10 +625,17 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
     c->L.desc[r].off_tc_ring = ring[r];
     c->L.desc[r].off_tc_sums = sums[r];
     c->L.desc[r].off_tc_part = d3 ? part[r] : 0;
+    c->L.desc[r].off_tc_tab = d3 ? tab[r] : 0;
   }
   rc = cuda_check(cudaMemcpy(c->ws + c->L.off_descs, c->L.desc.data(), c->n * sizeof(ReplicaDesc),
                              cudaMemcpyHostToDevice), "copy descriptors");
   if (rc) return rc;
+  if (d3) {
+    launch_point_tables(c->precision, descs_dev(c), c->n, base, c->stream);
+    rc = cuda_check(cudaGetLastError(), "phase tables");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(c->stream), "phase tables");
+    if (rc) return rc;
+  }
   c->tc.base = base;
   c->tc.n_lags = n_lags;
   c->tc.n_k = n_k;

@@ -58,6 +58,7 @@ struct ReplicaDesc {
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
   int64_t off_tc_ring, off_tc_sums; // time correlators: offsets in the TimeCorr buffer (see TimeCorr)
   int64_t off_tc_part;              // D3Q15: per-block partial transforms [blocks][F][n_k] double2
+  int64_t off_tc_tab;               // D3Q15: phase tables of the direct transforms (lb_d3q15.cu)
   int32_t acc_ncol;                 // pair-sum layout: 0 = [ky][kx]; c > 0 = blocked in the order
                                     // the column pass produces the points: [k1][kx / c][k2][kx % c]
                                     // (ky = k1 + N1 k2; kx padded to a multiple of c)

@@ -238,7 +238,8 @@ k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repl
     R f[15][VEC];
     pull_d3q15<R, VEC>(src, vol, d.nx, d.ny, d.nz, y, z, u, f);
     const bool noisy = d.noise_mask != 0;
-    R fld[15][VEC];
+    const int64_t off = (int64_t)row * d.nx + u.x0;
+    R* fields = SAMPLE ? reinterpret_cast<R*>(ws + d.off_fields) : nullptr;
 #pragma unroll
     for (int s = 0; s < VEC; ++s) {
       R g[15];
@@ -253,29 +254,21 @@ k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repl
 #pragma unroll
       for (int i = 0; i < 15; ++i) f[i][s] = g[i];
       if constexpr (SAMPLE) {
+        // the site's sampled fields, stored at once (scalar stores; the lanes of a warp
+        // cover contiguous rows of each field plane)
+        if (u.active)
+          for (int slot = 0; slot < (int)d.n_fields; ++slot) {
+            const int fid = d.field_id[slot];
+            R val = fl[0];
 #pragma unroll
-        for (int a = 0; a < 15; ++a) fld[a][s] = fl[a];
+            for (int a = 1; a < 15; ++a) val = (fid == a) ? fl[a] : val;
+            fields[slot * vol + off + s] = val;
+          }
       }
     }
     if (!u.active) continue;
-    const int64_t off = (int64_t)row * d.nx + u.x0;
 #pragma unroll
     for (int i = 0; i < 15; ++i) VecIO<R, VEC>::st(dst + i * vol + off, f[i]);
-    if constexpr (SAMPLE) {
-      R* fields = reinterpret_cast<R*>(ws + d.off_fields);
-      for (int slot = 0; slot < (int)d.n_fields; ++slot) {
-        const int fid = d.field_id[slot];
-        R v[VEC];
-#pragma unroll
-        for (int s = 0; s < VEC; ++s) {
-          R val = fld[0][s];
-#pragma unroll
-          for (int a = 1; a < 15; ++a) val = (fid == a) ? fld[a][s] : val;
-          v[s] = val;
-        }
-        VecIO<R, VEC>::st(fields + slot * vol + off, v);
-      }
-    }
   }
 }
 
@@ -366,18 +359,43 @@ __global__ void k_conserved3(const ReplicaDesc* __restrict__ descs, int r, const
 // mod nx) / nx) from a table, multiplies by the row phase exp(-2 pi i (ky y / ny + kz z /
 // nz)) (FP64 tables) and accumulates in FP64.  The parts are added in order at the end
 // and the block's sums go to partial [G][F n_k].
-// Shared memory: x table (nx complex R) | y, z tables (ny + nz complex double) | sums.
+// The phase tables are made once per replica (k_point_tables, at configuration) in the
+// correlator buffer at off_tc_tab: x table (nx complex R, 16-byte padded) | y, z tables
+// (ny + nz complex double); each block copies them to shared memory, followed by the
+// per-part sums.
 int point_dft_parts(int items) {
   int P = 1;
   while (items * P * 2 <= kStepThreads) P *= 2;
   return P;
 }
 
-size_t point_dft_smem(int precision, int nx, int ny, int nz, int items) {
+size_t point_tables_bytes(int precision, int nx, int ny, int nz) {
   const size_t cs = precision == FLB_FP64 ? 16 : 8;
-  const size_t tabs = ((nx * cs + 15) & ~size_t(15)) + (size_t)(ny + nz) * 16;
+  return ((nx * cs + 15) & ~size_t(15)) + (size_t)(ny + nz) * 16;
+}
+
+size_t point_dft_smem(int precision, int nx, int ny, int nz, int items) {
   const int P = point_dft_parts(items);
-  return tabs + (size_t)std::max(items * P, items) * 16;
+  return point_tables_bytes(precision, nx, ny, nz) + (size_t)std::max(items * P, items) * 16;
+}
+
+template <typename R>
+__global__ void k_point_tables(const ReplicaDesc* __restrict__ descs, char* __restrict__ base) {
+  const ReplicaDesc& d = descs[blockIdx.y];
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  cplx<R>* tx = reinterpret_cast<cplx<R>*>(base + d.off_tc_tab);
+  double2* tyz = reinterpret_cast<double2*>(base + d.off_tc_tab + ((nx * sizeof(cplx<R>) + 15) & ~size_t(15)));
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nx + ny + nz; m += gridDim.x * blockDim.x) {
+    double s, c;
+    if (m < nx) {
+      sincospi(-2.0 * (double)m / (double)nx, &s, &c);
+      tx[m].x = (R)c; tx[m].y = (R)s;
+    } else {
+      const int k = m - nx;
+      sincospi(k < ny ? -2.0 * (double)k / (double)ny : -2.0 * (double)(k - ny) / (double)nz, &s, &c);
+      tyz[k] = make_double2(c, s);
+    }
+  }
 }
 
 template <typename R>
@@ -388,19 +406,16 @@ k_point_dft(const ReplicaDesc* __restrict__ descs, const char* __restrict__ ws, 
   const int F = (int)d.n_fields, nk = tc.n_k, items = F * nk;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const int64_t vol = (int64_t)nx * ny * nz;
-  cplx<R>* tx = reinterpret_cast<cplx<R>*>(psm);
-  double2* tyz = reinterpret_cast<double2*>(psm + ((nx * sizeof(cplx<R>) + 15) & ~size_t(15)));
-  double2* acc = tyz + ny + nz;
-  for (int m = threadIdx.x; m < nx; m += blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)m / (double)nx, &s, &c);
-    tx[m].x = (R)c; tx[m].y = (R)s;
+  const size_t txb = (nx * sizeof(cplx<R>) + 15) & ~size_t(15);
+  {
+    const int4* src = reinterpret_cast<const int4*>(tc.base + d.off_tc_tab);
+    int4* dst = reinterpret_cast<int4*>(psm);
+    const int n16 = (int)((txb + (size_t)(ny + nz) * 16) / 16);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
   }
-  for (int m = threadIdx.x; m < ny + nz; m += blockDim.x) {
-    double s, c;
-    sincospi(m < ny ? -2.0 * (double)m / (double)ny : -2.0 * (double)(m - ny) / (double)nz, &s, &c);
-    tyz[m] = make_double2(c, s);
-  }
+  const cplx<R>* tx = reinterpret_cast<const cplx<R>*>(psm);
+  const double2* tyz = reinterpret_cast<const double2*>(psm + txb);
+  double2* acc = reinterpret_cast<double2*>(psm + txb + (size_t)(ny + nz) * 16);
   // parts per item (items <= blockDim / P); with more items than threads, P = 1 and a
   // thread takes items tid, tid + blockDim, ...
   int P = 1;
@@ -414,18 +429,31 @@ k_point_dft(const ReplicaDesc* __restrict__ descs, const char* __restrict__ ws, 
     const int z = row / ny, y = row - z * ny;
     for (int it = ibase; it < items; it += istride) {
       const int f = it / nk, j = it - f * nk;
-      const int kx = tc.kx[j], ky = tc.ky[j], kz = tc.kz ? tc.kz[j] : 0;
+      const int kx = tc.kx[j], ky = tc.ky[j], kz = tc.kz[j];
       const R* xr = fields + f * vol + (int64_t)row * nx;
-      R sr = (R)0, si = (R)0;
-      int m = (int)(((int64_t)kx * part) % nx);
       const int dm = (int)(((int64_t)kx * P) % nx);
-      for (int x = part; x < nx; x += P) {
-        const R v = xr[x];
-        sr += v * tx[m].x;
-        si += v * tx[m].y;
-        m += dm;
-        if (m >= nx) m -= nx;
+      int m0 = (int)(((int64_t)kx * part) % nx);
+      // four independent partial sums, loads issued ahead of the multiplies
+      R sr0 = (R)0, si0 = (R)0, sr1 = (R)0, si1 = (R)0;
+      int x = part;
+      for (; x + 3 * P < nx; x += 4 * P) {
+        const R v0 = xr[x], v1 = xr[x + P], v2 = xr[x + 2 * P], v3 = xr[x + 3 * P];
+        int m1 = m0 + dm; m1 -= m1 >= nx ? nx : 0;
+        int m2 = m1 + dm; m2 -= m2 >= nx ? nx : 0;
+        int m3 = m2 + dm; m3 -= m3 >= nx ? nx : 0;
+        const cplx<R> c0 = tx[m0], c1 = tx[m1], c2 = tx[m2], c3 = tx[m3];
+        sr0 += v0 * c0.x; si0 += v0 * c0.y;
+        sr1 += v1 * c1.x; si1 += v1 * c1.y;
+        sr0 += v2 * c2.x; si0 += v2 * c2.y;
+        sr1 += v3 * c3.x; si1 += v3 * c3.y;
+        m0 = m3 + dm; m0 -= m0 >= nx ? nx : 0;
       }
+      for (; x < nx; x += P) {
+        const R v = xr[x];
+        sr0 += v * tx[m0].x; si0 += v * tx[m0].y;
+        m0 += dm; m0 -= m0 >= nx ? nx : 0;
+      }
+      const R sr = sr0 + sr1, si = si0 + si1;
       const double2 py = tyz[(int)(((int64_t)ky * y) % ny)];
       const double2 pz = tyz[ny + (int)(((int64_t)kz * z) % nz)];
       const double pr = py.x * pz.x - py.y * pz.y, pi = py.x * pz.y + py.y * pz.x;
@@ -503,6 +531,12 @@ cudaError_t set_point_dft_smem(int precision, size_t bytes) {
   if (precision == FLB_FP64)
     return cudaFuncSetAttribute(k_point_dft<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaFuncSetAttribute(k_point_dft<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_point_tables(int precision, const ReplicaDesc* descs, int n_reps, char* base, cudaStream_t st) {
+  const dim3 grid(16, n_reps);
+  if (precision == FLB_FP64) k_point_tables<double><<<grid, 256, 0, st>>>(descs, base);
+  else k_point_tables<float><<<grid, 256, 0, st>>>(descs, base);
 }
 
 void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int max_items, const char* ws,
