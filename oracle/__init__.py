@@ -23,6 +23,10 @@ Galilean Invariance in Fluctuating Ideal Gas Lattice Boltzmann Simulations":
   (discrete Lyapunov equation per wave vector), which reduces to Eq. 7 at u0 = 0.
 * ``mlp``      -- FP64 forward/backward of the per-site noise-scale network and
   of its correlator loss (not in the paper; a learned extension).
+* ``lb3d``     -- the same scheme on the three-dimensional D3Q15 (which Sec. 3 reports
+  testing) and D3Q19 lattices: Gram-Schmidt moment bases in the Eq. 4 norm, step,
+  thermal start, direct DFT at chosen wave vectors, linear theory per k
+  (``d3q15`` is its D3Q15 view).
 
 Parity status per function is stated in each module header.
 """
