@@ -55,15 +55,27 @@ extern "C" {
                                (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1),
                                (1,-1,-1).  Noise normals 0..10 (Philox calls 0..2)
                                drive moments 4..14.                                  */
+#define FLB_D3Q19 4         /* the other standard 3D lattice (not in the paper): rest,
+                               +-x, +-y, +-z, then the edges (1,1,0), (-1,-1,0),
+                               (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1),
+                               (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1);
+                               weights 1/3, 1/18, 1/36; Gram-Schmidt basis (Eq. 4
+                               norm) of the D3Q15 list up to v^2, then vx v^2, vy v^2,
+                               vz v^2, vx (vy^2 - vz^2), vy (vz^2 - vx^2),
+                               vz (vx^2 - vy^2), v^4, (vx^2 - vy^2) v^2,
+                               (vx^2 + vy^2 - 2 vz^2) v^2 (moments 0-3 conserved, 4-8
+                               shear, 9 bulk, 10-18 ghosts).  Noise normals 0..14
+                               (Philox calls 0..3) drive moments 4..18.              */
 #define FLB_FP64     0      /* full f_i in FP64, all arithmetic FP64                 */
 #define FLB_FP32_DEV 1      /* f_i - w_i rho0 stored and processed in FP32;
                                correlators accumulated in FP64                      */
 
 /* ---- sampled fields (bit f of flb_replica.field_mask) -----------------
  * f = 0..q-1 : moment M^a - M^{a,0}(rho0, u0)   (M^0 = rho, M^1,2 = sqrt3 j)
- * f = 9, 10  : u_x - u0_x, u_y - u0_y           (u = j / rho; not for D3Q15)
- * Fields are taken from the pre-collision (post-streaming) state.  D3Q15
- * samples moments only and accumulates correlators at chosen wave vectors
+ * f = 9, 10  : u_x - u0_x, u_y - u0_y           (u = j / rho; D1Q3, D2Q9)
+ * Fields are taken from the pre-collision (post-streaming) state.  The 3D
+ * lattices (D3Q15, D3Q19) sample moments only (f < q, at most FLB_MAX_FIELDS
+ * of them) and accumulate correlators at chosen wave vectors
  * (flb_set_time_correlator3), not on the full FFT grid.                    */
 #define FLB_FIELD_UX 9
 #define FLB_FIELD_UY 10
@@ -72,15 +84,15 @@ extern "C" {
 /* One independent periodic lattice (a replica).  Several replicas with the
  * same lattice type and precision can run in one context (batched launch). */
 typedef struct {
-  int32_t  lattice;     /* FLB_D1Q3, FLB_D2Q9 or FLB_D3Q15                       */
+  int32_t  lattice;     /* FLB_D1Q3, FLB_D2Q9, FLB_D3Q15 or FLB_D3Q19            */
   int32_t  nx, ny;      /* lattice size; ny = 1 for D1Q3.  nx even.  Sampling
                            needs powers of two: 2 <= nx <= 16384, ny <= 16384  */
-  double   tau[16];     /* relaxation time per moment a (Eq. 5), a < q; entries of
+  double   tau[20];     /* relaxation time per moment a (Eq. 5), a < q; entries of
                            the conserved moments are ignored, the others must be
                            > 1/2                                                 */
   double   rho0;        /* mean density rho-bar (> 0)                            */
   double   kT;          /* temperature; mu = 3 kT scales the noise of Eq. 8      */
-  double   u0[3];       /* mean velocity of the initial state (u0[2]: D3Q15)     */
+  double   u0[3];       /* mean velocity of the initial state (u0[2]: 3D only)   */
   uint64_t seed;        /* Philox key                                            */
   uint32_t stream;      /* Philox counter word 3 (replica stream id)             */
   uint32_t noise_mask;  /* bit a = noise on moment a; bits of conserved moments
@@ -100,8 +112,8 @@ typedef struct {
                            mode 0.
                            2: Eq. 8 with the local density rho(x) of the site in
                            place of rho-bar (the amplitude times sqrt(rho/rho0)).
-                           D3Q15: mode 0 only                                   */
-  int32_t  nz;          /* D3Q15: lattice depth (>= 1); 0 or 1 otherwise.  The
+                           D3Q15, D3Q19: mode 0 only                            */
+  int32_t  nz;          /* D3Q15, D3Q19: lattice depth (>= 1); 0 or 1 otherwise.  The
                            populations are [q][nz][ny][nx], site index
                            (z ny + y) nx + x                                    */
 } flb_replica;
@@ -202,7 +214,7 @@ int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 int flb_time_correlator_bytes(flb_ctx* ctx, int n_lags, int n_k, size_t* bytes_out);
 int flb_set_time_correlator(flb_ctx* ctx, int n_lags, int n_k, const int32_t* kx, const int32_t* ky,
                             void* buf_dev, size_t bytes);
-/* Same with a third component kz (0 <= kz < nz) for D3Q15, whose transforms are
+/* Same with a third component kz (0 <= kz < nz) for D3Q15 / D3Q19, whose transforms are
  * direct sums over the lattice at the chosen wave vectors (no FFT grid); for
  * D1Q3 / D2Q9 kz must be 0.  With n_lags = 1 these are the equal-time correlators
  * C_ab(k) of Eqs. 11-12. */

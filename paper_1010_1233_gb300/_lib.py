@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libflb.so")
 
 FLB_OK, FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_EUNSTABLE, FLB_ETIMEOUT, FLB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-FLB_D1Q3, FLB_D2Q9, FLB_D3Q15 = 1, 2, 3
+FLB_D1Q3, FLB_D2Q9, FLB_D3Q15, FLB_D3Q19 = 1, 2, 3, 4
 FLB_FP64, FLB_FP32_DEV = 0, 1
 FIELD_UX, FIELD_UY = 9, 10
 
@@ -23,7 +23,7 @@ class FlbError(RuntimeError):
 
 
 class flb_replica(ctypes.Structure):
-    _fields_ = [("lattice", c_int32), ("nx", c_int32), ("ny", c_int32), ("tau", c_double * 16),
+    _fields_ = [("lattice", c_int32), ("nx", c_int32), ("ny", c_int32), ("tau", c_double * 20),
                 ("rho0", c_double), ("kT", c_double), ("u0", c_double * 3), ("seed", c_uint64),
                 ("stream", c_uint32), ("noise_mask", c_uint32), ("init_mode", c_uint32),
                 ("field_mask", c_uint32), ("noise_mode", c_uint32), ("nz", c_int32)]

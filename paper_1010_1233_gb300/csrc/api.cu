@@ -36,11 +36,11 @@ void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
-// D3Q15 (lb_d3q15.cu)
-void launch_step3(int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st);
-void launch_init3(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+// D3Q15 / D3Q19 (lb_3d.cu), q = 15 or 19
+void launch_step3(int q, int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st);
+void launch_init3(int q, int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
                   double* sums, double* partial, int64_t V, cudaStream_t st);
-void launch_conserved3(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
+void launch_conserved3(int q, int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
                        double* partial, DevStatus* status, int64_t V, cudaStream_t st);
 size_t point_dft_smem(int precision, int nx, int ny, int nz, int items);
 size_t point_tables_bytes(int precision, int nx, int ny, int nz);
@@ -79,16 +79,24 @@ static const int kVx3[3] = {0, 1, -1};
 static const int kVx15[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
 static const int kVy15[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
 static const int kVz15[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, 1, -1};
+// D3Q19: rest, +-x, +-y, +-z, then the edges in +- pairs (1,1,0), (1,-1,0), (1,0,1), (1,0,-1),
+// (0,1,1), (0,1,-1)
+static const int kVx19[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int kVy19[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int kVz19[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 static double lattice_weight(int q, int i) {
   if (q == 9) return kW9[i];
   if (q == 3) return kW3[i];
+  if (q == 19) return i == 0 ? 1.0 / 3 : (i < 7 ? 1.0 / 18 : 1.0 / 36);
   return i == 0 ? 2.0 / 9 : (i < 7 ? 1.0 / 9 : 1.0 / 72);
 }
 static inline int64_t volume(const ReplicaDesc& d) { return (int64_t)d.nx * d.ny * d.nz; }
-static inline int lattice_q(int lat) { return lat == FLB_D3Q15 ? 15 : (lat == FLB_D2Q9 ? 9 : 3); }
-static inline int first_nonconserved(int lat) { return lat == FLB_D3Q15 ? 4 : (lat == FLB_D2Q9 ? 3 : 2); }
-static constexpr int kMaxPointItems = 2048;    // D3Q15 direct transforms: fields x wave vectors
-static constexpr int kFeqStride = 32;          // doubles per replica: f^0_i(rho0, u0) at i, w_i rho0 at 16 + i
+static inline bool is3d(int lat) { return lat == FLB_D3Q15 || lat == FLB_D3Q19; }
+static inline int lattice_q(int lat) {
+  return lat == FLB_D3Q19 ? 19 : (lat == FLB_D3Q15 ? 15 : (lat == FLB_D2Q9 ? 9 : 3));
+}
+static inline int first_nonconserved(int lat) { return is3d(lat) ? 4 : (lat == FLB_D2Q9 ? 3 : 2); }
+static constexpr int kMaxPointItems = 2048;    // 3D direct transforms: fields x wave vectors
 
 static constexpr int kStepBlock = 256;
 
@@ -105,7 +113,7 @@ struct Layout {
 };
 
 static int field_valid(int lattice, int f) {
-  if (lattice == FLB_D3Q15) return f >= 0 && f < 15;
+  if (is3d(lattice)) return f >= 0 && f < lattice_q(lattice);
   if (lattice == FLB_D2Q9) return f >= 0 && f <= 10;
   return f == 0 || f == 1 || f == 2 || f == FLB_FIELD_UX;
 }
@@ -114,7 +122,7 @@ static int validate(int precision, const flb_replica* reps, int n) {
   if (precision != FLB_FP64 && precision != FLB_FP32_DEV) return set_error(FLB_EINVAL, "unknown precision %d", precision);
   if (!reps || n <= 0) return set_error(FLB_EINVAL, "need at least one replica");
   const int lat = reps[0].lattice;
-  if (lat != FLB_D1Q3 && lat != FLB_D2Q9 && lat != FLB_D3Q15) return set_error(FLB_EINVAL, "unknown lattice %d", lat);
+  if (lat != FLB_D1Q3 && lat != FLB_D2Q9 && !is3d(lat)) return set_error(FLB_EINVAL, "unknown lattice %d", lat);
   for (int r = 0; r < n; ++r) {
     const flb_replica& p = reps[r];
     if (p.lattice != lat) return set_error(FLB_EINVAL, "replica %d: all replicas must share the lattice type", r);
@@ -122,9 +130,9 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.nx < 2 || p.nx % 2) return set_error(FLB_EINVAL, "replica %d: nx must be even and >= 2", r);
     if (lat == FLB_D1Q3 && p.ny != 1) return set_error(FLB_EINVAL, "replica %d: D1Q3 needs ny = 1", r);
     if (lat != FLB_D1Q3 && p.ny < 1) return set_error(FLB_EINVAL, "replica %d: ny must be >= 1", r);
-    if (lat == FLB_D3Q15 ? p.nz < 1 : (p.nz < 0 || p.nz > 1))
-      return set_error(FLB_EINVAL, "replica %d: nz = %d (D3Q15: >= 1; otherwise 0 or 1)", r, p.nz);
-    const int64_t V = (int64_t)p.nx * p.ny * (lat == FLB_D3Q15 ? p.nz : 1);
+    if (is3d(lat) ? p.nz < 1 : (p.nz < 0 || p.nz > 1))
+      return set_error(FLB_EINVAL, "replica %d: nz = %d (D3Q15, D3Q19: >= 1; otherwise 0 or 1)", r, p.nz);
+    const int64_t V = (int64_t)p.nx * p.ny * (is3d(lat) ? p.nz : 1);
     if (V >= (int64_t(1) << 32)) return set_error(FLB_EINVAL, "replica %d: lattice too large", r);
     if (precision == FLB_FP64 && V >= (int64_t(1) << 31))
       return set_error(FLB_EINVAL, "replica %d: lattice too large for the FP64 path", r);
@@ -140,11 +148,11 @@ static int validate(int precision, const flb_replica* reps, int n) {
     if (p.noise_mask >> q) return set_error(FLB_EINVAL, "replica %d: noise_mask has bits beyond moment %d", r, q - 1);
     if (p.init_mode > 1) return set_error(FLB_EINVAL, "replica %d: init_mode must be 0 or 1", r);
     if (p.noise_mode > 2) return set_error(FLB_EINVAL, "replica %d: noise_mode must be 0, 1 or 2", r);
-    if (lat == FLB_D3Q15 && p.noise_mode != 0) return set_error(FLB_EINVAL, "replica %d: D3Q15 has noise_mode 0 only", r);
+    if (is3d(lat) && p.noise_mode != 0) return set_error(FLB_EINVAL, "replica %d: 3D lattices have noise_mode 0 only", r);
     for (int f = 0; f < 32; ++f)
       if (((p.field_mask >> f) & 1) && !field_valid(lat, f))
         return set_error(FLB_EINVAL, "replica %d: field %d not available on this lattice", r, f);
-    if (p.field_mask && lat == FLB_D3Q15) {
+    if (p.field_mask && is3d(lat)) {
       if (__builtin_popcount(p.field_mask) > kMaxFields)
         return set_error(FLB_EINVAL, "replica %d: at most %d sampled fields", r, kMaxFields);
       if (p.nx > 4096 || p.ny > 4096 || p.nz > 4096)
@@ -259,7 +267,7 @@ static int correlated_root(const flb_replica& p, double* out) {
 
 static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   memset(&d, 0, sizeof d);
-  const bool d2 = p.lattice == FLB_D2Q9, d3 = p.lattice == FLB_D3Q15;
+  const bool d2 = p.lattice == FLB_D2Q9, d3 = is3d(p.lattice);
   d.nx = p.nx; d.ny = p.ny; d.log2nx = ilog2(p.nx); d.log2ny = ilog2(p.ny);
   d.nz = d3 ? p.nz : 1;
   d.q = lattice_q(p.lattice);
@@ -276,7 +284,7 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   // moment in deviation storage, where the stored moment is that of f - w rho0
   const double ux = d.u0x, uy = d.u0y, uz = d.u0z, r0 = p.rho0, s3 = std::sqrt(3.0);
   if (d3) {
-    // the equilibrium moments of the D3Q15 basis (lb_d3q15.cu) at (rho0, u0); ghosts 0
+    // the equilibrium moments of the D3Q15 / D3Q19 bases (lb_3d.cu) at (rho0, u0); ghosts 0
     const double m[10] = {r0, s3 * r0 * ux, s3 * r0 * uy, s3 * r0 * uz, 1.5 * r0 * (ux * ux - uy * uy),
                           0.5 * s3 * r0 * (ux * ux + uy * uy - 2 * uz * uz), 3 * r0 * ux * uy, 3 * r0 * uy * uz,
                           3 * r0 * uz * ux, 0.5 * std::sqrt(6.0) * r0 * (ux * ux + uy * uy + uz * uz)};
@@ -356,8 +364,8 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     bool all4 = true;
     for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
     L.vec = all4 ? 4 : 2;
-  } else if (precision == FLB_FP32_DEV && lat == FLB_D3Q15) {
-    bool all4 = true;                            // nx is even
+  } else if (precision == FLB_FP32_DEV && is3d(lat)) {
+    bool all4 = lat == FLB_D3Q15;                // nx is even; D3Q19 at vec 4 spills registers
     for (int r = 0; r < n; ++r) all4 = all4 && reps[r].nx % 4 == 0;
     L.vec = all4 ? 4 : 2;
   }
@@ -458,24 +466,25 @@ struct flb_ctx {
   std::vector<float> mlp_host;
   TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
   int64_t tc_off_sums0 = 0, tc_bytes = 0;      // start of the sums (first replica) and buffer size
-  size_t tc_smem = 0;                          // D3Q15 direct transforms: dynamic shared memory
+  size_t tc_smem = 0;                          // 3D direct transforms: dynamic shared memory
 };
 
 static ReplicaDesc* descs_dev(flb_ctx* c) { return reinterpret_cast<ReplicaDesc*>(c->ws + c->L.off_descs); }
 static DevStatus* status_dev(flb_ctx* c) { return reinterpret_cast<DevStatus*>(c->ws + c->L.off_status); }
 
 static void feq0_host(const flb_replica& p, double out[kFeqStride]) {
-  // Eq. 2 (c = 1) at (rho0, u0) at [i], and w_i rho0 at [16 + i]
-  const bool d2 = p.lattice == FLB_D2Q9, d3 = p.lattice == FLB_D3Q15;
+  // Eq. 2 (c = 1) at (rho0, u0) at [i], and w_i rho0 at [kFeqW + i]
+  const bool d2 = p.lattice == FLB_D2Q9, d3 = is3d(p.lattice), q19 = p.lattice == FLB_D3Q19;
   const int q = lattice_q(p.lattice);
   const double ux = p.u0[0], uy = (d2 || d3) ? p.u0[1] : 0.0, uz = d3 ? p.u0[2] : 0.0;
   for (int i = 0; i < kFeqStride; ++i) out[i] = 0.0;
   for (int i = 0; i < q; ++i) {
     const double w = lattice_weight(q, i);
-    const double cu = d3 ? kVx15[i] * ux + kVy15[i] * uy + kVz15[i] * uz
-                         : (d2 ? kVx9[i] * ux + kVy9[i] * uy : kVx3[i] * ux);
+    const double cu = q19 ? kVx19[i] * ux + kVy19[i] * uy + kVz19[i] * uz
+                    : d3  ? kVx15[i] * ux + kVy15[i] * uy + kVz15[i] * uz
+                          : (d2 ? kVx9[i] * ux + kVy9[i] * uy : kVx3[i] * ux);
     out[i] = p.rho0 * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy + uz * uz));
-    out[16 + i] = w * p.rho0;
+    out[kFeqW + i] = w * p.rho0;
   }
 }
 
@@ -498,7 +507,7 @@ static int reset_stats_async(flb_ctx* c) {
   return FLB_OK;
 }
 
-// Blocks of the D3Q15 direct transforms: FLB_POINT_BPS per SM at most, no more than the
+// Blocks of the 3D direct transforms: FLB_POINT_BPS per SM at most, no more than the
 // rows, and partial sums of at most 64 MB per replica.
 #ifndef FLB_POINT_BPS
 #define FLB_POINT_BPS 8
@@ -515,7 +524,7 @@ static int point_blocks(const flb_ctx* c, int n_k) {
 }
 
 // Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | kz [n_k] | rings
-// of every replica | D3Q15 block partials and phase tables of every replica | sums of
+// of every replica | 3D block partials and phase tables of every replica | sums of
 // every replica (contiguous, so a reset is one memset).
 static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vector<int64_t>* ring,
                                 std::vector<int64_t>* sums, int64_t* sums0, std::vector<int64_t>* part = nullptr,
@@ -528,7 +537,7 @@ static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vect
     if (ring) (*ring)[r] = off;
     off = align256(off + 16 * (int64_t)n_lags * c->L.desc[r].n_fields * n_k);
   }
-  if (c->lattice == FLB_D3Q15) {
+  if (is3d(c->lattice)) {
     const int G = point_blocks(c, n_k);
     for (int r = 0; r < c->n; ++r) {
       const ReplicaDesc& d = c->L.desc[r];
@@ -576,7 +585,7 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
   if (n_lags < 1 || n_lags > 65536) return set_error(FLB_EINVAL, "n_lags must be in 1..65536 (0 = off)");
   if (n_k < 1 || n_k > 4096 || !kx || !ky) return set_error(FLB_EINVAL, "need 1..4096 wave vectors");
   if (!buf_dev || (reinterpret_cast<uintptr_t>(buf_dev) & 255)) return set_error(FLB_EINVAL, "buf_dev must be 256-B aligned");
-  const bool d3 = c->lattice == FLB_D3Q15;
+  const bool d3 = is3d(c->lattice);
   std::vector<int32_t> kzv(n_k, 0);
   if (kz) kzv.assign(kz, kz + n_k);
   size_t smem = 0;
@@ -669,7 +678,7 @@ int flb_get_time_correlator(flb_ctx* c, int replica, int fa, int fb, double* hos
                   "read sums");
   if (rc) return rc;
   // moments: mu rho0; velocities (D2Q9, D1Q3 field ids 9, 10): kT / rho0
-  auto var = [&](int f) { return (f < 9 || c->lattice == FLB_D3Q15) ? d.mu * d.rho0 : d.kT / d.rho0; };
+  auto var = [&](int f) { return (f < 9 || is3d(c->lattice)) ? d.mu * d.rho0 : d.kT / d.rho0; };
   const double vv = var(fa) * var(fb);
   const double V = (double)volume(d);
   const double norm = vv > 0 ? 1.0 / (V * std::sqrt(vv)) : 1.0 / V;
@@ -738,7 +747,8 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
     if (rc) break;
     const double* feq0 = reinterpret_cast<const double*>(c->ws + Lc.off_feq0) + kFeqStride * r;
     double* partial = reinterpret_cast<double*>(c->ws + Lc.off_partial);
-    if (c->lattice == FLB_D3Q15) launch_init3(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode, feq0, sums, partial, V, st);
+    if (is3d(c->lattice))
+      launch_init3(d.q, precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode, feq0, sums, partial, V, st);
     else launch_init(precision, descs_dev(c), r, c->ws, (int)reps[r].init_mode, feq0, sums, partial, V, st);
     if (d.n_pairs) {
       launch_twiddles(precision, c->ws + d.off_tw_x, d.nx, st);
@@ -756,7 +766,7 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
 // Issue one step (and its sampling) on stream st.  With S.step_dev set, S.step is the
 // offset from the device step counter (graph capture); otherwise the absolute step.
 static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S, bool sample, cudaStream_t st) {
-  if (c->lattice == FLB_D3Q15) launch_step3(c->precision, vec, S, sample, st);
+  if (is3d(c->lattice)) launch_step3(c->L.q, c->precision, vec, S, sample, st);
   else if (staged) launch_step_bulk(vec, S, sample, c->mlp_on, st);
   else launch_step(c->lattice, c->precision, vec, S, sample, c->mlp_on, st);
 }
@@ -764,7 +774,7 @@ static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S
 static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
   const Layout& L = c->L;
   launch_step_any(c, L.vec, L.staged, S, sample, st);
-  if (sample && c->lattice == FLB_D3Q15) {
+  if (sample && is3d(c->lattice)) {
     // direct transforms at the chosen wave vectors, then the time correlators
     if (c->tc.base) {
       int maxF = 0;
@@ -922,8 +932,8 @@ int flb_get_correlator(flb_ctx* c, int replica, int fa, int fb, double* host_out
   if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
-  if (c->lattice == FLB_D3Q15)
-    return set_error(FLB_EINVAL, "D3Q15 correlators are taken at chosen wave vectors (flb_set_time_correlator3)");
+  if (is3d(c->lattice))
+    return set_error(FLB_EINVAL, "3D correlators are taken at chosen wave vectors (flb_set_time_correlator3)");
   int sa = -1, sb = -1;
   for (int s = 0; s < (int)d.n_fields; ++s) { if (d.field_id[s] == fa) sa = s; if (d.field_id[s] == fb) sb = s; }
   if (sa < 0 || sb < 0) return set_error(FLB_EINVAL, "fields %d, %d are not both sampled", fa, fb);
@@ -993,7 +1003,7 @@ int flb_get_populations_window(flb_ctx* c, int replica, int x0, int y0, int w, i
   if (!c || !host_out) return set_error(FLB_EINVAL, "NULL argument");
   if (replica < 0 || replica >= c->n) return set_error(FLB_EINVAL, "replica %d out of range", replica);
   const ReplicaDesc& d = c->L.desc[replica];
-  if (c->lattice == FLB_D3Q15) return set_error(FLB_EINVAL, "windows are read from D1Q3 / D2Q9 lattices");
+  if (is3d(c->lattice)) return set_error(FLB_EINVAL, "windows are read from D1Q3 / D2Q9 lattices");
   if (w <= 0 || h <= 0 || x0 < 0 || y0 < 0 || x0 + w > d.nx || y0 + h > d.ny)
     return set_error(FLB_EINVAL, "window [%d,%d)x[%d,%d) outside the %dx%d lattice", x0, x0 + w, y0, y0 + h, d.nx, d.ny);
   int rc = flb_sync(c);
@@ -1061,8 +1071,8 @@ int flb_get_conserved(flb_ctx* c, int replica, double* out4) {
   const ReplicaDesc& d = c->L.desc[replica];
   double* sums = reinterpret_cast<double*>(c->ws + c->L.off_sums) + 4 * replica;
   double* partial = reinterpret_cast<double*>(c->ws + c->L.off_partial);
-  if (c->lattice == FLB_D3Q15)
-    launch_conserved3(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, partial, status_dev(c),
+  if (is3d(c->lattice))
+    launch_conserved3(d.q, c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, partial, status_dev(c),
                       volume(d), c->stream);
   else
     launch_conserved(c->precision, descs_dev(c), replica, c->ws, (int)(c->step & 1), sums, partial, status_dev(c),
@@ -1187,7 +1197,7 @@ int flb_set_step_config(flb_ctx* c, int vec, int grid_blocks, int staged) {
   if (staged != 0 && staged != 1) return set_error(FLB_EINVAL, "staged must be 0 or 1");
   if (staged && !staged_ok(c)) return set_error(FLB_EINVAL, "the staged kernel needs the FP32 D2Q9 path, every nx a multiple of 4");
   if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice == FLB_D1Q3))
-    return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9 or D3Q15 path");
+    return set_error(FLB_EINVAL, "vec > 1 needs the FP32 D2Q9, D3Q15 or D3Q19 path");
   for (int r = 0; r < c->n && !staged; ++r) {
     if (c->L.desc[r].nx % vec) return set_error(FLB_EINVAL, "replica %d: nx not a multiple of vec = %d", r, vec);
     // one thread per site: unit indices are 32-bit

@@ -20,7 +20,8 @@ constexpr int kMlpOut = 6;
 constexpr int kMlpWeights = kMlpHidden * 3 + kMlpHidden * kMlpHidden + kMlpOut * kMlpHidden;  // 1312
 constexpr int kMlpBiases = kMlpHidden + kMlpHidden + kMlpOut;                               // 70
 
-constexpr int kMaxQ = 16;                    // moments per site (D3Q15: 15)
+constexpr int kMaxQ = 20;                    // moments per site (D3Q19: 19)
+constexpr int kFeqW = 24, kFeqStride = 48;   // per replica: f^0_i(rho0, u0) at [i], w_i rho0 at [kFeqW + i]
 constexpr int kCoRho0 = 0, kCoU0x = 1, kCoU0y = 2, kCoU0z = 3;
 constexpr int kCoInvTau = 4, kCoAmp = kCoInvTau + kMaxQ, kCoMref = kCoAmp + kMaxQ;
 constexpr int kCoNoiseR = kCoMref + kMaxQ;   // 6 x 6 correlated-noise root (noise_mode 1), row-major

@@ -1,23 +1,36 @@
-// D3Q15 fluctuating lattice Boltzmann: the scheme of Sec. 2 (pull streaming, Eq. 1;
-// relaxation of the non-conserved moments, Eq. 5; noise of Eq. 8 on each of them) on
-// the three-dimensional lattice that Sec. 3 reports testing without printing its tables.
+// Three-dimensional fluctuating lattice Boltzmann: the scheme of Sec. 2 (pull streaming,
+// Eq. 1; relaxation of the non-conserved moments, Eq. 5; noise of Eq. 8 on each of them) on
+// D3Q15, the lattice that Sec. 3 reports testing without printing its tables, and on D3Q19.
 //
-// Velocities (order of the population index i): rest, +x, -x, +y, -y, +z, -z, (1,1,1),
-// (-1,-1,-1), (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); weights
-// 2/9, 1/9 (axes), 1/72 (corners), so that sum_i w_i v_i v_i = 1/3 as in Eq. 2.
+// D3Q15 velocities (order of the population index i): rest, +x, -x, +y, -y, +z, -z,
+// (1,1,1), (-1,-1,-1), (1,1,-1), (-1,-1,1), (1,-1,1), (-1,1,-1), (-1,1,1), (1,-1,-1); weights
+// 2/9, 1/9 (axes), 1/72 (corners).
+// D3Q19 velocities: rest, +x, -x, +y, -y, +z, -z, then the edges (1,1,0), (-1,-1,0),
+// (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1),
+// (0,-1,1); weights 1/3, 1/18 (axes), 1/36 (edges).  Both give sum_i w_i v_i v_i = 1/3 as
+// Eq. 2 needs.
 //
 // Moments: the basis orthonormal in the weighted norm of Eq. 4 that Gram-Schmidt gives
 // from the polynomials 1, vx, vy, vz, vx^2 - vy^2, vx^2 + vy^2 - 2 vz^2, vx vy, vy vz,
-// vz vx, v^2, vx v^2, vy v^2, vz v^2, vx vy vz, v^4 in that order.  Written out:
+// vz vx, v^2 and then the ghosts (D3Q15: vx v^2, vy v^2, vz v^2, vx vy vz, v^4; D3Q19:
+// vx v^2, vy v^2, vz v^2, vx (vy^2 - vz^2), vy (vz^2 - vx^2), vz (vx^2 - vy^2), v^4,
+// (vx^2 - vy^2) v^2, (vx^2 + vy^2 - 2 vz^2) v^2).  Written out (moment_row3), both share
 //   m^0 = 1, m^{1,2,3} = sqrt3 v, m^4 = 3/2 (vx^2 - vy^2), m^5 = sqrt3/2 (vx^2 + vy^2 - 2 vz^2),
-//   m^6 = 3 vx vy, m^7 = 3 vy vz, m^8 = 3 vz vx, m^9 = sqrt6/2 (v^2 - 1),
-//   m^{10,11,12} = sqrt6/4 v_a (3 v^2 - 5), m^13 = 3 vx vy vz, m^14 = sqrt2/4 (3 v^4 - 9 v^2 + 4).
-// The equilibrium moments (Eq. 10 in three dimensions) are those of f^0 of Eq. 2:
+//   m^6 = 3 vx vy, m^7 = 3 vy vz, m^8 = 3 vz vx, m^9 = sqrt6/2 (v^2 - 1);
+// D3Q15 ghosts: m^{10,11,12} = sqrt6/4 v_a (3 v^2 - 5), m^13 = 3 vx vy vz,
+//   m^14 = sqrt2/4 (3 v^4 - 9 v^2 + 4);
+// D3Q19 ghosts: m^{10,11,12} = sqrt6/2 v_a (3 v^2 - 5), m^13 = 3/sqrt2 vx (vy^2 - vz^2),
+//   m^14 = 3/sqrt2 vy (vz^2 - vx^2), m^15 = 3/sqrt2 vz (vx^2 - vy^2),
+//   m^16 = sqrt2/2 (3 v^4 - 6 v^2 + 1), m^17 = 3/2 (vx^2 - vy^2)(2 v^2 - 3),
+//   m^18 = sqrt3/2 (vx^2 + vy^2 - 2 vz^2)(2 v^2 - 3).
+// The equilibrium moments (Eq. 10 in three dimensions) are those of f^0 of Eq. 2, the same
+// on both lattices:
 //   M^{4..9,0} = rho (3/2 (ux^2 - uy^2), sqrt3/2 (ux^2 + uy^2 - 2 uz^2), 3 ux uy, 3 uy uz,
-//                     3 uz ux, sqrt6/2 u^2), and 0 for the ghosts 10..14 (f^0 / w is a
-//   polynomial of degree 2 in v, to which the ghost rows are orthogonal).
-// Noise: normals 0..10 of Philox calls 0..2 (counter site, step, call, stream) drive
-// moments 4..14.  Site index (z ny + y) nx + x; populations [15][nz][ny][nx].
+//                     3 uz ux, sqrt6/2 u^2), and 0 for the ghosts (f^0 / w is a polynomial
+//   of degree 2 in v, to which the ghost rows are orthogonal).
+// Noise: normals 0, 1, ... of Philox calls 0, 1, ... (counter site, step, call, stream)
+// drive moments 4, 5, ... (11 normals from 3 calls on D3Q15, 15 from 4 calls on D3Q19).
+// Site index (z ny + y) nx + x; populations [q][nz][ny][nx].
 //
 // Sampling: the step writes the moment fields (pre-collision state, minus M^{a,0}(rho0,
 // u0)); k_point_dft forms X_f(k) = sum_x X_f(x) exp(-i k.x) (Eq. 11) at the chosen wave
@@ -32,17 +45,35 @@
 
 namespace flb {
 
-// velocity components of population i: 2 bits per population, value + 1
-__host__ __device__ constexpr int v3x(int i) { return (int)((0x20889549u >> (2 * i)) & 3u) - 1; }
-__host__ __device__ constexpr int v3y(int i) { return (int)((0x0a089495u >> (2 * i)) & 3u) - 1; }
-__host__ __device__ constexpr int v3z(int i) { return (int)((0x08a08955u >> (2 * i)) & 3u) - 1; }
-static_assert(v3x(7) == 1 && v3y(7) == 1 && v3z(7) == 1, "corner (1,1,1)");
-static_assert(v3x(13) == -1 && v3y(13) == 1 && v3z(13) == 1, "corner (-1,1,1)");
-static_assert(v3x(6) == 0 && v3y(6) == 0 && v3z(6) == -1, "axis -z");
+// velocity components of population i of the Q-velocity lattice: 2 bits per population,
+// value + 1
+template <int Q> __host__ __device__ constexpr int v3x(int i) {
+  return (int)(((Q == 15 ? 0x20889549ull : 0x1548889549ull) >> (2 * i)) & 3u) - 1;
+}
+template <int Q> __host__ __device__ constexpr int v3y(int i) {
+  return (int)(((Q == 15 ? 0x0a089495ull : 0x895609495ull) >> (2 * i)) & 3u) - 1;
+}
+template <int Q> __host__ __device__ constexpr int v3z(int i) {
+  return (int)(((Q == 15 ? 0x08a08955ull : 0x20a0954955ull) >> (2 * i)) & 3u) - 1;
+}
+static_assert(v3x<15>(7) == 1 && v3y<15>(7) == 1 && v3z<15>(7) == 1, "corner (1,1,1)");
+static_assert(v3x<15>(13) == -1 && v3y<15>(13) == 1 && v3z<15>(13) == 1, "corner (-1,1,1)");
+static_assert(v3x<15>(6) == 0 && v3y<15>(6) == 0 && v3z<15>(6) == -1, "axis -z");
+static_assert(v3x<19>(9) == 1 && v3y<19>(9) == -1 && v3z<19>(9) == 0, "edge (1,-1,0)");
+static_assert(v3x<19>(14) == -1 && v3y<19>(14) == 0 && v3z<19>(14) == 1, "edge (-1,0,1)");
+static_assert(v3x<19>(18) == 0 && v3y<19>(18) == -1 && v3z<19>(18) == 1, "edge (0,-1,1)");
 
-__host__ __device__ constexpr double w15(int i) { return i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0); }
+template <int Q> __host__ __device__ constexpr double w3(int i) {
+  return Q == 15 ? (i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0))
+                 : (i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0));
+}
+// noise normals (non-conserved moments) and Philox calls of the step; calls of the thermal start
+template <int Q> struct Lat3 {
+  static constexpr int kNC = Q - 4, kCalls = (Q - 4 + 3) / 4, kThermalCalls = (Q + 3) / 4;
+};
 
 // m_i^a of the basis above at velocity (vx, vy, vz)
+template <int Q>
 __host__ __device__ inline double moment_row3(int a, int vx, int vy, int vz) {
   const double S2 = 1.4142135623730950488, S3 = 1.7320508075688772935, S6 = 2.4494897427831780982;
   const double v2 = vx * vx + vy * vy + vz * vz;
@@ -57,11 +88,27 @@ __host__ __device__ inline double moment_row3(int a, int vx, int vy, int vz) {
     case 7: return 3.0 * vy * vz;
     case 8: return 3.0 * vz * vx;
     case 9: return 0.5 * S6 * (v2 - 1.0);
-    case 10: return 0.25 * S6 * vx * (3.0 * v2 - 5.0);
-    case 11: return 0.25 * S6 * vy * (3.0 * v2 - 5.0);
-    case 12: return 0.25 * S6 * vz * (3.0 * v2 - 5.0);
-    case 13: return 3.0 * vx * vy * vz;
-    default: return 0.25 * S2 * (3.0 * v2 * v2 - 9.0 * v2 + 4.0);
+    default: break;
+  }
+  if (Q == 15) {
+    switch (a) {
+      case 10: return 0.25 * S6 * vx * (3.0 * v2 - 5.0);
+      case 11: return 0.25 * S6 * vy * (3.0 * v2 - 5.0);
+      case 12: return 0.25 * S6 * vz * (3.0 * v2 - 5.0);
+      case 13: return 3.0 * vx * vy * vz;
+      default: return 0.25 * S2 * (3.0 * v2 * v2 - 9.0 * v2 + 4.0);
+    }
+  }
+  switch (a) {
+    case 10: return 0.5 * S6 * vx * (3.0 * v2 - 5.0);
+    case 11: return 0.5 * S6 * vy * (3.0 * v2 - 5.0);
+    case 12: return 0.5 * S6 * vz * (3.0 * v2 - 5.0);
+    case 13: return 1.5 * S2 * vx * (vy * vy - vz * vz);
+    case 14: return 1.5 * S2 * vy * (vz * vz - vx * vx);
+    case 15: return 1.5 * S2 * vz * (vx * vx - vy * vy);
+    case 16: return 0.5 * S2 * (3.0 * v2 * v2 - 6.0 * v2 + 1.0);
+    case 17: return 1.5 * (vx * vx - vy * vy) * (2.0 * v2 - 3.0);
+    default: return 0.5 * S3 * (vx * vx + vy * vy - 2.0 * vz * vz) * (2.0 * v2 - 3.0);
   }
 }
 
@@ -69,31 +116,31 @@ __host__ __device__ inline double moment_row3(int a, int vx, int vy, int vz) {
 // Pull streaming f_i(x) = f*_i(x - v_i) on the periodic box: the source row of population
 // i is (y - v_iy, z - v_iz); the x shift is taken by warp shuffle from the adjacent lane,
 // with one extra load at warp and row edges (as in the D2Q9 kernels).
-template <typename R, int VEC>
-__device__ __forceinline__ void pull_d3q15(const R* __restrict__ src, int64_t vol, int nx, int ny, int nz, int y,
-                                           int z, const UnitPos& u, R (&f)[15][VEC]) {
-  R v[15][VEC], e[15];
+template <int Q, typename R, int VEC>
+__device__ __forceinline__ void pull_3d(const R* __restrict__ src, int64_t vol, int nx, int ny, int nz, int y, int z,
+                                        const UnitPos& u, R (&f)[Q][VEC]) {
+  R v[Q][VEC], e[Q];
   const int x0 = u.x0;
 #pragma unroll
-  for (int i = 0; i < 15; ++i) {
-    int ys = y - v3y(i), zs = z - v3z(i);
+  for (int i = 0; i < Q; ++i) {
+    int ys = y - v3y<Q>(i), zs = z - v3z<Q>(i);
     ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
     zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
     const R* row = src + i * vol + ((int64_t)zs * ny + ys) * nx;
     VecIO<R, VEC>::ld(row + x0, v[i]);
     e[i] = (R)0;
-    if (v3x(i) == 1) {
+    if (v3x<Q>(i) == 1) {
       if (!u.left_in_warp) e[i] = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
-    } else if (v3x(i) == -1) {
+    } else if (v3x<Q>(i) == -1) {
       if (!u.right_in_warp) e[i] = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
     }
   }
 #pragma unroll
-  for (int i = 0; i < 15; ++i) {
-    if (v3x(i) == 0) {
+  for (int i = 0; i < Q; ++i) {
+    if (v3x<Q>(i) == 0) {
 #pragma unroll
       for (int s = 0; s < VEC; ++s) f[i][s] = v[i][s];
-    } else if (v3x(i) == 1) {
+    } else if (v3x<Q>(i) == 1) {
       const R left = __shfl_up_sync(0xffffffffu, v[i][VEC - 1], 1);
       f[i][0] = u.left_in_warp ? left : e[i];
 #pragma unroll
@@ -107,7 +154,7 @@ __device__ __forceinline__ void pull_d3q15(const R* __restrict__ src, int64_t vo
   }
 }
 
-// Collision of one site in place (Eqs. 5, 8): moments in closed form, relaxation of
+// D3Q15 collision of one site in place (Eqs. 5, 8): moments in closed form, relaxation of
 // M^4..M^14 towards the equilibrium moments, noise amp_a N_{a-4}, and the back transform
 // f*_i = f_i + w_i sum_a m_i^a Delta M^a.  fld: the 15 moments minus their reference
 // values (SAMPLE).  DEV: g holds f - w rho0 (the non-conserved moments are the same).
@@ -197,30 +244,154 @@ __device__ __forceinline__ void collide_d3q15(const ReplicaDesc& d, R (&g)[15], 
   }
 }
 
-// The eleven unit normals of a site (Philox calls 0..2; the twelfth is not used).
-template <typename R>
-__device__ __forceinline__ void normals_d3q15(const ReplicaDesc& d, uint32_t site, uint32_t step, R (&n)[11]) {
-  const uint4 w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
-  const uint4 w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
-  const uint4 w2 = philox4x32_10(site, step, 2u, d.stream, d.seed_lo, d.seed_hi);
-  R spare;
-  box_muller(w0.x, w0.y, n[0], n[1]);
-  box_muller(w0.z, w0.w, n[2], n[3]);
-  box_muller(w1.x, w1.y, n[4], n[5]);
-  box_muller(w1.z, w1.w, n[6], n[7]);
-  box_muller(w2.x, w2.y, n[8], n[9]);
-  box_muller(w2.z, w2.w, n[10], spare);
-  (void)spare;
+// D3Q19 collision of one site in place: as collide_d3q15, on the 19 populations grouped
+// into the rest population and nine +-v pairs (sums e, differences o): the even moments
+// (0, 4-9, 16-18) are sums of e, the odd ones (1-3, 10-15) sums of o.
+template <typename R, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void collide_d3q19(const ReplicaDesc& d, R (&g)[19], bool noisy, const R (&n)[15],
+                                              R (&fld)[19]) {
+  const R S2 = (R)1.4142135623730950488, S3 = (R)1.7320508075688772935, S6 = (R)2.4494897427831780982;
+  const R hS2 = (R)0.70710678118654752440, hS3 = (R)0.86602540378443864676, hS6 = (R)1.2247448713915890491;
+  const R t2 = (R)2.1213203435596425732;           // 3 / sqrt2
+  // pair sums and differences: axes x, y, z; edges A (1,1,0), B (1,-1,0), C (1,0,1),
+  // D (1,0,-1), E (0,1,1), F (0,1,-1) (first member of each pair)
+  const R ax = g[1] + g[2], ay = g[3] + g[4], az = g[5] + g[6];
+  const R ox = g[1] - g[2], oy = g[3] - g[4], oz = g[5] - g[6];
+  const R eA = g[7] + g[8], eB = g[9] + g[10], eC = g[11] + g[12], eD = g[13] + g[14], eE = g[15] + g[16],
+          eF = g[17] + g[18];
+  const R dA = g[7] - g[8], dB = g[9] - g[10], dC = g[11] - g[12], dD = g[13] - g[14], dE = g[15] - g[16],
+          dF = g[17] - g[18];
+  const R Sxy = eA + eB, Sxz = eC + eD, Syz = eE + eF, S = (Sxy + Sxz) + Syz;
+  const R aa = (ax + ay) + az;
+  const R sum = (g[0] + aa) + S;
+  const R cx = (dA + dB) + (dC + dD), cy = (dA - dB) + (dE + dF), cz = (dC - dD) + (dE - dF);
+  const R jx = ox + cx, jy = oy + cy, jz = oz + cz;
+  const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
+  const R irho = (R)1 / rho;
+  const R ux = jx * irho, uy = jy * irho, uz = jz * irho;
+  // non-conserved moments
+  const R dxy = ax - ay, sxz = Sxz - Syz, pxy = ax + ay, t5 = (R)2 * Sxy - (Sxz + Syz);
+  const R M4 = (R)1.5 * (dxy + sxz);
+  const R M5 = hS3 * ((pxy - (R)2 * az) + t5);
+  const R M6 = (R)3 * (eA - eB), M7 = (R)3 * (eE - eF), M8 = (R)3 * (eC - eD);
+  const R M9 = hS6 * (S - g[0]);
+  const R M10 = hS6 * (cx - (R)2 * ox), M11 = hS6 * (cy - (R)2 * oy), M12 = hS6 * (cz - (R)2 * oz);
+  const R M13 = t2 * ((dA + dB) - (dC + dD));
+  const R M14 = t2 * ((dB - dA) + (dE + dF));
+  const R M15 = t2 * ((dC - dD) + (dF - dE));
+  const R M16 = hS2 * ((g[0] - (R)2 * aa) + S);
+  const R M17 = (R)1.5 * (sxz - dxy);
+  const R M18 = hS3 * (((R)2 * az - pxy) + t5);
+  // equilibrium moments
+  const R E4 = (R)1.5 * (jx * ux - jy * uy);
+  const R E5 = hS3 * ((jx * ux + jy * uy) - (R)2 * jz * uz);
+  const R E6 = (R)3 * jx * uy, E7 = (R)3 * jy * uz, E8 = (R)3 * jz * ux;
+  const R E9 = hS6 * ((jx * ux + jy * uy) + jz * uz);
+  if constexpr (SAMPLE) {
+    const R mom[19] = {sum, S3 * jx, S3 * jy, S3 * jz, M4, M5, M6, M7, M8, M9, M10, M11, M12, M13, M14, M15, M16,
+                       M17, M18};
+#pragma unroll
+    for (int a = 0; a < 19; ++a) fld[a] = mom[a] - coef<R>(d, kCoMref + a);
+  }
+  // relaxation (Eq. 5) and noise (Eq. 8)
+  R D[15] = {E4 - M4, E5 - M5, E6 - M6, E7 - M7, E8 - M8, E9 - M9, -M10, -M11, -M12, -M13, -M14, -M15, -M16,
+             -M17, -M18};
+#pragma unroll
+  for (int c = 0; c < 15; ++c) {
+    D[c] *= coef<R>(d, kCoInvTau + 4 + c);
+    if (noisy) D[c] += coef<R>(d, kCoAmp + 4 + c) * n[c];
+  }
+  const R D4 = D[0], D5 = D[1], D6 = D[2], D7 = D[3], D8 = D[4], D9 = D[5], D10 = D[6], D11 = D[7], D12 = D[8];
+  const R D13 = D[9], D14 = D[10], D15 = D[11], D16 = D[12], D17 = D[13], D18 = D[14];
+  // back transform, n_i^a = w_i m_i^a: f(+-v) += w (E(v) +- O(v))
+  const R wr = (R)1 / (R)3, wa = (R)1 / (R)18, we = (R)1 / (R)36;
+  g[0] = g[0] + wr * (hS2 * D16 - hS6 * D9);
+  const R p417 = (R)1.5 * (D4 - D17), p518 = D5 - D18, q16 = S2 * D16;
+  {
+    const R E = (p417 + hS3 * p518) - q16, O = -S6 * D10;                   // x
+    g[1] = g[1] + wa * (E + O);
+    g[2] = g[2] + wa * (E - O);
+  }
+  {
+    const R E = (hS3 * p518 - p417) - q16, O = -S6 * D11;                   // y
+    g[3] = g[3] + wa * (E + O);
+    g[4] = g[4] + wa * (E - O);
+  }
+  {
+    const R E = -S3 * p518 - q16, O = -S6 * D12;                            // z
+    g[5] = g[5] + wa * (E + O);
+    g[6] = g[6] + wa * (E - O);
+  }
+  const R G = hS6 * D9 + hS2 * D16;                  // common to the edges
+  const R s518 = D5 + D18, s417 = (R)1.5 * (D4 + D17);
+  const R Gxy = G + S3 * s518, Gxz = (G + s417) - hS3 * s518, Gyz = (G - s417) - hS3 * s518;
+  const R h10 = hS6 * D10, h11 = hS6 * D11, h12 = hS6 * D12;
+  const R k13 = t2 * D13, k14 = t2 * D14, k15 = t2 * D15;
+  {
+    const R E = Gxy + (R)3 * D6, O = (h10 + h11) + (k13 - k14);          // A (1,1,0)
+    g[7] = g[7] + we * (E + O);
+    g[8] = g[8] + we * (E - O);
+  }
+  {
+    const R E = Gxy - (R)3 * D6, O = (h10 - h11) + (k13 + k14);          // B (1,-1,0)
+    g[9] = g[9] + we * (E + O);
+    g[10] = g[10] + we * (E - O);
+  }
+  {
+    const R E = Gxz + (R)3 * D8, O = (h10 + h12) + (k15 - k13);          // C (1,0,1)
+    g[11] = g[11] + we * (E + O);
+    g[12] = g[12] + we * (E - O);
+  }
+  {
+    const R E = Gxz - (R)3 * D8, O = (h10 - h12) - (k13 + k15);          // D (1,0,-1)
+    g[13] = g[13] + we * (E + O);
+    g[14] = g[14] + we * (E - O);
+  }
+  {
+    const R E = Gyz + (R)3 * D7, O = (h11 + h12) + (k14 - k15);          // E (0,1,1)
+    g[15] = g[15] + we * (E + O);
+    g[16] = g[16] + we * (E - O);
+  }
+  {
+    const R E = Gyz - (R)3 * D7, O = (h11 - h12) + (k14 + k15);          // F (0,1,-1)
+    g[17] = g[17] + we * (E + O);
+    g[18] = g[18] + we * (E - O);
+  }
+}
+
+template <int Q, typename R, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void collide_3d(const ReplicaDesc& d, R (&g)[Q], bool noisy, const R (&n)[Q - 4],
+                                           R (&fld)[Q]) {
+  if constexpr (Q == 15) collide_d3q15<R, DEV, SAMPLE>(d, g, noisy, n, fld);
+  else collide_d3q19<R, DEV, SAMPLE>(d, g, noisy, n, fld);
+}
+
+// The Q - 4 unit normals of a site (Philox calls 0, 1, ...; the rest of the last call's
+// words are not used).
+template <int Q, typename R>
+__device__ __forceinline__ void normals_3d(const ReplicaDesc& d, uint32_t site, uint32_t step, R (&n)[Q - 4]) {
+  constexpr int NC = Q - 4;
+#pragma unroll
+  for (int c = 0; c < Lat3<Q>::kCalls; ++c) {
+    const uint4 w = philox4x32_10(site, step, (uint32_t)c, d.stream, d.seed_lo, d.seed_hi);
+    R a, b, e, h;
+    box_muller(w.x, w.y, a, b);
+    box_muller(w.z, w.w, e, h);
+    const R v[4] = {a, b, e, h};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (4 * c + k < NC) n[4 * c + k] = v[k];
+  }
 }
 
 // One thread = VEC consecutive sites of a row (y, z); a persistent grid loops over virtual
 // blocks of kStepThreads units, each within one replica.  ONE: a single replica whose
 // description is the kernel argument (constant bank).
-template <typename R, bool DEV, int VEC, bool SAMPLE, bool ONE>
+template <int Q, typename R, bool DEV, int VEC, bool SAMPLE, bool ONE>
 __global__ void __launch_bounds__(kStepThreads, FLB_STEP3_MINB)
-k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
-             const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_vblocks, char* __restrict__ ws, int parity,
-             uint32_t step, const uint64_t* __restrict__ step_dev) {
+k_step_3d(const ReplicaDesc* __restrict__ descs, const __grid_constant__ ReplicaDesc one,
+          const int64_t* __restrict__ vb_begin, int n_reps, int64_t n_vblocks, char* __restrict__ ws, int parity,
+          uint32_t step, const uint64_t* __restrict__ step_dev) {
   if (step_dev) {
     const uint64_t t = *step_dev + step;
     step = (uint32_t)t;
@@ -235,24 +406,24 @@ k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repl
     const int64_t vol = (int64_t)d.nx * d.ny * d.nz;
     const R* __restrict__ src = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
     R* __restrict__ dst = reinterpret_cast<R*>(ws + d.off_pop[parity ^ 1]);
-    R f[15][VEC];
-    pull_d3q15<R, VEC>(src, vol, d.nx, d.ny, d.nz, y, z, u, f);
+    R f[Q][VEC];
+    pull_3d<Q, R, VEC>(src, vol, d.nx, d.ny, d.nz, y, z, u, f);
     const bool noisy = d.noise_mask != 0;
     const int64_t off = (int64_t)row * d.nx + u.x0;
     R* fields = SAMPLE ? reinterpret_cast<R*>(ws + d.off_fields) : nullptr;
 #pragma unroll
     for (int s = 0; s < VEC; ++s) {
-      R g[15];
+      R g[Q];
 #pragma unroll
-      for (int i = 0; i < 15; ++i) g[i] = f[i][s];
-      R n[11];
+      for (int i = 0; i < Q; ++i) g[i] = f[i][s];
+      R n[Q - 4];
 #pragma unroll
-      for (int c = 0; c < 11; ++c) n[c] = (R)0;
-      if (noisy) normals_d3q15<R>(d, (uint32_t)row * (uint32_t)d.nx + (uint32_t)(u.x0 + s), step, n);
-      R fl[15];
-      collide_d3q15<R, DEV, SAMPLE>(d, g, noisy, n, fl);
+      for (int c = 0; c < Q - 4; ++c) n[c] = (R)0;
+      if (noisy) normals_3d<Q, R>(d, (uint32_t)row * (uint32_t)d.nx + (uint32_t)(u.x0 + s), step, n);
+      R fl[Q];
+      collide_3d<Q, R, DEV, SAMPLE>(d, g, noisy, n, fl);
 #pragma unroll
-      for (int i = 0; i < 15; ++i) f[i][s] = g[i];
+      for (int i = 0; i < Q; ++i) f[i][s] = g[i];
       if constexpr (SAMPLE) {
         // the site's sampled fields, stored at once (scalar stores; the lanes of a warp
         // cover contiguous rows of each field plane)
@@ -261,45 +432,47 @@ k_step_d3q15(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repl
             const int fid = d.field_id[slot];
             R val = fl[0];
 #pragma unroll
-            for (int a = 1; a < 15; ++a) val = (fid == a) ? fl[a] : val;
+            for (int a = 1; a < Q; ++a) val = (fid == a) ? fl[a] : val;
             fields[slot * vol + off + s] = val;
           }
       }
     }
     if (!u.active) continue;
 #pragma unroll
-    for (int i = 0; i < 15; ++i) VecIO<R, VEC>::st(dst + i * vol + off, f[i]);
+    for (int i = 0; i < Q; ++i) VecIO<R, VEC>::st(dst + i * vol + off, f[i]);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Initial state.  mode 0: f^0(rho0, u0).  mode 1: f^0 + sum_a n_i^a dM^a with dM^a =
-// sqrt(mu rho0) N_a (15 normals: Philox tag 1, step 0, calls 0..3) and the lattice mean of
-// the density and momentum fluctuations removed (k_thermal_sum3 sums them first).
-__device__ __forceinline__ void thermal_normals3(const ReplicaDesc& d, uint32_t site, double (&N)[16]) {
+// sqrt(mu rho0) N_a (Q normals: Philox tag 1, step 0, calls 0, 1, ...) and the lattice mean
+// of the density and momentum fluctuations removed (k_thermal_sum3 sums them first).
+template <int Q>
+__device__ __forceinline__ void thermal_normals3(const ReplicaDesc& d, uint32_t site, double (&N)[4 * Lat3<Q>::kThermalCalls]) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < Lat3<Q>::kThermalCalls; ++c) {
     const uint4 w = philox4x32_10(site, 0u, (uint32_t)c | (1u << 8), d.stream, d.seed_lo, d.seed_hi);
     box_muller(w.x, w.y, N[4 * c + 0], N[4 * c + 1]);
     box_muller(w.z, w.w, N[4 * c + 2], N[4 * c + 3]);
   }
 }
 
+template <int Q>
 __global__ void k_thermal_sum3(const ReplicaDesc* __restrict__ descs, int r, double* __restrict__ partial) {
   const ReplicaDesc& d = descs[r];
   const int64_t V = (int64_t)d.nx * d.ny * d.nz;
   double acc[kNumSums] = {0, 0, 0, 0};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
-    double N[16];
-    thermal_normals3(d, (uint32_t)s, N);
+    double N[4 * Lat3<Q>::kThermalCalls];
+    thermal_normals3<Q>(d, (uint32_t)s, N);
 #pragma unroll
     for (int a = 0; a < 4; ++a) acc[a] += N[a];
   }
   block_sums(acc, partial);
 }
 
-// feq0: f^0_i(rho0, u0) at [i], w_i rho0 at [16 + i]
-template <typename R, bool DEV>
+// feq0: f^0_i(rho0, u0) at [i], w_i rho0 at [kFeqW + i]
+template <int Q, typename R, bool DEV>
 __global__ void k_init3(const ReplicaDesc* __restrict__ descs, int r, char* __restrict__ ws, int mode,
                         const double* __restrict__ feq0, const double* __restrict__ sums) {
   const ReplicaDesc& d = descs[r];
@@ -307,32 +480,32 @@ __global__ void k_init3(const ReplicaDesc* __restrict__ descs, int r, char* __re
   R* dst = reinterpret_cast<R*>(ws + d.off_pop[0]);
   const double sm = sqrt(d.mu * d.rho0);
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
-    double M[15];
+    double M[Q];
     if (mode == 1) {
-      double N[16];
-      thermal_normals3(d, (uint32_t)s, N);
+      double N[4 * Lat3<Q>::kThermalCalls];
+      thermal_normals3<Q>(d, (uint32_t)s, N);
 #pragma unroll
-      for (int a = 0; a < 15; ++a) M[a] = sm * N[a];
+      for (int a = 0; a < Q; ++a) M[a] = sm * N[a];
 #pragma unroll
       for (int a = 0; a < 4; ++a) M[a] -= sm * sums[a] / (double)V;
     }
 #pragma unroll
-    for (int i = 0; i < 15; ++i) {
+    for (int i = 0; i < Q; ++i) {
       double v = feq0[i];
       if (mode == 1) {
         double acc = 0.0;
 #pragma unroll
-        for (int a = 0; a < 15; ++a) acc += moment_row3(a, v3x(i), v3y(i), v3z(i)) * M[a];
-        v += w15(i) * acc;
+        for (int a = 0; a < Q; ++a) acc += moment_row3<Q>(a, v3x<Q>(i), v3y<Q>(i), v3z<Q>(i)) * M[a];
+        v += w3<Q>(i) * acc;
       }
-      if (DEV) v -= feq0[16 + i];
+      if (DEV) v -= feq0[kFeqW + i];
       dst[i * V + s] = (R)v;
     }
   }
 }
 
 // FP64 lattice sums of rho, j_x, j_y, j_z of the stored state (per-block partials).
-template <typename R, bool DEV>
+template <int Q, typename R, bool DEV>
 __global__ void k_conserved3(const ReplicaDesc* __restrict__ descs, int r, const char* __restrict__ ws, int parity,
                              double* __restrict__ partial) {
   const ReplicaDesc& d = descs[r];
@@ -342,10 +515,10 @@ __global__ void k_conserved3(const ReplicaDesc* __restrict__ descs, int r, const
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
     double rho = DEV ? d.rho0 : 0.0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
-    for (int i = 0; i < 15; ++i) {
+    for (int i = 0; i < Q; ++i) {
       const double fv = (double)p[i * V + s];
       rho += fv;
-      jx += v3x(i) * fv; jy += v3y(i) * fv; jz += v3z(i) * fv;
+      jx += v3x<Q>(i) * fv; jy += v3y<Q>(i) * fv; jz += v3z<Q>(i) * fv;
     }
     acc[0] += rho; acc[1] += jx; acc[2] += jy; acc[3] += jz;
   }
@@ -491,9 +664,10 @@ __global__ void k_point_finish(const ReplicaDesc* __restrict__ descs, TimeCorr t
 void launch_finish_sums(const double* partial, int nblocks, double* sums, DevStatus* status, int r,
                         cudaStream_t st);
 
-void launch_step3(int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st) {
+template <int Q>
+static void launch_step3_q(int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st) {
   const bool one = L.n_reps == 1;
-#define FLB_L3(R, DEV, V, S, O) k_step_d3q15<R, DEV, V, S, O><<<L.grid, kStepThreads, 0, st>>>( \
+#define FLB_L3(R, DEV, V, S, O) k_step_3d<Q, R, DEV, V, S, O><<<L.grid, kStepThreads, 0, st>>>( \
       L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, L.step_dev)
 #define FLB_LS(R, DEV, V) { \
     if (one) { if (sample) FLB_L3(R, DEV, V, true, true); else FLB_L3(R, DEV, V, false, true); } \
@@ -506,25 +680,44 @@ void launch_step3(int precision, int vec, const StepLaunch& L, bool sample, cuda
 #undef FLB_L3
 }
 
-void launch_init3(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
-                  double* sums, double* partial, int64_t V, cudaStream_t st) {
+void launch_step3(int q, int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st) {
+  if (q == 15) launch_step3_q<15>(precision, vec, L, sample, st);
+  else launch_step3_q<19>(precision, vec, L, sample, st);
+}
+
+template <int Q>
+static void launch_init3_q(int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+                           double* sums, double* partial, int64_t V, cudaStream_t st) {
   const int block = 256;
   const int grid = (int)std::min<int64_t>((V + block - 1) / block, kReduceBlocks);
   if (mode == 1) {
-    k_thermal_sum3<<<grid, block, 0, st>>>(descs, r, partial);
+    k_thermal_sum3<Q><<<grid, block, 0, st>>>(descs, r, partial);
     launch_finish_sums(partial, grid, sums, nullptr, r, st);
   }
-  if (precision == FLB_FP64) k_init3<double, false><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
-  else k_init3<float, true><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
+  if (precision == FLB_FP64) k_init3<Q, double, false><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
+  else k_init3<Q, float, true><<<grid, block, 0, st>>>(descs, r, ws, mode, feq0, sums);
 }
 
-void launch_conserved3(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
-                       double* partial, DevStatus* status, int64_t V, cudaStream_t st) {
+void launch_init3(int q, int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
+                  double* sums, double* partial, int64_t V, cudaStream_t st) {
+  if (q == 15) launch_init3_q<15>(precision, descs, r, ws, mode, feq0, sums, partial, V, st);
+  else launch_init3_q<19>(precision, descs, r, ws, mode, feq0, sums, partial, V, st);
+}
+
+template <int Q>
+static void launch_conserved3_q(int precision, const ReplicaDesc* descs, int r, const char* ws, int parity,
+                                double* sums, double* partial, DevStatus* status, int64_t V, cudaStream_t st) {
   const int block = 256;
   const int grid = (int)std::min<int64_t>((V + block - 1) / block, kReduceBlocks);
-  if (precision == FLB_FP64) k_conserved3<double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
-  else k_conserved3<float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  if (precision == FLB_FP64) k_conserved3<Q, double, false><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
+  else k_conserved3<Q, float, true><<<grid, block, 0, st>>>(descs, r, ws, parity, partial);
   launch_finish_sums(partial, grid, sums, status, r, st);
+}
+
+void launch_conserved3(int q, int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
+                       double* partial, DevStatus* status, int64_t V, cudaStream_t st) {
+  if (q == 15) launch_conserved3_q<15>(precision, descs, r, ws, parity, sums, partial, status, V, st);
+  else launch_conserved3_q<19>(precision, descs, r, ws, parity, sums, partial, status, V, st);
 }
 
 cudaError_t set_point_dft_smem(int precision, size_t bytes) {

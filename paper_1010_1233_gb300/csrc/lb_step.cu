@@ -204,7 +204,7 @@ __global__ void k_init(const ReplicaDesc* __restrict__ descs, int r, char* __res
     }
     for (int i = 0; i < d.q; ++i) {
       double v = f[i];
-      if (DEV) v -= feq0[16 + i];         // w_i rho0
+      if (DEV) v -= feq0[kFeqW + i];      // w_i rho0
       dst[i * V + s] = (R)v;
     }
   }

@@ -10,9 +10,11 @@ import torch
 
 from . import _lib as L
 
-_NONCONSERVED = {"D2Q9": (3, 4, 5, 6, 7, 8), "D1Q3": (2,), "D3Q15": tuple(range(4, 15))}
-_LATTICE = {"D2Q9": L.FLB_D2Q9, "D1Q3": L.FLB_D1Q3, "D3Q15": L.FLB_D3Q15}
-_Q = {"D1Q3": 3, "D2Q9": 9, "D3Q15": 15}
+_NONCONSERVED = {"D2Q9": (3, 4, 5, 6, 7, 8), "D1Q3": (2,), "D3Q15": tuple(range(4, 15)),
+                 "D3Q19": tuple(range(4, 19))}
+_LATTICE = {"D2Q9": L.FLB_D2Q9, "D1Q3": L.FLB_D1Q3, "D3Q15": L.FLB_D3Q15, "D3Q19": L.FLB_D3Q19}
+_Q = {"D1Q3": 3, "D2Q9": 9, "D3Q15": 15, "D3Q19": 19}
+_3D = ("D3Q15", "D3Q19")
 _PREC = {"fp64": L.FLB_FP64, "fp32": L.FLB_FP32_DEV}
 
 
@@ -22,9 +24,9 @@ def replica_struct(p):
     s.lattice = _LATTICE[p["lattice"]]
     s.nx = int(p["nx"])
     s.ny = int(p["ny"]) if p["lattice"] != "D1Q3" else 1
-    s.nz = int(p.get("nz", 1)) if p["lattice"] == "D3Q15" else 1
-    tau = list(p["tau"]) + [1.0] * (16 - len(p["tau"]))
-    for a in range(16):
+    s.nz = int(p.get("nz", 1)) if p["lattice"] in _3D else 1
+    tau = list(p["tau"]) + [1.0] * (20 - len(p["tau"]))
+    for a in range(20):
         s.tau[a] = float(tau[a])
     s.rho0 = float(p["rho0"])
     s.kT = float(p["kT"])
@@ -96,9 +98,9 @@ class Sim:
         return (p["ny"] if p["lattice"] == "D2Q9" else 1, p["nx"])
 
     def _dims(self, r):
-        """Lattice shape of replica r: (nz, ny, nx) for D3Q15, else (ny, nx)."""
+        """Lattice shape of replica r: (nz, ny, nx) for D3Q15 / D3Q19, else (ny, nx)."""
         p = self.params[r] if 0 <= r < len(self.params) else None
-        if p is not None and p["lattice"] == "D3Q15":
+        if p is not None and p["lattice"] in _3D:
             return (int(p["nz"]), int(p["ny"]), int(p["nx"]))
         return self._shape(r)
 
@@ -141,10 +143,10 @@ class Sim:
         L.check(L.lib().flb_set_populations(self._ctx, r, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
     def conserved(self, r=0):
-        """Lattice sums (rho, j_x, j_y) (D3Q15: (rho, j_x, j_y, j_z)) of the stored state."""
+        """Lattice sums (rho, j_x, j_y) (3D lattices: (rho, j_x, j_y, j_z)) of the stored state."""
         out = np.empty(4)
         L.check(L.lib().flb_get_conserved(self._ctx, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
-        return out if self.params[min(max(r, 0), len(self.params) - 1)]["lattice"] == "D3Q15" else out[:3]
+        return out if self.params[min(max(r, 0), len(self.params) - 1)]["lattice"] in _3D else out[:3]
 
     # -- learned noise scale ----------------------------------------------
     def set_mlp(self, weights=None):
@@ -162,7 +164,7 @@ class Sim:
 
     # -- time correlators -------------------------------------------------
     def set_time_correlator(self, kpoints, n_lags):
-        """Accumulate F_ab(k, tau) at the wave vectors kpoints = [(ky, kx), ...] (D3Q15:
+        """Accumulate F_ab(k, tau) at the wave vectors kpoints = [(ky, kx), ...] (3D lattices:
         [(kz, ky, kx), ...]) for lags 0..n_lags-1 (samples); n_lags = 0 switches them off."""
         lib = L.lib()
         if n_lags == 0:

@@ -63,12 +63,21 @@ def taus_d3q15(tau_shear, tau_bulk=None, tau_ghost=1.0):
     return [1.0] * 4 + [tau_shear] * 5 + [tb] + [tau_ghost] * 5
 
 
+D3Q19 = "D3Q19"
+
+
+def taus_d3q19(tau_shear, tau_bulk=None, tau_ghost=1.0):
+    """Relaxation time per D3Q19 moment (0..18): shear 4..8, bulk 9, ghosts 10..18."""
+    tb = tau_shear if tau_bulk is None else tau_bulk
+    return [1.0] * 4 + [tau_shear] * 5 + [tb] + [tau_ghost] * 9
+
+
 def replica3(nx=8, ny=8, nz=8, tau=None, rho0=1.0, kT=1e-4, u0=(0.0, 0.0, 0.0), seed=0, stream=0,
-             noise_mask=None, init_mode=0, fields=()):
-    """One D3Q15 replica's parameters (keys shared by both sides)."""
+             noise_mask=None, init_mode=0, fields=(), lattice=D3Q15):
+    """One D3Q15 or D3Q19 replica's parameters (keys shared by both sides)."""
     if tau is None:
-        tau = taus_d3q15(1.0)
-    return dict(lattice=D3Q15, nx=int(nx), ny=int(ny), nz=int(nz), tau=[float(t) for t in tau],
+        tau = taus_d3q15(1.0) if lattice == D3Q15 else taus_d3q19(1.0)
+    return dict(lattice=lattice, nx=int(nx), ny=int(ny), nz=int(nz), tau=[float(t) for t in tau],
                 rho0=float(rho0), kT=float(kT), u0=tuple(float(v) for v in u0), seed=int(seed),
                 stream=int(stream), noise_mask=noise_mask, init_mode=int(init_mode), fields=list(fields),
                 noise_mode=0)

@@ -124,3 +124,18 @@ def test_nz_rejected_on_2d_lattices(lib):
     arr = (L.flb_replica * 1)(s)
     n = ctypes.c_size_t()
     assert lib.flb_workspace_bytes(L.FLB_FP32_DEV, arr, 1, ctypes.byref(n)) == L.FLB_EINVAL
+
+
+def test_d3q19_workspace_and_validation(lib):
+    rc, a = _ws([W.replica3(16, 8, 4, lattice="D3Q19")])
+    assert rc == 0 and a >= 2 * 19 * 16 * 8 * 4 * 4
+    for bad in (dict(fields=(19,)), dict(noise_mask=1 << 19), dict(noise_mask=1 << 2), dict(nz=0),
+                dict(tau=W.taus_d3q19(0.5))):
+        p = W.replica3(8, 8, 8, lattice="D3Q19")
+        p.update(bad)
+        rc, _ = _ws([p])
+        assert rc == L.FLB_EINVAL, bad
+    rc, _ = _ws([W.replica3(8, 8, 8, lattice="D3Q19", fields=(18,))])
+    assert rc == 0
+    rc, _ = _ws([W.replica3(8, 8, 8), W.replica3(8, 8, 8, lattice="D3Q19")])       # mixed lattices
+    assert rc == L.FLB_EINVAL
