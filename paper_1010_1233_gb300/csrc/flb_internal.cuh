@@ -58,8 +58,8 @@ struct ReplicaDesc {
   int32_t wpitch;                   // pitch (complex elements) of spec rows
   int32_t log2n1;                   // column FFT split ny = N1 * N2 (0: one pass of length ny)
   int64_t off_tc_ring, off_tc_sums; // time correlators: offsets in the TimeCorr buffer (see TimeCorr)
-  int64_t off_tc_part;              // D3Q15: per-block partial transforms [blocks][F][n_k] double2
-  int64_t off_tc_tab;               // D3Q15: phase tables of the direct transforms (lb_d3q15.cu)
+  int64_t off_tc_part;              // 3D lattices: per-block partial transforms [blocks][F][n_k] double2
+  int64_t off_tc_tab;               // 3D lattices: phase tables of the direct transforms (lb_3d.cu)
   int32_t acc_ncol;                 // pair-sum layout: 0 = [ky][kx]; c > 0 = blocked in the order
                                     // the column pass produces the points: [k1][kx / c][k2][kx % c]
                                     // (ky = k1 + N1 k2; kx padded to a multiple of c)
@@ -148,7 +148,7 @@ struct TimeCorr {
   const int32_t* ky = nullptr;      // [n_k], 0 <= ky < ny
   const int32_t* kz = nullptr;      // [n_k], 0 <= kz < nz (D3Q15; 0 otherwise)
   uint64_t* count = nullptr;        // [n_replicas]: samples written so far
-  int part_blocks = 0;              // D3Q15: blocks of the direct transform (partials per replica)
+  int part_blocks = 0;              // 3D lattices: blocks of the direct transform (partials per replica)
 };
 
 // Arguments of one step launch (lb_step.cu).
