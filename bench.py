@@ -15,6 +15,11 @@ API with host buffers, and the oracle's throughput on the host cores.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 16384]
 Under torchrun every rank runs its own replica (weak scaling, no data-path
 collective); the time is the maximum over ranks.
+
+``--workload d3q15_512`` / ``d3q19_512`` measure the three-dimensional lattices the
+same way (512^3 FP32 deviation storage, three moment fields every 20 steps into time
+correlators at 16 wave vectors; dominant kernel k_step_3d with 8 q algorithmic bytes
+per site; the oracle timed on a bounded 3D sample).
 """
 import argparse
 import json
@@ -34,7 +39,11 @@ FALLBACK_HBM_GBS = 6800.0
 # launch configuration (direct tensor-core step kernel, vec 2): ncu capture of
 # k_step_d2q9_tc<2,0,0> on the 4096^2 case (profiles/k_step_d2q9_tc_fp32_mlp_4096.md),
 # scaled by the site count; None for any other configuration.
-TRAFFIC_PER_SITE = {(2, 0): (604170240 + 559957248) / 4096**2}
+TRAFFIC_PER_SITE = {(2, 0): (604123904 + 560039168) / 4096**2}
+# The same for the 3D step kernels (k_step_3d, one replica, tuned vec) from ncu captures at
+# 256^3 (profiles/k_step_3d_fp32_256.md), scaled by the site count; keyed by (workload, vec).
+TRAFFIC_PER_SITE_3D = {("d3q15_512", 4): (1006748000 + 958004736) / 256**3,
+                       ("d3q19_512", 2): (1275584000 + 1229752000) / 256**3}
 
 
 def parse():
@@ -43,12 +52,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=16384, help="lattice edge (default: the 16384^2 workload)")
+    ap.add_argument("--workload", default="d2q9_16384", choices=["d2q9_16384", "d3q15_512", "d3q19_512"])
+    ap.add_argument("--n", type=int, default=None, help="lattice edge (default: that of the workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=400)
-    ap.add_argument("--cpu-n", type=int, default=256)
-    return ap.parse_args()
+    ap.add_argument("--cpu-n", type=int, default=None, help="edge of the oracle's sample (256 for D2Q9, 24 for 3D)")
+    args = ap.parse_args()
+    three_d = args.workload != "d2q9_16384"
+    if args.n is None:
+        args.n = 512 if three_d else 16384
+    if args.cpu_n is None:
+        args.cpu_n = 24 if three_d else 256
+    return args
 
 
 def rank_replica(p, rank):
@@ -186,9 +202,57 @@ print(json.dumps({"seconds": dt, "sites": p["nx"] * p["ny"], "steps": %d}))
                       f"{max(1, steps // SAMPLE_EVERY)} direct-DFT samples, {d['seconds']:.1f} s"}
 
 
+def cpu_baseline3(workload_name, n, steps, args_threads=1):
+    """Time the FP64 3D oracle on the host (one thread) on an n^3 sample of the workload."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+from oracle import lb3d
+from paper_1010_1233_gb300 import workloads as W
+wl = getattr(W, %r)(%d)
+p = dict(wl["replicas"][0])
+P = lb3d.Params3(nx=p["nx"], ny=p["ny"], nz=p["nz"], tau=p["tau"], rho0=p["rho0"], kT=p["kT"], u0=p["u0"],
+                 seed=p["seed"], stream=p["stream"], init_mode=p["init_mode"], fields=list(p["fields"]),
+                 lattice=p["lattice"])
+r = lb3d.Run3(P, wl["kpoints"])
+r.run(1, %d)
+t0 = time.perf_counter()
+r.run(%d, %d)
+dt = time.perf_counter() - t0
+print(json.dumps({"seconds": dt, "sites": p["nx"] * p["ny"] * p["nz"], "steps": %d}))
+""" % (ROOT, workload_name, n, SAMPLE_EVERY, steps, SAMPLE_EVERY, steps)
+    env = dict(os.environ, OMP_NUM_THREADS=str(args_threads), OPENBLAS_NUM_THREADS=str(args_threads),
+               MKL_NUM_THREADS=str(args_threads), CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        return {"error": out.stderr[-400:]}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    mlups = d["sites"] * d["steps"] / d["seconds"] / 1e6
+    lat = workload_name[:5].upper()
+    return {"value": mlups, "unit": "MLUPS", "cores": args_threads, "kind": "oracle",
+            "sample": f"{lat} {n}^3 FP64 oracle, same taus/u0/fields, {steps} steps incl. "
+                      f"{max(1, steps // SAMPLE_EVERY)} samples at 16 wave vectors, {d['seconds']:.1f} s"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload != "d2q9_16384":
+        n = args.cpu_n
+        per = cpu_baseline3(args.workload, n, max(SAMPLE_EVERY, args.steps // 5) if args.steps > 0 else SAMPLE_EVERY)
+        if "error" in per:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + per["error"][-200:]}))
+            return
+        line = {
+            "impl": "reference", "metric": f"{args.workload[:5].upper()} fluctuating-LB MLUPS", "value": per["value"],
+            "unit": "MLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (bounded CPU sample)", "nx": n, "ny": n, "nz": n},
+            "cpu_baseline": per,
+            "e2e": {"value": per["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line))
         return
     n = args.cpu_n
     per = cpu_baseline(n, max(SAMPLE_EVERY, args.steps // 5) if args.steps > 0 else SAMPLE_EVERY)
@@ -207,7 +271,118 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_ours3(args):
+    """The 3D workloads: same timing rules, the k_step_3d roofline, e2e and the 3D oracle."""
+    import torch
+    import torch.distributed as dist
+    from paper_1010_1233_gb300 import Sim, build
+    from paper_1010_1233_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    wl = getattr(W, args.workload)(args.n)
+    p = rank_replica(wl["replicas"][0], rank)
+    q = 15 if p["lattice"] == "D3Q15" else 19
+    sim = Sim(p, precision="fp32")
+    tuned = sim.autotune(trials=5)
+    sim.set_time_correlator(wl["kpoints"], wl["n_lags"])
+    stream = sim.stream
+    V = p["nx"] * p["ny"] * p["nz"]
+    K, Wm = args.steps, max(3, args.warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim.run(Wm, SAMPLE_EVERY)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.run(K, SAMPLE_EVERY)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
+    # per sample: point transform, its finishing pass, the lagged products, the ring advance
+    launches = expected_launches(Wm, K, SAMPLE_EVERY, sample_kernels=4)
+
+    Kd = max(20, min(K, 100))
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    sim.run(Kd, 0)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = d0.elapsed_time(d1) / Kd
+    hbm, peak_kind = peaks()
+    alg = 8 * q
+    achieved = alg * V / (step_ms * 1e-3) / 1e9
+    tps = TRAFFIC_PER_SITE_3D.get((args.workload, tuned[0]))
+    traffic = tps * V if tps else None
+
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+        from paper_1010_1233_gb300 import _lib as L
+        lib = L.lib()
+        size = ctypes.c_size_t()
+        L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
+        nb = int(size.value)
+        host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
+        barrier()
+        t0 = time.perf_counter()
+        L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
+        sim.run(K, SAMPLE_EVERY)
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
+        e2e = {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
+               "pinned": True, "what": "flb_load(host state) + K steps + flb_save(host state)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline3(args.workload, args.cpu_n, args.cpu_steps)
+
+    if rank == 0:
+        line = {
+            "metric": f"{p['lattice']} fluctuating-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": K, "warmup": Wm, "ms_per_step": t_max * 1e3 / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": p["lattice"], "nx": p["nx"], "ny": p["ny"],
+                       "nz": p["nz"], "storage": "fp32 deviation f - w rho0, FP64 correlator sums",
+                       "tau_shear": 0.8, "tau_ghost": 1.0, "u0": list(p["u0"]), "kT": p["kT"],
+                       "sample_every": SAMPLE_EVERY, "fields": list(p["fields"]), "n_k": len(wl["kpoints"]),
+                       "n_lags": wl["n_lags"], "parallelism": f"replica x{world}",
+                       "l2": "inputs larger than L2 (%.1f GB state), no flush" % (2 * q * 4 * V / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": f"k_step_3d<{q}> (fused pull-stream/collide/noise)",
+                         "alg_bytes_per_launch": alg * V, "avg_launch_ms": step_ms,
+                         "launch": {"vec": tuned[0], "grid_blocks_requested": tuned[1], "block": 256}},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_ours(args):
+    if args.workload != "d2q9_16384":
+        return run_ours3(args)
     import numpy as np
     import torch
     import torch.distributed as dist

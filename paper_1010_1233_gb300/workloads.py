@@ -22,6 +22,10 @@ Sec. 3) at the sizes the library is measured on:
 * ``d2q9_16384``   D2Q9 16384 x 16384 FP32 deviation storage, tau_shear =
                    tau_bulk = 0.6, tau_ghost = 1.0, u0 = (0.1, 0.05), kT = 1e-4,
                    noise-scale network on, 1e4 steps, rho/u_x/u_y spectra every 20.
+* ``d3q15_512``, ``d3q19_512``  the 3D lattices at 512^3, FP32 deviation storage,
+                   tau_shear = tau_bulk = 0.8, tau_ghost = 1.0, u0 = (0.05, 0.02, 0),
+                   thermal start, three moment fields every 20 steps into time
+                   correlators at 16 wave vectors.
 """
 import numpy as np
 
@@ -119,6 +123,32 @@ def d2q9_16384(n=16384):
                                   u0=(0.1, 0.05), seed=11, init_mode=0,
                                   fields=(0, FIELD_UX, FIELD_UY))],
                 warmup=3, steps=10_000, sample_every=20, mlp=True)
+
+
+def kpoints3(n, count=16):
+    """Wave vectors (kz, ky, kx) of the 3D correlator workloads: the first axis and
+    diagonal modes of an n^3 box (none at k = 0 or with a component at pi)."""
+    ks = []
+    for m in range(1, count + 1):
+        k = (m - 1) // 4 + 1
+        ks.append([(0, 0, k), (0, k, 0), (k, 0, 0), (k, k, k)][(m - 1) % 4])
+    return [tuple(c % n for c in k) for k in ks]
+
+
+def d3q15_512(n=512):
+    """D3Q15 n^3 FP32 deviation storage, tau_shear = tau_bulk = 0.8, tau_ghost = 1.0,
+    u0 = (0.05, 0.02, 0), kT = 1e-4, thermal start; density, shear M^4 and bulk M^9
+    fields every 20 steps into time correlators (8 lags) at 16 wave vectors."""
+    return dict(replicas=[replica3(n, n, n, taus_d3q15(0.8, 0.8, 1.0), kT=1e-4, u0=(0.05, 0.02, 0.0), seed=21,
+                                   init_mode=1, fields=(0, 4, 9), lattice=D3Q15)],
+                kpoints=kpoints3(n), n_lags=8, sample_every=20)
+
+
+def d3q19_512(n=512):
+    """As d3q15_512 on D3Q19."""
+    return dict(replicas=[replica3(n, n, n, taus_d3q19(0.8, 0.8, 1.0), kT=1e-4, u0=(0.05, 0.02, 0.0), seed=21,
+                                   init_mode=1, fields=(0, 4, 9), lattice=D3Q19)],
+                kpoints=kpoints3(n), n_lags=8, sample_every=20)
 
 
 def random_perturbation(shape, seed, amp=1.0):
