@@ -31,7 +31,7 @@ constexpr int kNumCoef = kCoNoiseR + 36;
 // Offsets are byte offsets from the workspace base.
 struct ReplicaDesc {
   int32_t nx, ny, log2nx, log2ny;
-  int32_t nz;                   // D3Q15 depth (1 otherwise); a row is (y, z), row = z ny + y
+  int32_t nz;                   // 3D depth (1 otherwise); a row is (y, z), row = z ny + y
   int32_t q;
   int32_t units_per_row;        // nx / VEC of the step launch
   uint32_t upr_magic;           // row of a unit u < 2^31: (u * upr_magic) >> upr_shift
@@ -146,7 +146,7 @@ struct TimeCorr {
   int n_lags = 0, n_k = 0;
   const int32_t* kx = nullptr;      // [n_k], 0 <= kx <= nx/2
   const int32_t* ky = nullptr;      // [n_k], 0 <= ky < ny
-  const int32_t* kz = nullptr;      // [n_k], 0 <= kz < nz (D3Q15; 0 otherwise)
+  const int32_t* kz = nullptr;      // [n_k], 0 <= kz < nz (3D lattices; 0 otherwise)
   uint64_t* count = nullptr;        // [n_replicas]: samples written so far
   int part_blocks = 0;              // 3D lattices: blocks of the direct transform (partials per replica)
 };
