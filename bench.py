@@ -338,6 +338,8 @@ def run_ours3(args):
         host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
         host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
         L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
+        # untimed: one save into the output buffer too, so both buffers have been used once
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
         barrier()
         t0 = time.perf_counter()
         L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
@@ -457,6 +459,8 @@ def run_ours(args):
             host_out = torch.empty(nb, dtype=torch.uint8)
             pinned = False
         L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
+        # untimed: one save into the output buffer too, so both buffers have been used once
+        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
         barrier()
         t0 = time.perf_counter()
         L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
