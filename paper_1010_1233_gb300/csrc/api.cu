@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/flb.h: validation, workspace
 // layout, launch sequencing and host I/O.  All compute runs in the kernels of
 // lb_step.cu and spectra.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,7 +43,7 @@ void launch_init3(int q, int precision, const ReplicaDesc* descs, int r, char* w
                   double* sums, double* partial, int64_t V, cudaStream_t st);
 void launch_conserved3(int q, int precision, const ReplicaDesc* descs, int r, const char* ws, int parity, double* sums,
                        double* partial, DevStatus* status, int64_t V, cudaStream_t st);
-size_t point_dft_smem(int precision, int nx, int ny, int nz, int items);
+size_t point_dft_smem(int precision, int nx, int ny, int nz, int items, int items2);
 size_t point_tables_bytes(int precision, int nx, int ny, int nz);
 void launch_point_tables(int precision, const ReplicaDesc* descs, int n_reps, char* base, cudaStream_t st);
 cudaError_t set_point_dft_smem(int precision, size_t bytes);
@@ -523,16 +524,15 @@ static int point_blocks(const flb_ctx* c, int n_k) {
   return (int)std::max<int64_t>(g, 1);
 }
 
-// Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | kz [n_k] | rings
+// Time-correlator buffer layout: counts [n] u64 | kx [n_k] | ky [n_k] | kz [n_k] |
+// kx index [n_k] | distinct kx [n_k] | rings
 // of every replica | 3D block partials and phase tables of every replica | sums of
 // every replica (contiguous, so a reset is one memset).
 static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vector<int64_t>* ring,
                                 std::vector<int64_t>* sums, int64_t* sums0, std::vector<int64_t>* part = nullptr,
                                 std::vector<int64_t>* tab = nullptr) {
   int64_t off = align256(8 * (int64_t)c->n);
-  off = align256(off + 4 * (int64_t)n_k);
-  off = align256(off + 4 * (int64_t)n_k);
-  off = align256(off + 4 * (int64_t)n_k);
+  for (int a = 0; a < 5; ++a) off = align256(off + 4 * (int64_t)n_k);
   for (int r = 0; r < c->n; ++r) {
     if (ring) (*ring)[r] = off;
     off = align256(off + 16 * (int64_t)n_lags * c->L.desc[r].n_fields * n_k);
@@ -588,6 +588,13 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
   const bool d3 = is3d(c->lattice);
   std::vector<int32_t> kzv(n_k, 0);
   if (kz) kzv.assign(kz, kz + n_k);
+  // distinct kx values (the row sums of the 3D direct transforms depend on kx only)
+  std::vector<int32_t> kxl(kx, kx + n_k), kxi(n_k, 0);
+  std::sort(kxl.begin(), kxl.end());
+  kxl.erase(std::unique(kxl.begin(), kxl.end()), kxl.end());
+  for (int j = 0; j < n_k; ++j) kxi[j] = (int32_t)(std::lower_bound(kxl.begin(), kxl.end(), kx[j]) - kxl.begin());
+  const int n_kx = (int)kxl.size();
+  kxl.resize(n_k, 0);
   size_t smem = 0;
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
@@ -608,7 +615,7 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
       const int items = (int)d.n_fields * n_k;
       if (items > kMaxPointItems)
         return set_error(FLB_EINVAL, "fields x wave vectors = %d > %d", items, kMaxPointItems);
-      smem = std::max(smem, point_dft_smem(c->precision, d.nx, d.ny, d.nz, items));
+      smem = std::max(smem, point_dft_smem(c->precision, d.nx, d.ny, d.nz, items, (int)d.n_fields * n_kx));
     }
   }
   if (d3) {
@@ -623,9 +630,14 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
   char* base = static_cast<char*>(buf_dev);
   const int64_t okx = align256(8 * (int64_t)c->n), oky = align256(okx + 4 * (int64_t)n_k);
   const int64_t okz = align256(oky + 4 * (int64_t)n_k);
+  const int64_t okxi = align256(okz + 4 * (int64_t)n_k), okxl = align256(okxi + 4 * (int64_t)n_k);
   rc = cuda_check(cudaMemcpy(base + okx, kx, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
   if (!rc) rc = cuda_check(cudaMemcpy(base + oky, ky, 4 * (size_t)n_k, cudaMemcpyHostToDevice), "copy wave vectors");
   if (!rc) rc = cuda_check(cudaMemcpy(base + okz, kzv.data(), 4 * (size_t)n_k, cudaMemcpyHostToDevice),
+                           "copy wave vectors");
+  if (!rc) rc = cuda_check(cudaMemcpy(base + okxi, kxi.data(), 4 * (size_t)n_k, cudaMemcpyHostToDevice),
+                           "copy wave vectors");
+  if (!rc) rc = cuda_check(cudaMemcpy(base + okxl, kxl.data(), 4 * (size_t)n_k, cudaMemcpyHostToDevice),
                            "copy wave vectors");
   if (!rc) rc = cuda_check(cudaMemset(base, 0, 8 * (size_t)c->n), "zero counts");
   if (!rc) rc = cuda_check(cudaMemset(base + sums0, 0, (size_t)(need - sums0)), "zero sums");
@@ -651,6 +663,9 @@ int flb_set_time_correlator3(flb_ctx* c, int n_lags, int n_k, const int32_t* kx,
   c->tc.kx = reinterpret_cast<const int32_t*>(base + okx);
   c->tc.ky = reinterpret_cast<const int32_t*>(base + oky);
   c->tc.kz = reinterpret_cast<const int32_t*>(base + okz);
+  c->tc.kxi = reinterpret_cast<const int32_t*>(base + okxi);
+  c->tc.kxl = reinterpret_cast<const int32_t*>(base + okxl);
+  c->tc.n_kx = n_kx;
   c->tc.count = reinterpret_cast<uint64_t*>(base);
   c->tc.part_blocks = d3 ? point_blocks(c, n_k) : 0;
   c->tc_smem = smem;

@@ -147,6 +147,9 @@ struct TimeCorr {
   const int32_t* kx = nullptr;      // [n_k], 0 <= kx <= nx/2
   const int32_t* ky = nullptr;      // [n_k], 0 <= ky < ny
   const int32_t* kz = nullptr;      // [n_k], 0 <= kz < nz (3D lattices; 0 otherwise)
+  const int32_t* kxi = nullptr;     // 3D: [n_k] index of kx[j] in kxl
+  const int32_t* kxl = nullptr;     // 3D: [n_kx] the distinct kx values
+  int n_kx = 0;
   uint64_t* count = nullptr;        // [n_replicas]: samples written so far
   int part_blocks = 0;              // 3D lattices: blocks of the direct transform (partials per replica)
 };

@@ -527,19 +527,24 @@ __global__ void k_conserved3(const ReplicaDesc* __restrict__ descs, int r, const
 
 // ---------------------------------------------------------------------------
 // Direct transforms at the time-correlator wave vectors.  Block b of replica blockIdx.y
-// takes the rows b, b + G, ... (G = gridDim.x); a thread is (item, part) with item =
-// f n_k + j: it sums x = part, part + P, ... of the row with the phase exp(-2 pi i (kx x
-// mod nx) / nx) from a table, multiplies by the row phase exp(-2 pi i (ky y / ny + kz z /
-// nz)) (FP64 tables) and accumulates in FP64.  The parts are added in order at the end
-// and the block's sums go to partial [G][F n_k].
+// takes the row groups b, b + G, ... (G = gridDim.x) of R consecutive rows.  The x sum
+// of a row depends on the field and on k_x only, so it is formed once per (row, field,
+// distinct k_x): thread (q, part) sums x = part, part + P, ... with the phase
+// exp(-2 pi i (kx x mod nx) / nx) from a table, in the path's precision; then each item
+// (field f, wave vector j) adds, row by row, its row sum times the row phase
+// exp(-2 pi i (ky y / ny + kz z / nz)) (FP64 tables) to its FP64 accumulator.  The
+// block's sums go to partial [G][F n_k].
 // The phase tables are made once per replica (k_point_tables, at configuration) in the
 // correlator buffer at off_tc_tab: x table (nx complex R, 16-byte padded) | y, z tables
 // (ny + nz complex double); each block copies them to shared memory, followed by the
-// per-part sums.
-int point_dft_parts(int items) {
-  int P = 1;
-  while (items * P * 2 <= kStepThreads) P *= 2;
-  return P;
+// per-part row sums [P][R F n_kx] (complex R) and the accumulators [F n_k] (complex double).
+// Shape of one pass: R consecutive rows at a time, P parts per (row, field, k_x) item,
+// R * items2 * P <= kStepThreads.
+__host__ __device__ inline void point_dft_shape(int items2, int& R, int& P) {
+  R = kStepThreads / (4 * items2);
+  R = R < 1 ? 1 : (R > 8 ? 8 : R);
+  P = 1;
+  while (R * items2 * P * 2 <= kStepThreads) P *= 2;
 }
 
 size_t point_tables_bytes(int precision, int nx, int ny, int nz) {
@@ -547,9 +552,13 @@ size_t point_tables_bytes(int precision, int nx, int ny, int nz) {
   return ((nx * cs + 15) & ~size_t(15)) + (size_t)(ny + nz) * 16;
 }
 
-size_t point_dft_smem(int precision, int nx, int ny, int nz, int items) {
-  const int P = point_dft_parts(items);
-  return point_tables_bytes(precision, nx, ny, nz) + (size_t)std::max(items * P, items) * 16;
+// items = F n_k, items2 = F n_kx
+size_t point_dft_smem(int precision, int nx, int ny, int nz, int items, int items2) {
+  const size_t cs = precision == FLB_FP64 ? 16 : 8;
+  int R, P;
+  point_dft_shape(items2, R, P);
+  const size_t red = ((size_t)P * R * items2 * cs + 15) & ~size_t(15);
+  return point_tables_bytes(precision, nx, ny, nz) + red + (size_t)items * 16;
 }
 
 template <typename R>
@@ -576,7 +585,8 @@ __global__ void __launch_bounds__(kStepThreads)
 k_point_dft(const ReplicaDesc* __restrict__ descs, const char* __restrict__ ws, TimeCorr tc) {
   extern __shared__ __align__(16) unsigned char psm[];
   const ReplicaDesc& d = descs[blockIdx.y];
-  const int F = (int)d.n_fields, nk = tc.n_k, items = F * nk;
+  const int F = (int)d.n_fields, nk = tc.n_k, nkx = tc.n_kx;
+  const int items = F * nk, items2 = F * nkx;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const int64_t vol = (int64_t)nx * ny * nz;
   const size_t txb = (nx * sizeof(cplx<R>) + 15) & ~size_t(15);
@@ -588,74 +598,112 @@ k_point_dft(const ReplicaDesc* __restrict__ descs, const char* __restrict__ ws, 
   }
   const cplx<R>* tx = reinterpret_cast<const cplx<R>*>(psm);
   const double2* tyz = reinterpret_cast<const double2*>(psm + txb);
-  double2* acc = reinterpret_cast<double2*>(psm + txb + (size_t)(ny + nz) * 16);
-  // parts per item (items <= blockDim / P); with more items than threads, P = 1 and a
-  // thread takes items tid, tid + blockDim, ...
-  int P = 1;
-  while (items * P * 2 <= (int)blockDim.x) P *= 2;
-  const int part = (int)threadIdx.x % P, ibase = (int)threadIdx.x / P, istride = (int)blockDim.x / P;
-  for (int it = ibase; it < items; it += istride) acc[part * items + it] = make_double2(0.0, 0.0);
-  __syncthreads();
+  int RR, P;
+  point_dft_shape(items2, RR, P);
+  const int q2n = RR * items2;                        // (row in pass, field, k_x) items
+  cplx<R>* red = reinterpret_cast<cplx<R>*>(psm + txb + (size_t)(ny + nz) * 16);               // [P][q2n]
+  double2* acc = reinterpret_cast<double2*>(reinterpret_cast<unsigned char*>(red) +
+                                            (((size_t)P * q2n * sizeof(cplx<R>) + 15) & ~size_t(15)));
+  for (int it = threadIdx.x; it < items; it += blockDim.x) acc[it] = make_double2(0.0, 0.0);
+  const int part = (int)threadIdx.x % P, qbase = (int)threadIdx.x / P, qstride = (int)blockDim.x / P;
   const R* fields = reinterpret_cast<const R*>(ws + d.off_fields);
   const int rows = ny * nz;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int z = row / ny, y = row - z * ny;
-    for (int it = ibase; it < items; it += istride) {
-      const int f = it / nk, j = it - f * nk;
-      const int kx = tc.kx[j], ky = tc.ky[j], kz = tc.kz[j];
-      const R* xr = fields + f * vol + (int64_t)row * nx;
-      const int dm = (int)(((int64_t)kx * P) % nx);
-      int m0 = (int)(((int64_t)kx * part) % nx);
-      // four independent partial sums, loads issued ahead of the multiplies
-      R sr0 = (R)0, si0 = (R)0, sr1 = (R)0, si1 = (R)0;
-      int x = part;
-      for (; x + 3 * P < nx; x += 4 * P) {
-        const R v0 = xr[x], v1 = xr[x + P], v2 = xr[x + 2 * P], v3 = xr[x + 3 * P];
-        int m1 = m0 + dm; m1 -= m1 >= nx ? nx : 0;
-        int m2 = m1 + dm; m2 -= m2 >= nx ? nx : 0;
-        int m3 = m2 + dm; m3 -= m3 >= nx ? nx : 0;
-        const cplx<R> c0 = tx[m0], c1 = tx[m1], c2 = tx[m2], c3 = tx[m3];
-        sr0 += v0 * c0.x; si0 += v0 * c0.y;
-        sr1 += v1 * c1.x; si1 += v1 * c1.y;
-        sr0 += v2 * c2.x; si0 += v2 * c2.y;
-        sr1 += v3 * c3.x; si1 += v3 * c3.y;
-        m0 = m3 + dm; m0 -= m0 >= nx ? nx : 0;
-      }
-      for (; x < nx; x += P) {
-        const R v = xr[x];
-        sr0 += v * tx[m0].x; si0 += v * tx[m0].y;
-        m0 += dm; m0 -= m0 >= nx ? nx : 0;
-      }
-      const R sr = sr0 + sr1, si = si0 + si1;
-      const double2 py = tyz[(int)(((int64_t)ky * y) % ny)];
-      const double2 pz = tyz[ny + (int)(((int64_t)kz * z) % nz)];
-      const double pr = py.x * pz.x - py.y * pz.y, pi = py.x * pz.y + py.y * pz.x;
-      double2& a = acc[part * items + it];
-      a.x += (double)sr * pr - (double)si * pi;
-      a.y += (double)sr * pi + (double)si * pr;
-    }
-  }
+  const uint32_t unx = (uint32_t)nx, uny = (uint32_t)ny, unz = (uint32_t)nz;
   __syncthreads();
-  double2* out = reinterpret_cast<double2*>(tc.base + d.off_tc_part) + (int64_t)blockIdx.x * items;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    double2 s = acc[it];
-    for (int p = 1; p < P; ++p) { s.x += acc[p * items + it].x; s.y += acc[p * items + it].y; }
-    out[it] = s;
+  for (int row0 = blockIdx.x * RR; row0 < rows; row0 += gridDim.x * RR) {
+    // row sums per (row, field, distinct k_x); all index products stay below 2^24
+    for (int q2 = qbase; q2 < q2n; q2 += qstride) {
+      const int rr = q2 / items2, q = q2 - rr * items2;
+      const int row = row0 + rr;
+      cplx<R> sv;
+      sv.x = (R)0; sv.y = (R)0;
+      if (row < rows) {
+        const int f = q / nkx;
+        const uint32_t kx = (uint32_t)tc.kxl[q - f * nkx];
+        const R* xr = fields + f * vol + (int64_t)row * nx;
+        const int dm = (int)((kx * (uint32_t)P) % unx);
+        int m0 = (int)((kx * (uint32_t)part) % unx);
+        R sr0 = (R)0, si0 = (R)0, sr1 = (R)0, si1 = (R)0;
+        int x = part;
+        for (; x + 3 * P < nx; x += 4 * P) {
+          const R v0 = xr[x], v1 = xr[x + P], v2 = xr[x + 2 * P], v3 = xr[x + 3 * P];
+          int m1 = m0 + dm; m1 -= m1 >= nx ? nx : 0;
+          int m2 = m1 + dm; m2 -= m2 >= nx ? nx : 0;
+          int m3 = m2 + dm; m3 -= m3 >= nx ? nx : 0;
+          const cplx<R> c0 = tx[m0], c1 = tx[m1], c2 = tx[m2], c3 = tx[m3];
+          sr0 += v0 * c0.x; si0 += v0 * c0.y;
+          sr1 += v1 * c1.x; si1 += v1 * c1.y;
+          sr0 += v2 * c2.x; si0 += v2 * c2.y;
+          sr1 += v3 * c3.x; si1 += v3 * c3.y;
+          m0 = m3 + dm; m0 -= m0 >= nx ? nx : 0;
+        }
+        for (; x < nx; x += P) {
+          const R v = xr[x];
+          sr0 += v * tx[m0].x; si0 += v * tx[m0].y;
+          m0 += dm; m0 -= m0 >= nx ? nx : 0;
+        }
+        sv.x = sr0 + sr1; sv.y = si0 + si1;
+      }
+      red[part * q2n + q2] = sv;
+    }
+    __syncthreads();
+    // each wave vector: its field's row sums at its k_x times the row phases, in FP64,
+    // rows in order
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int f = it / nk, j = it - f * nk;
+      const int q = f * nkx + tc.kxi[j];
+      const uint32_t ky = (uint32_t)tc.ky[j], kz = (uint32_t)tc.kz[j];
+      double2 a = acc[it];
+      for (int rr = 0; rr < RR; ++rr) {
+        const int row = row0 + rr;
+        if (row >= rows) break;
+        const int q2 = rr * items2 + q;
+        R sr = red[q2].x, si = red[q2].y;
+        for (int p = 1; p < P; ++p) { sr += red[p * q2n + q2].x; si += red[p * q2n + q2].y; }
+        const uint32_t z = (uint32_t)row / uny, y = (uint32_t)row - z * uny;
+        const double2 py = tyz[(ky * y) % uny];
+        const double2 pz = tyz[ny + (kz * z) % unz];
+        const double pr = py.x * pz.x - py.y * pz.y, pi = py.x * pz.y + py.y * pz.x;
+        a.x += (double)sr * pr - (double)si * pi;
+        a.y += (double)sr * pi + (double)si * pr;
+      }
+      acc[it] = a;
+    }
+    __syncthreads();
   }
+  double2* out = reinterpret_cast<double2*>(tc.base + d.off_tc_part) + (int64_t)blockIdx.x * items;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) out[it] = acc[it];
 }
 
-// Adds the G block partials in block order into the replica's ring slot count % n_lags.
-__global__ void k_point_finish(const ReplicaDesc* __restrict__ descs, TimeCorr tc) {
+// Adds the G block partials of one item (blockIdx.x) into the replica's ring slot
+// count % n_lags: thread t sums blocks t, t + 256, ... in order, then a fixed tree adds
+// the 256 partial sums (the same order every time).
+__global__ void __launch_bounds__(256) k_point_finish(const ReplicaDesc* __restrict__ descs, TimeCorr tc) {
+  __shared__ double2 sred[256];
   const int r = blockIdx.y;
   const ReplicaDesc& d = descs[r];
   const int items = (int)d.n_fields * tc.n_k;
-  const int it = blockIdx.x * blockDim.x + threadIdx.x;
-  if (it >= items) return;
+  const int it = blockIdx.x;
+  if (it >= items) return;                      // uniform over the block
   const double2* part = reinterpret_cast<const double2*>(tc.base + d.off_tc_part);
   double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < tc.part_blocks; ++b) { s.x += part[(int64_t)b * items + it].x; s.y += part[(int64_t)b * items + it].y; }
-  const int slot = (int)(tc.count[r] % (uint64_t)tc.n_lags);
-  reinterpret_cast<double2*>(tc.base + d.off_tc_ring)[(int64_t)slot * items + it] = s;
+  for (int b = threadIdx.x; b < tc.part_blocks; b += blockDim.x) {
+    const double2 v = part[(int64_t)b * items + it];
+    s.x += v.x; s.y += v.y;
+  }
+  sred[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sred[threadIdx.x].x += sred[threadIdx.x + h].x;
+      sred[threadIdx.x].y += sred[threadIdx.x + h].y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int slot = (int)(tc.count[r] % (uint64_t)tc.n_lags);
+    reinterpret_cast<double2*>(tc.base + d.off_tc_ring)[(int64_t)slot * items + it] = sred[0];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -737,7 +785,7 @@ void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int m
   const dim3 grid(tc.part_blocks, n_reps);
   if (precision == FLB_FP64) k_point_dft<double><<<grid, kStepThreads, smem, st>>>(descs, ws, tc);
   else k_point_dft<float><<<grid, kStepThreads, smem, st>>>(descs, ws, tc);
-  k_point_finish<<<dim3((max_items + 255) / 256, n_reps), 256, 0, st>>>(descs, tc);
+  k_point_finish<<<dim3(max_items, n_reps), 256, 0, st>>>(descs, tc);
 }
 
 }  // namespace flb
