@@ -412,7 +412,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
   if (maxF) {
     L.rows_smem = fft_rows_smem(precision, maxnx);
-    L.rows_block = std::max(32, std::min(512, maxnx / 2));
+    L.rows_block = std::max(32, std::min(kRowsBlockMax, maxnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
   }
   plan_step(lat, L.vec, 0, L);

@@ -173,6 +173,7 @@ template <int FL> struct Flavor { static constexpr bool kOne = FL != 2, kGen = F
 // length ny when F columns of 4 fit the budget, else ny = N1 * N2 with
 // N1 = 2^floor(log2(ny)/2) (four-step).
 constexpr int kColsSmemBudget = 200 * 1024;
+constexpr int kRowsBlockMax = 1024;      // threads of a row-FFT block (at most nx / 2)
 constexpr int kColsBlock = 256;
 #ifndef FLB_COLS_MAX
 #define FLB_COLS_MAX 16

@@ -143,7 +143,8 @@ __device__ __forceinline__ int find_rep(const int64_t* vb_begin, int n_reps, int
 
 // Pass 1: one block per (replica, packed field pair, row).
 template <typename R>
-__global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
+__global__ void __launch_bounds__(kRowsBlockMax)
+k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
                            int n_reps, int64_t n_vblocks, char* __restrict__ ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* z = reinterpret_cast<C<R>*>(smem_raw);
@@ -162,6 +163,24 @@ __global__ void k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t*
     const R* xb = fields + fb * plane + (int64_t)y * nx;
     const int ps = logn > 5 ? logn - 5 : 31;        // 32 pad slots per row
     const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_x);
+    // the rows of this block's next pair into L2 while this pair is transformed
+    if (threadIdx.x == 0 && vb + gridDim.x < n_vblocks) {
+      const int64_t vbn = vb + gridDim.x;
+      const int rn = find_rep(vb_begin, n_reps, vbn);
+      const ReplicaDesc& dn = descs[rn];
+      const int64_t ln = vbn - vb_begin[rn];
+      const int yn = (int)(ln & (dn.ny - 1)), pn = (int)(ln >> dn.log2ny);
+      const int64_t pl = (int64_t)dn.nx * dn.ny;
+      const R* fn = reinterpret_cast<const R*>(ws + dn.off_fields);
+      const uint32_t bytes = (uint32_t)(dn.nx * sizeof(R));
+      if (bytes % 16 == 0) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(fn + 2 * pn * pl + (int64_t)yn * dn.nx),
+                     "r"(bytes) : "memory");
+        if (2 * pn + 1 < (int)dn.n_fields)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                       :: "l"(fn + (2 * pn + 1) * pl + (int64_t)yn * dn.nx), "r"(bytes) : "memory");
+      }
+    }
     if (logn >= 3) {
       // thread x0 < nx/8 loads x0 + j nx/8 (j < 8, coalesced): after bit reversal these are
       // elements t = brev3(j) of the group m = brev(x0) of the first three stages, which
@@ -230,6 +249,28 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     const int total = F * n1 * ncol;
+    // the next tile of this block into L2 (one bulk prefetch per (field, y1) segment)
+    if (vb + gridDim.x < n_vblocks) {
+      const int64_t vbn = vb + gridDim.x;
+      const int rn = find_rep(vb_begin, n_reps, vbn);
+      const ReplicaDesc& dn = descs[rn];
+      const int tn = (dn.half_nx + ncol - 1) >> lc;
+      const int64_t ln = vbn - vb_begin[rn];
+      const int y2n = (int)(ln / tn);
+      const int kxn = (int)(ln - (int64_t)y2n * tn) << lc;
+      const int ncn = min(ncol, dn.half_nx - kxn);
+      const int l1n = dn.log2n1, n2n = dn.ny >> l1n;
+      const uint32_t bytes = (uint32_t)(((ncn * (int)sizeof(C<R>)) + 15) & ~15);
+      const C<R>* sp = reinterpret_cast<const C<R>*>(ws + dn.off_spec);
+      const int64_t fpn = (int64_t)dn.ny * dn.wpitch;
+      const int segs = (int)dn.n_fields << l1n;
+      for (int i = threadIdx.x; i < segs; i += blockDim.x) {
+        const int f = i >> l1n, y1 = i & ((1 << l1n) - 1);
+        const C<R>* a = sp + f * fpn + (int64_t)(n2n * y1 + y2n) * dn.wpitch + kxn;
+        if ((reinterpret_cast<uintptr_t>(a) & 15) == 0)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a), "r"(bytes) : "memory");
+      }
+    }
     // gather, four loads in flight per thread
     for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
       C<R> v[4];

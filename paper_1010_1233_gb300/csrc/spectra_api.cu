@@ -55,7 +55,7 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   P.ncol = kColsMax;
   while (P.ncol > 1 && fft_cols_smem(precision, F, len, P.ncol) > kColsSmemBudget) P.ncol >>= 1;
   P.rows_smem = fft_rows_smem(precision, nx);
-  P.rows_block = std::max(32, std::min(512, nx / 2));
+  P.rows_block = std::max(32, std::min(kRowsBlockMax, nx / 2));
   P.cols_smem = fft_cols_smem(precision, F, len, P.ncol);
   const int64_t tiles = (d.half_nx + P.ncol - 1) / P.ncol;
   P.n_vb_rows = (int64_t)((F + 1) / 2) * ny;
