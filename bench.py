@@ -110,6 +110,32 @@ def workload(n):
     return wl, wl["replicas"][0]
 
 
+def bind_local_cpus(device):
+    """Run on the CPUs local to `device` (sysfs local_cpulist of its PCI address), so that
+    the pinned host buffers of the end-to-end leg are allocated next to the GPU.  Returns
+    the CPU list used, or None when it cannot be determined."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(device)
+        dom, bus, dev = (getattr(pr, k, None) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+        if bus is None:
+            return None
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (dom or 0, bus, dev or 0)
+        with open(path) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return spec
+    except Exception:
+        return None
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -332,6 +358,7 @@ def run_ours3(args):
         import ctypes
         from paper_1010_1233_gb300 import _lib as L
         lib = L.lib()
+        local_cpus = bind_local_cpus(local)
         size = ctypes.c_size_t()
         L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
         nb = int(size.value)
@@ -349,7 +376,8 @@ def run_ours3(args):
         dt = time.perf_counter() - t0
         e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
         e2e = {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
-               "pinned": True, "what": "flb_load(host state) + K steps + flb_save(host state)"}
+               "pinned": True, "local_cpus": local_cpus,
+               "what": "flb_load(host state) + K steps + flb_save(host state)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -447,6 +475,7 @@ def run_ours(args):
         import ctypes
         from paper_1010_1233_gb300 import _lib as L
         lib = L.lib()
+        local_cpus = bind_local_cpus(local)
         size = ctypes.c_size_t()
         L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
         nb = int(size.value)
@@ -471,7 +500,8 @@ def run_ours(args):
         e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
         e2e = {"value": e2e_value, "unit": "MLUPS",
                "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
-               "pinned": pinned, "what": "flb_load(host state) + K steps + flb_save(host state)"}
+               "pinned": pinned, "local_cpus": local_cpus,
+               "what": "flb_load(host state) + K steps + flb_save(host state)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
