@@ -70,7 +70,7 @@ def build(force=False, verbose=False, ptxas_info=False):
             if log:
                 sys.stderr.write(log)
     tmp = LIB + ".tmp"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-lcuda"]
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

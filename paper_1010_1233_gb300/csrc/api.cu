@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "flb_internal.cuh"
 
 namespace flb {
@@ -51,6 +53,14 @@ void launch_point_dft(int precision, const ReplicaDesc* descs, int n_reps, int m
                       const TimeCorr& tc, size_t smem, cudaStream_t st);
 
 static thread_local std::string g_last_error;
+
+// NVTX range on the host timeline around a library call (no cost without an attached tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int set_error(int code, const char* fmt, ...) {
   char buf[512];
@@ -722,6 +732,7 @@ int flb_workspace_bytes(int precision, const flb_replica* reps, int n_replicas, 
 
 int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev_workspace,
                size_t workspace_bytes, void* cuda_stream, flb_ctx** out) {
+  NvtxRange range("flb_create");
   if (!out) return set_error(FLB_EINVAL, "out is NULL");
   *out = nullptr;
   Layout L;
@@ -787,6 +798,7 @@ static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S
 }
 
 static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
+  NvtxRange range(sample ? "flb step + sample" : "flb step");
   const Layout& L = c->L;
   launch_step_any(c, L.vec, L.staged, S, sample, st);
   if (sample && is3d(c->lattice)) {
@@ -872,6 +884,7 @@ static int chunk_graph(flb_ctx* c, uint32_t len, bool sample, cudaGraphExec_t* o
 }
 
 int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
+  NvtxRange range("flb_run");
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   const Layout& L = c->L;
   const bool sampling = sample_every && L.any_fields;
@@ -897,6 +910,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
       int rc = chunk_graph(c, len, sampling, &exec);
       if (rc) return rc;
       launch_set_step(reinterpret_cast<uint64_t*>(c->ws + L.off_stepdev), c->step, c->stream);
+      NvtxRange chunks_range(sampling ? "flb graph chunks (sampling)" : "flb graph chunks");
       for (uint64_t k = 0; k < chunks; ++k) {
         rc = cuda_check(cudaGraphLaunch(exec, c->stream), "graph launch");
         if (rc) return rc;
@@ -1130,6 +1144,7 @@ int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int ena
 }
 
 int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
+  NvtxRange range("flb_save");
   if (!c || !bytes_inout) return set_error(FLB_EINVAL, "NULL argument");
   const int64_t rs = c->precision == FLB_FP64 ? 8 : 4;
   size_t need = 64;
@@ -1165,6 +1180,7 @@ int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
 }
 
 int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
+  NvtxRange range("flb_load");
   if (!c || !host_buf) return set_error(FLB_EINVAL, "NULL argument");
   size_t need = 0;
   int rc = flb_save(c, nullptr, &need);
@@ -1241,6 +1257,7 @@ int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks, int* staged) {
 }
 
 int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out) {
+  NvtxRange range("flb_autotune");
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   if (trials < 1) return set_error(FLB_EINVAL, "trials must be >= 1");
   cudaEvent_t e0, e1;
