@@ -136,6 +136,41 @@ def bind_local_cpus(device):
     return None
 
 
+def end_to_end(sim, K, V, world, local, barrier):
+    """The same K steps through the public API with host buffers: load the state (a
+    checkpoint: populations and correlator sums) from pinned host memory, run, save the
+    final state back into the same buffer.  One buffer serves both directions (the load
+    reads it before the save overwrites it), so a rank pins one state's worth of host
+    memory; pageable memory when pinning fails."""
+    import ctypes
+    import torch
+    from paper_1010_1233_gb300 import _lib as L
+    lib = L.lib()
+    local_cpus = bind_local_cpus(local)
+    size = ctypes.c_size_t()
+    L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
+    nb = int(size.value)
+    try:
+        buf = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        pinned = True
+    except Exception:
+        buf = torch.empty(nb, dtype=torch.uint8)
+        pinned = False
+    ptr = ctypes.c_void_p(buf.data_ptr())
+    L.check(lib.flb_save(sim._ctx, ptr, ctypes.byref(size)))          # untimed: the initial state
+    barrier()
+    t0 = time.perf_counter()
+    L.check(lib.flb_load(sim._ctx, ptr, nb))
+    sim.run(K, SAMPLE_EVERY)
+    L.check(lib.flb_save(sim._ctx, ptr, ctypes.byref(size)))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    value, _ = job_throughput(V, K, dt, world, device="cuda")
+    return {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
+            "pinned": pinned, "local_cpus": local_cpus,
+            "what": "flb_load(host state) + K steps + flb_save(host state)"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -355,29 +390,7 @@ def run_ours3(args):
 
     e2e = None
     if not args.no_e2e:
-        import ctypes
-        from paper_1010_1233_gb300 import _lib as L
-        lib = L.lib()
-        local_cpus = bind_local_cpus(local)
-        size = ctypes.c_size_t()
-        L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
-        nb = int(size.value)
-        host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-        host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
-        # untimed: one save into the output buffer too, so both buffers have been used once
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
-        barrier()
-        t0 = time.perf_counter()
-        L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
-        sim.run(K, SAMPLE_EVERY)
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
-        e2e = {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
-               "pinned": True, "local_cpus": local_cpus,
-               "what": "flb_load(host state) + K steps + flb_save(host state)"}
+        e2e = end_to_end(sim, K, V, world, local, barrier)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -470,38 +483,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        # end to end through the public API with host buffers: load a checkpoint from pinned
-        # host memory, run K steps, save the final state (populations + correlator sums) back
-        import ctypes
-        from paper_1010_1233_gb300 import _lib as L
-        lib = L.lib()
-        local_cpus = bind_local_cpus(local)
-        size = ctypes.c_size_t()
-        L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
-        nb = int(size.value)
-        try:
-            host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-            host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-            pinned = True
-        except Exception:
-            host_in = torch.empty(nb, dtype=torch.uint8)
-            host_out = torch.empty(nb, dtype=torch.uint8)
-            pinned = False
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), ctypes.byref(size)))
-        # untimed: one save into the output buffer too, so both buffers have been used once
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
-        barrier()
-        t0 = time.perf_counter()
-        L.check(lib.flb_load(sim._ctx, ctypes.c_void_p(host_in.data_ptr()), nb))
-        sim.run(K, SAMPLE_EVERY)
-        L.check(lib.flb_save(sim._ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(size)))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e_value, _ = job_throughput(V, K, dt, world, device="cuda")
-        e2e = {"value": e2e_value, "unit": "MLUPS",
-               "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
-               "pinned": pinned, "local_cpus": local_cpus,
-               "what": "flb_load(host state) + K steps + flb_save(host state)"}
+        e2e = end_to_end(sim, K, V, world, local, barrier)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
