@@ -234,6 +234,18 @@ int flb_get_time_correlator(flb_ctx* ctx, int replica, int field_a, int field_b,
 int flb_set_step_config(flb_ctx* ctx, int vec, int grid_blocks, int staged);
 int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks, int* staged);
 
+/* Linear stability of one replica's parameters, on the host (no GPU, no context):
+ * the largest modulus of the eigenvalues of the one-step operator A_k = P_k J of the
+ * noise-free dynamics linearised about f^0(rho0, u0) (P_k the pull-streaming phases of
+ * Eq. 1, J the Jacobian of the collision of Eq. 5 with the equilibrium of Eq. 2), over
+ * the wave vectors k = 2 pi j / N, N = min(n, max_k) per lattice dimension, k = 0
+ * included (where the conserved moments give exactly 1).  A radius above 1 (beyond
+ * rounding) means some fluctuation grows every step: the run will diverge.  Spectral
+ * radius by Gelfand's formula (2^40-th power by normalised squaring).  radius_out: the
+ * maximum; k_out[3] (may be NULL): its (jx, jy, jz).  Validates the replica as
+ * flb_workspace_bytes does. */
+int flb_stability(const flb_replica* rep, int max_k, double* radius_out, int32_t* k_out);
+
 /* Autotuner: times `trials` launches of the step kernel (current network
  * setting, no sampling) for every valid configuration: direct kernels with
  * every vec and grid size in {2,4,8,16} x SMs and all-blocks, and the staged

@@ -8,5 +8,5 @@ structure factors / cross correlators (and time correlators at chosen wave
 vectors).  The compute path is libflb.so (hand-written sm_103a CUDA behind
 the C ABI of include/flb.h); this package binds it.
 """
-from .sim import Sim, philox, replica_struct, bf16_bits  # noqa: F401
+from .sim import Sim, philox, replica_struct, bf16_bits, stability  # noqa: F401
 from . import workloads  # noqa: F401

@@ -67,6 +67,7 @@ _SIGS = {
                                        c_size_t, c_void_p]),
     "flb_spectra_accumulate_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                               c_void_p]),
+    "flb_stability": (c_int, [POINTER(flb_replica), c_int, POINTER(c_double), POINTER(c_int32)]),
     "flb_philox": (c_int, [c_void_p, c_int, c_uint32, c_uint32, c_uint32, c_uint32, c_uint64, c_int,
                            c_void_p, c_void_p, c_void_p]),
 }

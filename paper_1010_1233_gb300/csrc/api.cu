@@ -9,9 +9,12 @@
 #include <string>
 #include <vector>
 
+#include <complex>
+
 #include <nvtx3/nvToolsExt.h>
 
 #include "flb_internal.cuh"
+#include "lattice3.cuh"
 
 namespace flb {
 
@@ -451,6 +454,62 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   L.off_stepdev = off; off = align256(off + 8);
   L.total = off;
   return FLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Linear stability of the noise-free dynamics about the uniform state f^0(rho0, u0).
+// At wave vector k one step acts as A_k = P_k J: P_k = diag(exp(-i k.v_i)) (pull
+// streaming, Eq. 1) and J the Jacobian of the collision (Eq. 5),
+//   J = I + N Lambda (M E - M),   E_ij = d f^0_i / d f_j  (Eq. 2 through rho and j),
+// with M the moment rows, N = (w_i m_i^a) the back transform and Lambda = diag(1/tau^a)
+// on the non-conserved moments.  f^0_i = w_i (rho + 3 v.j + 9/2 (v.j)^2 / rho - 3/2 j^2 / rho)
+// gives d f^0_i / d rho = w_i (1 - 9/2 (v.u)^2 + 3/2 u^2) and
+// d f^0_i / d j_a = w_i (3 v_a + 9 (v.u) v_a - 3 u_a).
+
+static int lattice_tables(int lat, int v[20][3], double w[20], double m[20][20]) {
+  const int q = lattice_q(lat);
+  for (int i = 0; i < q; ++i) {
+    if (lat == FLB_D2Q9) { v[i][0] = kVx9[i]; v[i][1] = kVy9[i]; v[i][2] = 0; }
+    else if (lat == FLB_D1Q3) { v[i][0] = kVx3[i]; v[i][1] = 0; v[i][2] = 0; }
+    else if (lat == FLB_D3Q15) { v[i][0] = v3x<15>(i); v[i][1] = v3y<15>(i); v[i][2] = v3z<15>(i); }
+    else { v[i][0] = v3x<19>(i); v[i][1] = v3y<19>(i); v[i][2] = v3z<19>(i); }
+    w[i] = lattice_weight(q, i);
+    for (int a = 0; a < q; ++a)
+      m[a][i] = is3d(lat) ? (lat == FLB_D3Q15 ? moment_row3<15>(a, v[i][0], v[i][1], v[i][2])
+                                              : moment_row3<19>(a, v[i][0], v[i][1], v[i][2]))
+                          : moment_row(lat == FLB_D2Q9, a, v[i][0], v[i][1]);
+  }
+  return q;
+}
+
+// rho(A) = lim ||A^n||^(1/n) (Gelfand), n = 2^40 by repeated squaring with the norm
+// factored out at every step
+static double spectral_radius_of(int q, std::complex<double> A[20][20]) {
+  typedef std::complex<double> cd;
+  cd B[20][20], T[20][20];
+  double nrm = 0.0;
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) nrm = std::max(nrm, std::abs(A[i][j]));
+  if (nrm == 0.0) return 0.0;
+  double logc = std::log(nrm);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) B[i][j] = A[i][j] / nrm;
+  const int kSquarings = 40;
+  for (int t = 0; t < kSquarings; ++t) {
+    double mx = 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        cd acc = 0.0;
+        for (int l = 0; l < q; ++l) acc += B[i][l] * B[l][j];
+        T[i][j] = acc;
+        mx = std::max(mx, std::abs(acc));
+      }
+    if (mx == 0.0) return 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) B[i][j] = T[i][j] / mx;
+    logc = 2.0 * logc + std::log(mx);
+  }
+  return std::exp(std::ldexp(logc, -kSquarings));
 }
 
 }  // namespace flb
@@ -1330,6 +1389,63 @@ void flb_destroy(flb_ctx* c) {
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
+}
+
+int flb_stability(const flb_replica* rep, int max_k, double* radius_out, int32_t* k_out) {
+  if (!rep || !radius_out) return set_error(FLB_EINVAL, "NULL argument");
+  if (max_k < 1) return set_error(FLB_EINVAL, "max_k must be >= 1");
+  int rc = validate(FLB_FP64, rep, 1);
+  if (rc) return rc;
+  const flb_replica& p = *rep;
+  const int lat = p.lattice, q = lattice_q(lat), nc0 = first_nonconserved(lat);
+  int v[20][3];
+  double w[20], m[20][20];
+  lattice_tables(lat, v, w, m);
+  const double u[3] = {p.u0[0], lat == FLB_D1Q3 ? 0.0 : p.u0[1], is3d(lat) ? p.u0[2] : 0.0};
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  // E = d f^0 / d f, then J = I + N Lambda (M E - M)
+  double E[20][20], ME[20][20], J[20][20];
+  for (int i = 0; i < q; ++i) {
+    const double vu = v[i][0] * u[0] + v[i][1] * u[1] + v[i][2] * u[2];
+    const double drho = w[i] * (1.0 - 4.5 * vu * vu + 1.5 * uu);
+    double dj[3];
+    for (int a = 0; a < 3; ++a) dj[a] = w[i] * (3.0 * v[i][a] + 9.0 * vu * v[i][a] - 3.0 * u[a]);
+    for (int j = 0; j < q; ++j) E[i][j] = drho + dj[0] * v[j][0] + dj[1] * v[j][1] + dj[2] * v[j][2];
+  }
+  for (int a = 0; a < q; ++a)
+    for (int j = 0; j < q; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < q; ++i) acc += m[a][i] * E[i][j];
+      ME[a][j] = acc;
+    }
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      double acc = i == j ? 1.0 : 0.0;
+      for (int a = nc0; a < q; ++a) acc += w[i] * m[a][i] / p.tau[a] * (ME[a][j] - m[a][j]);
+      J[i][j] = acc;
+    }
+  // the k-grid: N points per lattice dimension, N = min(n, max_k), k = 2 pi j / N
+  const int N[3] = {std::min(p.nx, max_k), lat == FLB_D1Q3 ? 1 : std::min(p.ny, max_k),
+                    is3d(lat) ? std::min(p.nz, max_k) : 1};
+  const double two_pi = 6.283185307179586477;
+  double best = 0.0;
+  int bk[3] = {0, 0, 0};
+  std::complex<double> A[20][20];
+  for (int kz = 0; kz < N[2]; ++kz)
+    for (int ky = 0; ky < N[1]; ++ky)
+      for (int kx = 0; kx < N[0]; ++kx) {
+        const double k[3] = {two_pi * kx / N[0], two_pi * ky / N[1], two_pi * kz / N[2]};
+        for (int i = 0; i < q; ++i) {
+          const double ph = -(k[0] * v[i][0] + k[1] * v[i][1] + k[2] * v[i][2]);
+          const std::complex<double> e(std::cos(ph), std::sin(ph));
+          for (int j = 0; j < q; ++j) A[i][j] = e * J[i][j];
+        }
+        const double r = spectral_radius_of(q, A);
+        if (r > best) { best = r; bk[0] = kx; bk[1] = ky; bk[2] = kz; }
+      }
+  *radius_out = best;
+  if (k_out) { k_out[0] = bk[0]; k_out[1] = bk[1]; k_out[2] = bk[2]; }
+  return FLB_OK;
 }
 
 int flb_philox(const uint32_t* site_dev, int n, uint32_t step, uint32_t call, uint32_t tag, uint32_t stream,

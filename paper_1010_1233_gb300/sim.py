@@ -42,6 +42,16 @@ def replica_struct(p):
     return s
 
 
+def stability(p, max_k=64):
+    """(spectral radius, (jx, jy, jz)) of the linearised one-step operator of replica
+    parameters p over a k-grid (flb_stability); a radius above 1 means the run diverges."""
+    s = replica_struct(p)
+    r = ctypes.c_double()
+    k = (ctypes.c_int32 * 3)()
+    L.check(L.lib().flb_stability(ctypes.byref(s), int(max_k), ctypes.byref(r), k))
+    return float(r.value), (int(k[0]), int(k[1]), int(k[2]))
+
+
 def bf16_bits(x):
     """bfloat16 bit patterns (round to nearest even) of an FP32 array, via torch."""
     t = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16)
