@@ -140,8 +140,9 @@ def end_to_end(sim, K, V, world, local, barrier):
     """The same K steps through the public API with host buffers: load the state (a
     checkpoint: populations and correlator sums) from pinned host memory, run, save the
     final state to a second pinned buffer.  (Loading from and saving to one buffer was
-    measured 2-5 % slower on GB300, its copy rate falling from run to run.)  Pageable
-    memory when pinning fails."""
+    measured 2-5 % slower on GB300, its copy rate falling from run to run; it is used
+    only when two buffers per rank do not fit in the host's memory.)  Pageable memory
+    when pinning fails."""
     import ctypes
     import torch
     from paper_1010_1233_gb300 import _lib as L
@@ -150,13 +151,26 @@ def end_to_end(sim, K, V, world, local, barrier):
     size = ctypes.c_size_t()
     L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
     nb = int(size.value)
+    # host memory: every rank of this node holds its buffers at once; two buffers when
+    # they fit in 60 % of the physical memory, one shared buffer otherwise, none below that
+    try:
+        phys = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        phys = 0
+    ranks_here = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    n_buf = 2
+    if phys and 2 * nb * ranks_here > 0.6 * phys:
+        n_buf = 1 if nb * ranks_here <= 0.6 * phys else 0
+    if n_buf == 0:
+        return {"value": None, "unit": "MLUPS", "skipped": "state of %.1f GB per rank x %d ranks exceeds the host's "
+                "memory" % (nb / 1e9, ranks_here)}
     try:
         host_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-        host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True) if n_buf == 2 else host_in
         pinned = True
     except Exception:
         host_in = torch.empty(nb, dtype=torch.uint8)
-        host_out = torch.empty(nb, dtype=torch.uint8)
+        host_out = torch.empty(nb, dtype=torch.uint8) if n_buf == 2 else host_in
         pinned = False
     pin, pout = ctypes.c_void_p(host_in.data_ptr()), ctypes.c_void_p(host_out.data_ptr())
     L.check(lib.flb_save(sim._ctx, pin, ctypes.byref(size)))          # untimed: the initial state
@@ -170,7 +184,7 @@ def end_to_end(sim, K, V, world, local, barrier):
     dt = time.perf_counter() - t0
     value, _ = job_throughput(V, K, dt, world, device="cuda")
     return {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
-            "pinned": pinned, "local_cpus": local_cpus,
+            "pinned": pinned, "host_buffers": n_buf, "local_cpus": local_cpus,
             "what": "flb_load(host state) + K steps + flb_save(host state)"}
 
 
