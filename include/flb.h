@@ -152,24 +152,28 @@ int flb_reset_stats(flb_ctx* ctx);
  * on the full grid: host_out[(ky*nx + kx)*2 + {0,1}] = {Re, Im}, with
  * k = 2 pi (kx/nx, ky/ny).  N^ab = 1/(V sqrt(var_a var_b)), var = mu rho0 for a
  * moment field, kT/rho0 for a velocity field (both fields must be sampled).
- * n_samples (may be NULL) receives the number of samples.  Synchronises. */
+ * n_samples (may be NULL) receives the number of samples.  D1Q3 and D2Q9 only: the
+ * 3D lattices accumulate correlators at chosen wave vectors (flb_set_time_correlator3,
+ * flb_get_time_correlator; FLB_EINVAL here).  Synchronises. */
 int flb_get_correlator(flb_ctx* ctx, int replica, int field_a, int field_b,
                        double* host_out, uint64_t* n_samples);
 
 /* Copy the stored (post-collision) populations f_i of a replica to / from host
- * FP64 [q][ny][nx].  For FLB_FP32_DEV they are converted from / to f - w rho0
- * in FP32.  Synchronises. */
+ * FP64 [q][ny][nx] ([q][nz][ny][nx] on the 3D lattices).  For FLB_FP32_DEV they
+ * are converted from / to f - w rho0 in FP32.  Synchronises. */
 int flb_get_populations(flb_ctx* ctx, int replica, double* host_out);
 int flb_set_populations(flb_ctx* ctx, int replica, const double* host_in);
 
 /* Copy the populations of a rectangular window [x0, x0+w) x [y0, y0+h) of a replica
  * (no wrap-around: the window must lie inside the lattice) to host FP64 [q][h][w].
- * For sampling outputs of large lattices without copying the whole state.  Synchronises. */
+ * For sampling outputs of large lattices without copying the whole state.  D1Q3 and
+ * D2Q9 only (FLB_EINVAL on the 3D lattices).  Synchronises. */
 int flb_get_populations_window(flb_ctx* ctx, int replica, int x0, int y0, int w, int h,
                                double* host_out);
 
 /* The fields of the most recent sample of a replica (Eq. 11 inputs, before the
- * transform): host FP64 [n_fields][ny][nx], fields in increasing id order.
+ * transform): host FP64 [n_fields][ny][nx] ([n_fields][nz][ny][nx] on the 3D
+ * lattices), fields in increasing id order.
  * FLB_ESTATE before the first sample.  Synchronises. */
 int flb_get_fields(flb_ctx* ctx, int replica, double* host_out);
 
