@@ -81,16 +81,18 @@ __device__ __forceinline__ void dit_group(C<R> (&v)[1 << RS], int logn, int s, i
 
 // RS consecutive stages in one pass through shared memory: each thread takes groups of
 // 2^RS elements closed under those stages, keeps them in registers through the RS stages
-// and writes them back (one barrier per RS stages).
+// and writes them back (one barrier per RS stages).  Work item g = q n_fft + k (group q of
+// sequence k): neighbouring threads take the same group of neighbouring sequences, so with
+// an odd seq_stride their accesses fall in distinct banks and they share the twiddles.
 template <typename R, int RS>
 __device__ __forceinline__ void dit_pass(C<R>* data, int logn, int n_fft, int seq_stride,
                                          const C<R>* __restrict__ tw, int tw_stride, int pad_shift, int s) {
   constexpr int G = 1 << RS;
   const int lg = logn - RS;                          // log2 of the groups per sequence
-  const int total = n_fft << lg;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
-    const int k = g >> lg;
-    const int q = g & ((1 << lg) - 1);
+  const int groups = 1 << lg;
+  int q = (int)threadIdx.x / n_fft, k = (int)threadIdx.x - q * n_fft;
+  const int dq = (int)blockDim.x / n_fft, dk = (int)blockDim.x - dq * n_fft;
+  for (; q < groups;) {
     const int low = q & ((1 << s) - 1);
     const int i0 = ((q >> s) << (s + RS)) | low;
     C<R>* d = data + k * seq_stride;
@@ -106,6 +108,9 @@ __device__ __forceinline__ void dit_pass(C<R>* data, int logn, int n_fft, int se
       const int e = i0 + (t << s);
       d[e + (e >> pad_shift)] = v[t];
     }
+    q += dq;                                         // g += blockDim.x
+    k += dk;
+    if (k >= n_fft) { k -= n_fft; ++q; }
   }
 }
 
@@ -309,7 +314,8 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
 // Pass 2b: one block per (replica, k1, tile of ncol columns); all fields of the tile.
 // One-pass columns are the case N1 = 1.
 template <typename R>
-__global__ void k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
+__global__ void __launch_bounds__(kColsBlock, sizeof(R) == 4 ? 4 : 2)     // FP32: four blocks per SM
+k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
                                int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol, TimeCorr tc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* s = reinterpret_cast<C<R>*>(smem_raw);
@@ -475,6 +481,11 @@ int fft_cols_smem(int precision, int F, int ny, int ncol) { return F * (ny + 1) 
 cudaError_t set_fft_smem_limits() {
   cudaError_t e;
   const int maxb = 227 * 1024;
+  // the transforms want shared memory, not L1 (a preference; the driver may round it)
+  const int carve = (int)cudaSharedmemCarveoutMaxShared;
+  if ((e = cudaFuncSetAttribute(k_fft_rows<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+  if ((e = cudaFuncSetAttribute(k_fft_cols_a<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+  if ((e = cudaFuncSetAttribute(k_fft_cols_acc<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_acc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
