@@ -436,7 +436,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.vb_cols_a[r] = L.n_vb_cols_a;
     if (d.n_pairs) {
       const int64_t tiles = (d.half_nx + L.ncol - 1) / L.ncol;
-      L.n_vb_rows += (int64_t)((d.n_fields + 1) / 2) * d.ny;
+      L.n_vb_rows += ((int64_t)d.n_fields * d.ny + 1) / 2;           // two row units per block
       L.n_vb_cols += tiles << d.log2n1;                       // (k1, tile)
       if (d.log2n1) L.n_vb_cols_a += tiles * (d.ny >> d.log2n1);   // (y2, tile)
     }

@@ -3,9 +3,10 @@
 // of X_a(k) X_b(k)^* for every sampled field pair on the half spectrum
 // kx in [0, nx/2] (the other half follows from X(-k) = X(k)^* for real fields).
 //
-// Pass 1 (rows): two real fields are packed as one complex row z = X_a + i X_b,
-// transformed along x in shared memory, and unpacked into the row transforms
-// of both fields, X_a(kx) = (Z(kx) + Z(-kx)^*)/2, X_b(kx) = (Z(kx) - Z(-kx)^*)/(2i).
+// Pass 1 (rows): two real rows (consecutive (field, row) units) are packed as one
+// complex row z = X_a + i X_b, transformed along x in shared memory, and unpacked
+// into the transforms of both rows, X_a(kx) = (Z(kx) + Z(-kx)^*)/2,
+// X_b(kx) = (Z(kx) - Z(-kx)^*)/(2i).
 // Pass 2 (columns): tiles of columns of every field are transformed along y in
 // shared memory and the pair products are added to the FP64 sums.  Columns too
 // long for shared memory use the four-step split ny = N1 N2, y = N2 y1 + y2,
@@ -55,12 +56,25 @@ __device__ __forceinline__ C<R> rot8(C<R> w, int st, int u) {
   return r;
 }
 
+// w * exp(-2 pi i u / 2^(st+1)) for st <= 3 (u < 2^st): odd sixteenth roots of unity
+// by a complex multiplication with cos(pi/8), sin(pi/8), the others through rot8
+template <typename R>
+__device__ __forceinline__ C<R> rot16(C<R> w, int st, int u) {
+  if (st < 3) return rot8<R>(w, st, u);
+  if ((u & 1) == 0) return rot8<R>(w, 2, u >> 1);
+  const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173;
+  C<R> z;                                             // exp(-2 pi i u / 16), u = 1, 3, 5, 7
+  z.x = u == 1 ? c1 : (u == 3 ? s1 : (u == 5 ? -s1 : -c1));
+  z.y = u == 1 ? -s1 : (u == 3 ? -c1 : (u == 5 ? -c1 : -s1));
+  return cmul<R>(w, z);
+}
+
 // The butterflies of RS consecutive radix-2 decimation-in-time stages s .. s + RS - 1
 // on a group of 2^RS elements held in registers: v[t] is element i0 + t 2^s of the
 // sequence, where i0 has bits s .. s+RS-1 clear and low = i0 mod 2^s.  Stage S = s + st
 // pairs t with t + 2^st and multiplies by exp(-2 pi i pos / 2^(S+1)),
 // pos = low + (t mod 2^st) 2^s, i.e. the base twiddle exp(-2 pi i low / 2^(S+1)) (one
-// table read per stage) times an eighth root of unity.
+// table read per stage) times an eighth (sixteenth for RS = 4) root of unity.
 template <typename R, int RS>
 __device__ __forceinline__ void dit_group(C<R> (&v)[1 << RS], int logn, int s, int low,
                                           const C<R>* __restrict__ tw, int tw_stride) {
@@ -70,7 +84,7 @@ __device__ __forceinline__ void dit_group(C<R> (&v)[1 << RS], int logn, int s, i
 #pragma unroll
     for (int t = 0; t < (1 << RS); ++t) {
       if (t & (1 << st)) continue;
-      const C<R> w = rot8<R>(base, st, t & ((1 << st) - 1));
+      const C<R> w = rot16<R>(base, st, t & ((1 << st) - 1));
       const C<R> a = v[t];
       const C<R> tt = cmul<R>(v[t + (1 << st)], w);
       v[t].x = a.x + tt.x; v[t].y = a.y + tt.y;
@@ -118,14 +132,16 @@ __device__ __forceinline__ void dit_pass(C<R>* data, int logn, int n_fft, int se
 // shared memory, sequence k at data + k * seq_stride, already in bit-reversed order.
 // tw[m * tw_stride] = exp(-2 pi i m / 2^logn), m < 2^(logn-1).  Element i of a sequence is
 // stored at i + (i >> pad_shift) (one pad slot per 2^pad_shift elements, so that the
-// bit-reversed scatter does not hit one bank).  Stages s0 .. logn - 1 run three at a
+// bit-reversed scatter does not hit one bank).  Stages s0 .. logn - 1 run MAXRS at a
 // time (dit_pass).  All threads of the block call it.
-template <typename R>
+template <typename R, int MAXRS = 3>
 __device__ void dit_fft(C<R>* data, int logn, int n_fft, int seq_stride, const C<R>* __restrict__ tw,
                         int tw_stride, int pad_shift = 31, int s0 = 0) {
+  static_assert(MAXRS == 3 || MAXRS == 4, "three or four stages per pass");
   for (int s = s0; s < logn;) {
-    const int rs = logn - s >= 3 ? 3 : logn - s;
-    if (rs == 3) dit_pass<R, 3>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
+    const int rs = logn - s >= MAXRS ? MAXRS : logn - s;
+    if (rs == 4) dit_pass<R, (MAXRS == 4 ? 4 : 3)>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
+    else if (rs == 3) dit_pass<R, 3>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
     else if (rs == 2) dit_pass<R, 2>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
     else dit_pass<R, 1>(data, logn, n_fft, seq_stride, tw, tw_stride, pad_shift, s);
     s += rs;
@@ -146,7 +162,7 @@ __device__ __forceinline__ int find_rep(const int64_t* vb_begin, int n_reps, int
   return lo;
 }
 
-// Pass 1: one block per (replica, packed field pair, row).
+// Pass 1: one block per (replica, packed pair of row units).
 template <typename R>
 __global__ void __launch_bounds__(kRowsBlockMax)
 k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
@@ -156,16 +172,17 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
-    const int64_t local = vb - vb_begin[r];
-    const int y = (int)(local & (d.ny - 1));              // ny is a power of two
-    const int p = (int)(local >> d.log2ny);
-    const int fa = 2 * p, fb = 2 * p + 1;
-    const bool has_b = fb < (int)d.n_fields;
+    // block vb packs the row units u = 2 local and u + 1 (unit u: field u / ny, row u % ny;
+    // ny is a power of two), so an odd field count leaves at most one half-empty transform
+    const int64_t ua = 2 * (vb - vb_begin[r]), ub = ua + 1;
+    const bool has_b = ub < (int64_t)d.n_fields << d.log2ny;
+    const int fa = (int)(ua >> d.log2ny), ya = (int)(ua & (d.ny - 1));
+    const int fb = (int)(ub >> d.log2ny), yb = (int)(ub & (d.ny - 1));
     const int nx = d.nx, logn = d.log2nx;
     const int64_t plane = (int64_t)nx * d.ny;
     const R* fields = reinterpret_cast<const R*>(ws + d.off_fields);
-    const R* xa = fields + fa * plane + (int64_t)y * nx;
-    const R* xb = fields + fb * plane + (int64_t)y * nx;
+    const R* xa = fields + fa * plane + (int64_t)ya * nx;
+    const R* xb = fields + fb * plane + (int64_t)yb * nx;
     const int ps = logn > 5 ? logn - 5 : 31;        // 32 pad slots per row
     const C<R>* tw = reinterpret_cast<const C<R>*>(ws + d.off_tw_x);
     // the rows of this block's next pair into L2 while this pair is transformed
@@ -173,17 +190,14 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
       const int64_t vbn = vb + gridDim.x;
       const int rn = find_rep(vb_begin, n_reps, vbn);
       const ReplicaDesc& dn = descs[rn];
-      const int64_t ln = vbn - vb_begin[rn];
-      const int yn = (int)(ln & (dn.ny - 1)), pn = (int)(ln >> dn.log2ny);
-      const int64_t pl = (int64_t)dn.nx * dn.ny;
+      const int64_t un = 2 * (vbn - vb_begin[rn]);
       const R* fn = reinterpret_cast<const R*>(ws + dn.off_fields);
       const uint32_t bytes = (uint32_t)(dn.nx * sizeof(R));
-      if (bytes % 16 == 0) {
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(fn + 2 * pn * pl + (int64_t)yn * dn.nx),
-                     "r"(bytes) : "memory");
-        if (2 * pn + 1 < (int)dn.n_fields)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                       :: "l"(fn + (2 * pn + 1) * pl + (int64_t)yn * dn.nx), "r"(bytes) : "memory");
+      if (bytes % 16 == 0) {         // unit u starts at u nx (the fields are contiguous rows)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(fn + un * dn.nx), "r"(bytes) : "memory");
+        if (un + 1 < (int64_t)dn.n_fields << dn.log2ny)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(fn + (un + 1) * dn.nx), "r"(bytes)
+                       : "memory");
       }
     }
     if (logn >= 3) {
@@ -205,7 +219,7 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
         for (int t = 0; t < 8; ++t) z[i0 + t + ((i0 + t) >> ps)] = v[t];
       }
       __syncthreads();
-      dit_fft<R>(z, logn, 1, 0, tw, 1, ps, 3);
+      dit_fft<R, sizeof(R) == 4 ? 4 : 3>(z, logn, 1, 0, tw, 1, ps, 3);   // FP32: four stages per pass
     } else {
       for (int x = threadIdx.x; x < nx; x += blockDim.x) {
         C<R> v; v.x = xa[x]; v.y = has_b ? xb[x] : (R)0;
@@ -217,8 +231,8 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
     }
     C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
-    C<R>* ra = spec + fa * fplane + (int64_t)y * d.wpitch;
-    C<R>* rb = spec + fb * fplane + (int64_t)y * d.wpitch;
+    C<R>* ra = spec + fa * fplane + (int64_t)ya * d.wpitch;
+    C<R>* rb = spec + fb * fplane + (int64_t)yb * d.wpitch;
     const int hn = nx >> 1;
     for (int k = threadIdx.x; k <= hn; k += blockDim.x) {
       const int km = (nx - k) & (nx - 1);

@@ -58,7 +58,7 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   P.rows_block = std::max(32, std::min(kRowsBlockMax, nx / 2));
   P.cols_smem = fft_cols_smem(precision, F, len, P.ncol);
   const int64_t tiles = (d.half_nx + P.ncol - 1) / P.ncol;
-  P.n_vb_rows = (int64_t)((F + 1) / 2) * ny;
+  P.n_vb_rows = ((int64_t)F * ny + 1) / 2;                   // two row units per block
   P.n_vb_cols = tiles << l1;
   P.n_vb_cols_a = l1 ? tiles * (ny >> l1) : 0;
   int64_t off = 0;
