@@ -516,7 +516,7 @@ static double spectral_radius_of(int q, std::complex<double> A[20][20]) {
 
 using namespace flb;
 
-static constexpr uint32_t kGraphChunk = 32;      // steps per captured chunk without sampling
+static constexpr uint32_t kGraphChunk = 32;      // at least this many steps per captured chunk
 static constexpr uint32_t kMaxGraphChunk = 4096;  // longer sampling periods are issued directly
 
 struct flb_ctx {
@@ -531,7 +531,7 @@ struct flb_ctx {
   bool mlp_on = false;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
-  struct Graph { uint32_t len; bool sample; cudaGraphExec_t exec; };
+  struct Graph { uint32_t len, every; cudaGraphExec_t exec; };
   std::vector<Graph> graphs;
   std::vector<float> mlp_host;
   TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
@@ -913,10 +913,11 @@ static void drop_graphs(flb_ctx* c) {
 }
 
 // A chunk of `len` steps starting at a step that is a multiple of len, sampling at its
-// first step when `sample`; it ends by advancing the device step counter by len.
-static int chunk_graph(flb_ctx* c, uint32_t len, bool sample, cudaGraphExec_t* out) {
+// steps o with o % every == 0 (every = 0: no sampling; len is a multiple of every); it
+// ends by advancing the device step counter by len.
+static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t* out) {
   for (auto& g : c->graphs)
-    if (g.len == len && g.sample == sample) { *out = g.exec; return FLB_OK; }
+    if (g.len == len && g.every == every) { *out = g.exec; return FLB_OK; }
   if (!c->cap_stream) {
     int rc = cuda_check(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
     if (rc) return rc;
@@ -927,7 +928,7 @@ static int chunk_graph(flb_ctx* c, uint32_t len, bool sample, cudaGraphExec_t* o
   if (rc) return rc;
   for (uint32_t o = 0; o < len; ++o) {
     S.step = o;
-    issue_step(c, S, sample && o == 0, c->cap_stream);
+    issue_step(c, S, every && o % every == 0, c->cap_stream);
   }
   launch_advance_step(reinterpret_cast<uint64_t*>(c->ws + c->L.off_stepdev), len, c->cap_stream);
   cudaGraph_t graph = nullptr;
@@ -937,7 +938,7 @@ static int chunk_graph(flb_ctx* c, uint32_t len, bool sample, cudaGraphExec_t* o
   rc = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "instantiate graph");
   cudaGraphDestroy(graph);
   if (rc) return rc;
-  c->graphs.push_back({len, sample, exec});
+  c->graphs.push_back({len, every, exec});
   *out = exec;
   return FLB_OK;
 }
@@ -957,16 +958,20 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
     if (sample) ++c->n_samples;
     ++c->step;
   };
-  // chunks of `len` steps replay a captured graph; steps before the first aligned chunk
-  // and after the last one are issued directly
-  const uint32_t len = sampling ? sample_every : kGraphChunk;
+  // chunks of `len` steps (whole sampling periods, at least kGraphChunk steps) replay a
+  // captured graph; steps before the first aligned chunk and after the last one are
+  // issued directly
+  const uint32_t every = sampling ? sample_every : 0;
+  const uint32_t len = !sampling ? kGraphChunk
+                       : (sample_every >= kGraphChunk ? sample_every
+                                                      : sample_every * ((kGraphChunk + sample_every - 1) / sample_every));
   uint64_t i = 0;
   if (c->use_graphs && n_steps >= 2 * (uint64_t)len && len <= kMaxGraphChunk) {
     while (i < n_steps && (c->step % len) != 0) { plain(); ++i; }
     const uint64_t chunks = (n_steps - i) / len;
     if (chunks) {
       cudaGraphExec_t exec = nullptr;
-      int rc = chunk_graph(c, len, sampling, &exec);
+      int rc = chunk_graph(c, len, every, &exec);
       if (rc) return rc;
       launch_set_step(reinterpret_cast<uint64_t*>(c->ws + L.off_stepdev), c->step, c->stream);
       NvtxRange chunks_range(sampling ? "flb graph chunks (sampling)" : "flb graph chunks");
@@ -975,7 +980,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
         if (rc) return rc;
       }
       c->step += chunks * len;
-      if (sampling) c->n_samples += chunks;
+      if (sampling) c->n_samples += chunks * (len / every);
       i += chunks * len;
     }
   }

@@ -321,6 +321,23 @@ def test_step_configs_and_autotune(with_mlp):
     assert _rel(sim.populations(), ref[0], ref[0] - feq) < 1e-5
 
 
+@pytest.mark.parametrize("every", [1, 3])
+def test_graph_chunks_of_several_sampling_periods_d1q3(every):
+    """A captured chunk holds whole sampling periods of at least 32 steps (32 or 33 steps
+    here); replaying it gives the populations, sums and sample count of direct steps."""
+    p = W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1, 2))
+    a, b = Sim(p, precision="fp64"), Sim(p, precision="fp64")
+    b.set_graphs(False)
+    for n in (5, 100, 7):
+        a.run(n, every)
+        b.run(n, every)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in ((0, 0), (0, 1), (1, 2)):
+        ca, na = a.correlator(0, x, y, with_count=True)
+        cb, nb = b.correlator(0, x, y, with_count=True)
+        assert na == nb == len(range(0, 112, every)) and np.array_equal(ca, cb)
+
+
 @pytest.mark.parametrize("every", [0, 4, 5])
 def test_graph_replay_bitwise_equal_direct(every):
     reps = [W.replica("D2Q9", 32, 16, W.taus_d2q9(0.8), kT=1e-4, u0=(0.05, 0), seed=3, init_mode=1,

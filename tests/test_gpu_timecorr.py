@@ -45,7 +45,7 @@ def test_batched_replicas_and_graphs():
                       fields=(0, 9)),
             W.replica("D2Q9", 32, 16, W.taus_d2q9(0.7), kT=1e-4, u0=(0.0, 0.1), seed=2, stream=2, init_mode=1,
                       fields=(0, 9, 10))]
-    T, steps, every = 4, 60, 2
+    T, steps, every = 4, 80, 2                      # 80 steps: two graph chunks of 32 steps and direct steps
     outs = []
     for graphs in (True, False):
         sim = Sim(reps, precision="fp32")
