@@ -42,6 +42,10 @@ void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+// D1Q3 runs of steps with their sampling in one launch (lb_d1q3_fused.cu)
+size_t d1q3_fused_smem(int precision, int nx, int F);
+cudaError_t launch_d1q3_fused(int precision, const ReplicaDesc* descs, int n_reps, char* ws, uint64_t t0,
+                              uint32_t n_steps, uint32_t every, size_t smem, cudaStream_t st);
 // D3Q15 / D3Q19 (lb_3d.cu), q = 15 or 19
 void launch_step3(int q, int precision, int vec, const StepLaunch& L, bool sample, cudaStream_t st);
 void launch_init3(int q, int precision, const ReplicaDesc* descs, int r, char* ws, int mode, const double* feq0,
@@ -518,6 +522,8 @@ using namespace flb;
 
 static constexpr uint32_t kGraphChunk = 32;      // at least this many steps per captured chunk
 static constexpr uint32_t kMaxGraphChunk = 4096;  // longer sampling periods are issued directly
+static constexpr uint32_t kFusedChunk = 4096;     // D1Q3 steps per fused launch
+static constexpr size_t kFusedSmemMax = 200 * 1024;
 
 struct flb_ctx {
   int precision = 0, lattice = 0, n = 0;
@@ -537,6 +543,7 @@ struct flb_ctx {
   TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
   int64_t tc_off_sums0 = 0, tc_bytes = 0;      // start of the sums (first replica) and buffer size
   size_t tc_smem = 0;                          // 3D direct transforms: dynamic shared memory
+  size_t fused_smem = 0;                       // D1Q3: shared memory of the fused kernel (0: not used)
 };
 
 static ReplicaDesc* descs_dev(flb_ctx* c) { return reinterpret_cast<ReplicaDesc*>(c->ws + c->L.off_descs); }
@@ -811,6 +818,12 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
   if ((rc = cuda_check(set_fft_smem_limits(), "smem limits"))) { delete c; return rc; }
+  if (c->lattice == FLB_D1Q3) {      // the fused kernel holds a replica in one block's shared memory
+    size_t smem = 0;
+    for (const ReplicaDesc& d : c->L.desc)
+      smem = std::max(smem, d1q3_fused_smem(precision, d.nx, (int)d.n_fields));
+    c->fused_smem = smem <= kFusedSmemMax ? smem : 0;
+  }
   cudaStream_t st = c->stream;
   const Layout& Lc = c->L;
   rc = cuda_check(cudaMemcpyAsync(c->ws + Lc.off_descs, Lc.desc.data(), n_replicas * sizeof(ReplicaDesc),
@@ -948,6 +961,24 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
   const Layout& L = c->L;
   const bool sampling = sample_every && L.any_fields;
+  if (c->fused_smem && c->use_graphs && !c->tc.base) {
+    // D1Q3: runs of up to kFusedChunk steps with their sampling in one launch
+    NvtxRange fused_range("flb fused D1Q3 steps");
+    const uint32_t every = sampling ? sample_every : 0;
+    for (uint64_t i = 0; i < n_steps;) {
+      const uint32_t n = (uint32_t)std::min<uint64_t>(n_steps - i, kFusedChunk);
+      int rc = cuda_check(launch_d1q3_fused(c->precision, descs_dev(c), c->n, c->ws, c->step, n, every,
+                                            c->fused_smem, c->stream), "fused D1Q3 launch");
+      if (rc) return rc;
+      if (every) {               // samples at the steps t in [step, step + n) with t % every == 0
+        const uint64_t first = (c->step + every - 1) / every * every;
+        if (first < c->step + n) c->n_samples += (c->step + n - 1 - first) / every + 1;
+      }
+      c->step += n;
+      i += n;
+    }
+    return FLB_OK;
+  }
   StepLaunch S = step_launch(c);
   auto plain = [&]() {
     const uint64_t t = c->step;

@@ -11,6 +11,7 @@
 // The variant with the noise-scale network is in lb_step_tc.cu.
 #include <cstdio>
 #include "step_common.cuh"
+#include "d1q3_common.cuh"
 
 #ifndef FLB_STEP_MINB_PLAIN
 #define FLB_STEP_MINB_PLAIN 3  // minimum resident blocks per SM (caps the registers at 85)
@@ -70,7 +71,7 @@ k_step_d2q9(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Repli
 }
 
 // ---------------------------------------------------------------------------
-// D1Q3: v = (0, +1, -1), w = (2/3, 1/6, 1/6), moments 1, sqrt3 v, (3 v^2 - 1)/sqrt2.
+// D1Q3, one step (d1q3_common.cuh) per launch.
 template <typename R, bool DEV, bool SAMPLE>
 __global__ void __launch_bounds__(256)
 k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin, int n_reps,
@@ -88,39 +89,9 @@ k_step_d1q3(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ v
     const int64_t x64 = (vb - vb_begin[r]) * blockDim.x + threadIdx.x;
     if (x64 >= d.n_units) continue;
     const int x = (int)x64;
-    const R* src = reinterpret_cast<const R*>(ws + d.off_pop[parity]);
-    R* dst = reinterpret_cast<R*>(ws + d.off_pop[parity ^ 1]);
-    const R g0 = src[x];
-    const R g1 = src[nx + (x == 0 ? nx - 1 : x - 1)];
-    const R g2 = src[2 * nx + (x == nx - 1 ? 0 : x + 1)];
-    const R sum = g0 + (g1 + g2);
-    const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
-    const R j = g1 - g2;
-    const R u = j / rho;
-    const R S2 = (R)1.4142135623730950488, IS2 = (R)0.70710678118654752440;
-    const R M2 = S2 * (g1 + g2) - IS2 * g0;
-    const R E2 = (R)3 * IS2 * rho * u * u;
-    if constexpr (SAMPLE) {
-      R* fields = reinterpret_cast<R*>(ws + d.off_fields);
-      const R mom[3] = {sum, (R)1.7320508075688772935 * j, M2};
-      for (int slot = 0; slot < (int)d.n_fields; ++slot) {
-        const int fid = d.field_id[slot];
-        const R val = fid < 3 ? mom[fid] - coef<R>(d, kCoMref + fid) : u - coef<R>(d, kCoU0x);
-        fields[(int64_t)slot * nx + x] = val;
-      }
-    }
-    R D2 = (E2 - M2) * coef<R>(d, kCoInvTau + 2);
-    if (d.noise_mask) {
-      const uint4 w = philox4x32_10((uint32_t)x, step, 0u, d.stream, d.seed_lo, d.seed_hi);
-      R n0, n1;
-      box_muller(w.x, w.y, n0, n1);
-      if (d.noise_mode == 2) n0 *= sqrt(rho / coef<R>(d, kCoRho0));    // local density in Eq. 8
-      D2 += coef<R>(d, kCoAmp + 2) * n0;
-    }
-    dst[x] = g0 - (R)(2.0 / 3.0) * IS2 * D2;
-    const R side = (R)(1.0 / 6.0) * S2 * D2;
-    dst[nx + x] = g1 + side;
-    dst[2 * nx + x] = g2 + side;
+    d1q3_site<R, DEV, SAMPLE>(d, reinterpret_cast<const R*>(ws + d.off_pop[parity]),
+                              reinterpret_cast<R*>(ws + d.off_pop[parity ^ 1]),
+                              SAMPLE ? reinterpret_cast<R*>(ws + d.off_fields) : nullptr, nx, x, step);
   }
 }
 

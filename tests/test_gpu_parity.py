@@ -321,21 +321,36 @@ def test_step_configs_and_autotune(with_mlp):
     assert _rel(sim.populations(), ref[0], ref[0] - feq) < 1e-5
 
 
-@pytest.mark.parametrize("every", [1, 3])
-def test_graph_chunks_of_several_sampling_periods_d1q3(every):
-    """A captured chunk holds whole sampling periods of at least 32 steps (32 or 33 steps
-    here); replaying it gives the populations, sums and sample count of direct steps."""
-    p = W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1, 2))
-    a, b = Sim(p, precision="fp64"), Sim(p, precision="fp64")
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("every", [0, 1, 3])
+def test_d1q3_fused_launch_matches_per_step_launches(precision, every):
+    """D1Q3 runs of steps go through one fused launch (state, fields and row transforms in
+    shared memory); with graphs off every step and every sample is launched separately.
+    Uneven replicas, one without fields; starts at odd and even steps.  The two paths do
+    the same arithmetic in the same order (they may differ in multiply-add contraction)."""
+    reps = [W.replica("D1Q3", 64, 1, W.taus_d1q3(0.8), kT=1e-4, seed=1, init_mode=1, fields=(0, 1, 2, 9)),
+            W.replica("D1Q3", 256, 1, W.taus_d1q3(0.6), kT=1e-4, u0=(0.1, 0.0), seed=2, stream=1, init_mode=1,
+                      fields=(1,)),
+            W.replica("D1Q3", 30, 1, W.taus_d1q3(0.7), kT=1e-4, seed=3, stream=2, init_mode=1),
+            W.replica("D1Q3", 4, 1, W.taus_d1q3(0.9), kT=1e-4, seed=4, stream=3, init_mode=1, fields=(0, 2))]
+    a, b = Sim(reps, precision=precision), Sim(reps, precision=precision)
     b.set_graphs(False)
     for n in (5, 100, 7):
         a.run(n, every)
         b.run(n, every)
-    assert np.array_equal(a.populations(), b.populations())
-    for x, y in ((0, 0), (0, 1), (1, 2)):
-        ca, na = a.correlator(0, x, y, with_count=True)
-        cb, nb = b.correlator(0, x, y, with_count=True)
-        assert na == nb == len(range(0, 112, every)) and np.array_equal(ca, cb)
+    assert a.step == b.step == 112
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    for r, p in enumerate(reps):
+        fa, fb = a.populations(r), b.populations(r)
+        feq = lb.uniform_state(lb.Params(**p))
+        assert _rel(fa, fb, fb - feq) < tol, r
+        fl = list(p["fields"])
+        for i, x in enumerate(fl if every else []):
+            for y in fl[i:]:
+                ca, na = a.correlator(r, x, y, with_count=True)
+                cb, nb = b.correlator(r, x, y, with_count=True)
+                assert na == nb == len(range(0, 112, every))
+                assert np.abs(ca - cb).max() < tol * max(1.0, np.abs(cb).max()), (r, x, y)
 
 
 @pytest.mark.parametrize("every", [0, 4, 5])
