@@ -4,8 +4,8 @@
 // launches per step (step, row transform, pair accumulation) they are bound by launch
 // latency, not by the GPU.  Here one block per replica keeps the populations (both
 // buffers), the sampled fields and the row transforms in shared memory for a run of
-// steps and touches global memory only for the FP64 pair sums (Eqs. 11-12) and the
-// final state.  Each step is d1q3_site (d1q3_common.cuh) and each sample the packed row
+// steps and touches global memory only for the FP64 pair sums (Eqs. 11-12), the final
+// state and the fields of the last sample.  Each step is d1q3_site (d1q3_common.cuh) and each sample the packed row
 // transform of k_fft_rows and the pair products of k_fft_cols_acc (spectra.cu) with the
 // same building blocks (fft_common.cuh) in the same order, so the results match the
 // separate launches.
@@ -51,9 +51,11 @@ k_d1q3_fused(const ReplicaDesc* __restrict__ descs, char* __restrict__ ws, uint6
   for (int i = tid; i < 3 * nx; i += nt) pop[i] = g_src[i];
   __syncthreads();
 
+  bool sampled = false;
   for (uint32_t s = 0; s < n_steps; ++s) {
     const uint64_t t = t0 + s;
     const bool sample = every != 0 && F > 0 && t % every == 0;
+    sampled = sampled || sample;
     const R* src = pop + (s & 1) * 3 * nx;
     R* dst = pop + ((s & 1) ^ 1) * 3 * nx;
     if (sample) {
@@ -147,6 +149,10 @@ k_d1q3_fused(const ReplicaDesc* __restrict__ descs, char* __restrict__ ws, uint6
   R* g_dst = reinterpret_cast<R*>(ws + d.off_pop[(int)((t0 + n_steps) & 1)]);
   const R* fin = pop + (n_steps & 1) * 3 * nx;
   for (int i = tid; i < 3 * nx; i += nt) g_dst[i] = fin[i];
+  if (sampled) {                // the fields of the last sample, as the per-step kernel leaves them
+    R* g_fld = reinterpret_cast<R*>(ws + d.off_fields);
+    for (int i = tid; i < F * nx; i += nt) g_fld[i] = fld[i];
+  }
 }
 
 cudaError_t launch_d1q3_fused(int precision, const ReplicaDesc* descs, int n_reps, char* ws, uint64_t t0,
