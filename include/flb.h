@@ -259,10 +259,14 @@ int flb_stability(const flb_replica* rep, int max_k, double* radius_out, int32_t
 int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out);
 
 /* CUDA graphs (default on): flb_run replays a captured graph for every aligned
- * chunk of sample_every steps (32 steps without sampling), which removes the
- * per-kernel launch cost on small lattices.  Results are identical either way.
- * The captured graphs are dropped when the launch configuration or the network
- * switch changes.  enable = 0 issues every kernel directly. */
+ * chunk of whole sampling periods (at least 32 steps; 32 steps without
+ * sampling), which removes the per-kernel launch cost on small lattices.  D1Q3
+ * contexts (without time correlators) instead run up to 4096 steps and their
+ * samples per launch of one fused kernel, one block per replica with its state
+ * in shared memory.  Results are identical to direct launches up to the
+ * contraction of multiply-adds.  The captured graphs are dropped when the
+ * launch configuration or the network switch changes.  enable = 0 issues every
+ * kernel of every step directly. */
 int flb_set_graphs(flb_ctx* ctx, int enable);
 
 /* Destroy the context (does not free the caller's workspace). */
