@@ -269,6 +269,16 @@ int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, int* sta
  * kernel of every step directly. */
 int flb_set_graphs(flb_ctx* ctx, int enable);
 
+/* Failure-detection check: launches on the context's stream one bounded
+ * mbarrier wait that nothing completes (the wait the network step kernels use
+ * for their MMAs and copies, here limited to limit_clocks SM clocks, 1 .. 2^32)
+ * and records its timeout in the context's status word, as a step kernel whose
+ * MMA never completed would.  The next synchronising call (flb_sync) returns
+ * FLB_ETIMEOUT; the status stays set for the life of the context.  No
+ * asynchronous operation is left in flight and the device stays usable.
+ * FLB_EINVAL for a limit out of range.  Asynchronous. */
+int flb_probe_wait_timeout(flb_ctx* ctx, uint64_t limit_clocks);
+
 /* Destroy the context (does not free the caller's workspace). */
 void flb_destroy(flb_ctx* ctx);
 

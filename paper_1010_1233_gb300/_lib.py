@@ -60,6 +60,7 @@ _SIGS = {
     "flb_get_step_config": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_set_graphs": (c_int, [c_void_p, c_int]),
+    "flb_probe_wait_timeout": (c_int, [c_void_p, c_uint64]),
     "flb_destroy": (None, [c_void_p]),
     "flb_last_error": (ctypes.c_char_p, []),
     "flb_spectra_scratch_bytes": (c_int, [c_int, c_int, c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),

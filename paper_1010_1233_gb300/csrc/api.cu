@@ -42,6 +42,7 @@ void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+void launch_wait_probe(DevStatus* status, long long limit, cudaStream_t st);   // lb_step_tc.cu
 // D1Q3 runs of steps with their sampling in one launch (lb_d1q3_fused.cu)
 size_t d1q3_fused_smem(int precision, int nx, int F);
 cudaError_t launch_d1q3_fused(int precision, const ReplicaDesc* descs, int n_reps, char* ws, uint64_t t0,
@@ -1017,6 +1018,14 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   }
   while (i < n_steps) { plain(); ++i; }
   return cuda_check(cudaGetLastError(), "flb_run launch");
+}
+
+int flb_probe_wait_timeout(flb_ctx* c, uint64_t limit_clocks) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  if (limit_clocks < 1 || limit_clocks > (1ull << 32))
+    return set_error(FLB_EINVAL, "limit_clocks must be in 1 .. 2^32");
+  launch_wait_probe(status_dev(c), (long long)limit_clocks, c->stream);
+  return cuda_check(cudaGetLastError(), "wait probe launch");
 }
 
 int flb_set_graphs(flb_ctx* c, int enable) {

@@ -159,6 +159,25 @@ static void launch_tc_vec(const StepLaunch& L, bool sample, cudaStream_t st) {
 #undef FLB_L
 }
 
+// Diagnostic: one bounded wait (the network kernels' mbar_wait, with a shorter limit) on
+// an mbarrier that nothing arrives at, reported through the status word the way a step
+// kernel reports an MMA or a copy that never completed.  No asynchronous operation is
+// involved, so giving up leaves nothing in flight.
+__global__ void k_wait_probe(DevStatus* status, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit) && atomicCAS(&status->error, 0, FLB_ETIMEOUT) == 0)
+    status->replica = -2;
+}
+
+void launch_wait_probe(DevStatus* status, long long limit, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status, limit);
+}
+
 void launch_step_tc(int vec, const StepLaunch& L, bool sample, cudaStream_t st) {
   if (vec == 4) launch_tc_vec<4>(L, sample, st);
   else if (vec == 2) launch_tc_vec<2>(L, sample, st);

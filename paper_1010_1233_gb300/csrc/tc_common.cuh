@@ -73,9 +73,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 
 // bounded wait for the mbarrier phase with the given parity; false on timeout
 // (each try_wait may suspend the thread for up to kWaitHintNs until the phase completes;
-// the clock is read every 16 polls and the wait gives up after 2^32 SM clocks, about
-// two seconds)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// the clock is read every 16 polls and the wait gives up after `limit` SM clocks, by
+// default 2^32, about two seconds)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 1LL << 32) {
   const long long t0 = clock64();
   for (;;) {
 #pragma unroll 1
@@ -85,7 +85,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
                    : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "n"(kWaitHintNs));
       if (done) return true;
     }
-    if (clock64() - t0 > (1LL << 32)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 

@@ -218,6 +218,11 @@ class Sim:
     def set_graphs(self, enable=True):
         L.check(L.lib().flb_set_graphs(self._ctx, int(bool(enable))))
 
+    def probe_wait_timeout(self, limit_clocks):
+        """Failure-detection check: one bounded device wait that nothing completes; the
+        next sync() raises FlbError(FLB_ETIMEOUT) and the status stays set."""
+        L.check(L.lib().flb_probe_wait_timeout(self._ctx, int(limit_clocks)))
+
     def autotune(self, trials=5):
         """Pick the fastest step-kernel configuration; returns (vec, grid, staged, ms per step)."""
         v, g, s, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

@@ -4,8 +4,11 @@ A linearly unstable replica (u0 = 0.5, tau = 0.505: spectral radius ~1.46 per st
 by the linear theory) blows up to non-finite values within a few hundred steps;
 the conservation check must turn that into FLB_EUNSTABLE on the host, and the
 status must stay set.  Non-finite values are ordinary IEEE arithmetic on the
-device: nothing faults or hangs.
+device: nothing faults or hangs.  A bounded wait that runs out is reported as
+FLB_ETIMEOUT.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -29,3 +32,32 @@ def test_unstable_replica_reported():
     with pytest.raises(L.FlbError) as e:                   # sticky until the context is rebuilt
         sim.sync()
     assert e.value.code == L.FLB_EUNSTABLE
+
+
+def test_bounded_wait_timeout_reported():
+    """A bounded device wait that nothing completes (the mbarrier wait of the network
+    kernels, limited to 2^26 SM clocks) gives up, the host reads FLB_ETIMEOUT, and the
+    device stays usable.  The wait is on an mbarrier no thread or copy arrives at: no
+    asynchronous operation is in flight, nothing faults or hangs."""
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8), kT=1e-4, seed=1)
+    sim = Sim(p, precision="fp32")
+    sim.sync()
+    with pytest.raises(L.FlbError) as e:
+        sim.probe_wait_timeout(0)
+    assert e.value.code == L.FLB_EINVAL
+    t0 = time.perf_counter()
+    sim.probe_wait_timeout(1 << 26)
+    with pytest.raises(L.FlbError) as e:
+        sim.sync()
+    assert e.value.code == L.FLB_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(L.FlbError) as e:                   # sticky for the life of the context
+        sim.sync()
+    assert e.value.code == L.FLB_ETIMEOUT
+    sim.close()
+    fresh = Sim(p, precision="fp32")
+    fresh.run(3)
+    fresh.sync()
+    assert np.all(np.isfinite(fresh.populations()))
+    fresh.close()
+
