@@ -136,6 +136,15 @@ def bind_local_cpus(device):
     return None
 
 
+def host_buffer_count(nb, ranks_here, phys):
+    """Pinned host buffers per rank for the end-to-end run (every rank of the node holds
+    its buffers at once): two when they fit in 60 % of the physical memory, one shared
+    buffer when one does, none otherwise.  phys = 0 (unknown): two."""
+    if not phys or 2 * nb * ranks_here <= 0.6 * phys:
+        return 2
+    return 1 if nb * ranks_here <= 0.6 * phys else 0
+
+
 def end_to_end(sim, K, V, world, local, barrier):
     """The same K steps through the public API with host buffers: load the state (a
     checkpoint: populations and correlator sums) from pinned host memory, run, save the
@@ -151,16 +160,12 @@ def end_to_end(sim, K, V, world, local, barrier):
     size = ctypes.c_size_t()
     L.check(lib.flb_save(sim._ctx, None, ctypes.byref(size)))
     nb = int(size.value)
-    # host memory: every rank of this node holds its buffers at once; two buffers when
-    # they fit in 60 % of the physical memory, one shared buffer otherwise, none below that
     try:
         phys = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
     except (ValueError, OSError):
         phys = 0
     ranks_here = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
-    n_buf = 2
-    if phys and 2 * nb * ranks_here > 0.6 * phys:
-        n_buf = 1 if nb * ranks_here <= 0.6 * phys else 0
+    n_buf = host_buffer_count(nb, ranks_here, phys)
     if n_buf == 0:
         return {"value": None, "unit": "MLUPS", "skipped": "state of %.1f GB per rank x %d ranks exceeds the host's "
                 "memory" % (nb / 1e9, ranks_here)}
