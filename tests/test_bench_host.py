@@ -21,3 +21,17 @@ def test_host_buffer_count():
     assert b.host_buffer_count(19 * GB, 16, 480 * GB) == 0         # 304 GB for one buffer each
     assert b.host_buffer_count(11 * GB, 3, 100 * GB) == 1          # 66 GB > 60 % of 100, 33 GB fits
     assert b.host_buffer_count(5 * GB, 6, 100 * GB) == 2           # exactly 60 % fits
+
+
+def test_clock_summary_median_and_reasons():
+    b = _bench()
+    c = b.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2040, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line",
+               "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = []
+    assert c.summary() is None
