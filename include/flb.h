@@ -189,9 +189,8 @@ int flb_get_step(flb_ctx* ctx, uint64_t* step_out);
  * a = 3..8, o = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with W1 32x3, W2 32x32,
  * W3 6x32 (row-major, bfloat16 bit patterns, 96 + 1024 + 192 values in that
  * order) and biases b1(32) b2(32) b3(6) given in FP32.  Evaluated on the tensor
- * cores (tcgen05) with bfloat16 operands and FP32 accumulation: the inputs, the
- * biases (weights of a constant-1 input) and the hidden activations are rounded
- * to bfloat16.  FP32 D2Q9 path only.  enable = 0 switches it off (s = 1,
+ * cores (flb_set_network_engine) with bfloat16 operands and FP32 accumulation:
+ * the inputs, the biases and the hidden activations are rounded to bfloat16.  FP32 D2Q9 path only.  enable = 0 switches it off (s = 1,
  * bit-identical to the plain method).  Copies the weights. */
 int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int enable);
 
@@ -238,6 +237,20 @@ int flb_get_time_correlator(flb_ctx* ctx, int replica, int field_a, int field_b,
 int flb_set_step_config(flb_ctx* ctx, int vec, int grid_blocks, int staged);
 int flb_get_step_config(flb_ctx* ctx, int* vec, int* grid_blocks, int* staged);
 
+/* How the direct D2Q9 step kernels (staged = 0) evaluate the noise-scale
+ * network (flb_set_mlp); the arithmetic is the same (bfloat16 operands, FP32
+ * accumulation), results agree to the rounding of the accumulation order.
+ * FLB_NET_WARP (default): each warp runs the three layers for 64 sites with
+ * warp-level tensor-core MMAs (m16n8k16), all operands in registers, no
+ * barrier between warps.  FLB_NET_TCGEN05: each warpgroup runs them for 128
+ * sites per tile with tcgen05 MMAs, operand A and the accumulators in tensor
+ * memory, warpgroup barriers between the layers.  The staged kernel always
+ * uses the tcgen05 form.  flb_autotune tries both.  Synchronises. */
+#define FLB_NET_WARP    0
+#define FLB_NET_TCGEN05 1
+int flb_set_network_engine(flb_ctx* ctx, int engine);
+int flb_get_network_engine(flb_ctx* ctx, int* engine);
+
 /* Linear stability of one replica's parameters, on the host (no GPU, no context):
  * the largest modulus of the eigenvalues of the one-step operator A_k = P_k J of the
  * noise-free dynamics linearised about f^0(rho0, u0) (P_k the pull-streaming phases of
@@ -252,9 +265,9 @@ int flb_stability(const flb_replica* rep, int max_k, double* radius_out, int32_t
 
 /* Autotuner: times `trials` launches of the step kernel (current network
  * setting, no sampling) for every valid configuration: direct kernels with
- * every vec and grid size in {2,4,8,16} x SMs and all-blocks, and the staged
- * kernel with every vec; keeps the fastest and reports it (ms_out: time per
- * launch).  The timing launches recompute the next step from the current state
+ * every vec and grid size in {2,4,8,16} x SMs and all-blocks (with the network
+ * on: with each network engine), and the staged kernel with every vec; keeps
+ * the fastest, engine included, and reports it (ms_out: time per launch).  The timing launches recompute the next step from the current state
  * without advancing it, so the simulation is unchanged.  Synchronises. */
 int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out);
 

@@ -14,6 +14,7 @@ FLB_OK, FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_EUNSTABLE, FLB_ETIMEOUT, FLB_ESTA
 FLB_D1Q3, FLB_D2Q9, FLB_D3Q15, FLB_D3Q19 = 1, 2, 3, 4
 FLB_FP64, FLB_FP32_DEV = 0, 1
 FIELD_UX, FIELD_UY = 9, 10
+FLB_NET_WARP, FLB_NET_TCGEN05 = 0, 1
 
 
 class FlbError(RuntimeError):
@@ -58,6 +59,8 @@ _SIGS = {
     "flb_load": (c_int, [c_void_p, c_void_p, c_size_t]),
     "flb_set_step_config": (c_int, [c_void_p, c_int, c_int, c_int]),
     "flb_get_step_config": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "flb_set_network_engine": (c_int, [c_void_p, c_int]),
+    "flb_get_network_engine": (c_int, [c_void_p, POINTER(c_int)]),
     "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_set_graphs": (c_int, [c_void_p, c_int]),
     "flb_probe_wait_timeout": (c_int, [c_void_p, c_uint64]),

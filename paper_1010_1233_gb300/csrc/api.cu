@@ -291,6 +291,10 @@ static void fill_desc(int precision, const flb_replica& p, ReplicaDesc& d) {
   d.nz = d3 ? p.nz : 1;
   d.q = lattice_q(p.lattice);
   d.seed_lo = (uint32_t)p.seed; d.seed_hi = (uint32_t)(p.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    d.rkey[2 * r] = d.seed_lo + (uint32_t)r * 0x9E3779B9u;
+    d.rkey[2 * r + 1] = d.seed_hi + (uint32_t)r * 0xBB67AE85u;
+  }
   d.stream = p.stream; d.noise_mask = p.noise_mask; d.field_mask = p.field_mask;
   d.rho0 = p.rho0; d.kT = p.kT; d.mu = 3.0 * p.kT; d.u0x = p.u0[0]; d.u0y = (d2 || d3) ? p.u0[1] : 0.0;
   d.u0z = d3 ? p.u0[2] : 0.0;
@@ -536,6 +540,7 @@ struct flb_ctx {
   int sms = 1;
   int step_grid = 0;          // 0: min(virtual blocks, 16 x SMs)
   bool mlp_on = false;
+  int net_engine = FLB_NET_WARP;   // network of the direct D2Q9 kernels
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
   struct Graph { uint32_t len, every; cudaGraphExec_t exec; };
@@ -917,6 +922,7 @@ static StepLaunch step_launch(flb_ctx* c) {
   S.status = status_dev(c);
   S.sms = c->sms;
   S.desc0 = &L.desc[0];
+  S.net_engine = c->net_engine;
   for (const ReplicaDesc& d : L.desc) S.noise_general = S.noise_general || d.noise_mode != 0;
   return S;
 }
@@ -1360,6 +1366,24 @@ int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks, int* staged) {
   return FLB_OK;
 }
 
+int flb_set_network_engine(flb_ctx* c, int engine) {
+  if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
+  if (engine != FLB_NET_WARP && engine != FLB_NET_TCGEN05)
+    return set_error(FLB_EINVAL, "engine must be FLB_NET_WARP or FLB_NET_TCGEN05");
+  if (engine == c->net_engine) return FLB_OK;
+  int rc = cuda_check(cudaStreamSynchronize(c->stream), "network engine");
+  if (rc) return rc;
+  drop_graphs(c);
+  c->net_engine = engine;
+  return FLB_OK;
+}
+
+int flb_get_network_engine(flb_ctx* c, int* engine) {
+  if (!c || !engine) return set_error(FLB_EINVAL, "NULL argument");
+  *engine = c->net_engine;
+  return FLB_OK;
+}
+
 int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* staged_out, double* ms_out) {
   NvtxRange range("flb_autotune");
   if (!c) return set_error(FLB_EINVAL, "ctx is NULL");
@@ -1370,10 +1394,14 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
   rc = cuda_check(cudaEventCreate(&e1), "event");
   if (rc) { cudaEventDestroy(e0); return rc; }
   const int vecs[3] = {1, 2, 4};
-  int best_vec = c->L.vec, best_grid = c->step_grid, best_staged = c->L.staged;
+  int best_vec = c->L.vec, best_grid = c->step_grid, best_staged = c->L.staged, best_engine = c->net_engine;
   float best = 1e30f;
-  for (int cfg = 0; cfg < 6 && !rc; ++cfg) {
-    const int vec = vecs[cfg % 3], staged = cfg / 3;
+  // direct kernels with either network engine (when the network is on), then the staged kernel
+  const bool two_engines = c->mlp_on && c->lattice == FLB_D2Q9;
+  for (int cfg = 0; cfg < 9 && !rc; ++cfg) {
+    const int vec = vecs[cfg % 3], staged = cfg / 3 == 2 ? 1 : 0;
+    const int engine = cfg / 3 == 1 ? FLB_NET_TCGEN05 : FLB_NET_WARP;
+    if (engine == FLB_NET_TCGEN05 && !two_engines) continue;
     if (vec > 1 && (c->precision != FLB_FP32_DEV || c->lattice == FLB_D1Q3)) continue;
     if (staged && !staged_ok(c)) continue;
     bool ok = true;
@@ -1402,6 +1430,7 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
       S.status = status_dev(c);
       S.sms = c->sms;
       S.desc0 = &c->L.desc[0];
+      S.net_engine = engine;
       for (const ReplicaDesc& d : c->L.desc) S.noise_general = S.noise_general || d.noise_mode != 0;
       auto launch = [&] { launch_step_any(c, vec, staged, S, false, c->stream); };
       launch();
@@ -1413,7 +1442,7 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= trials;
-      if (ms < best) { best = ms; best_vec = vec; best_grid = S.grid; best_staged = staged; }
+      if (ms < best) { best = ms; best_vec = vec; best_grid = S.grid; best_staged = staged; best_engine = engine; }
     }
   }
   cudaEventDestroy(e0);
@@ -1421,6 +1450,10 @@ int flb_autotune(flb_ctx* c, int trials, int* vec_out, int* grid_out, int* stage
   if (rc) return rc;
   rc = flb_set_step_config(c, best_vec, best_grid, best_staged);
   if (rc) return rc;
+  if (two_engines) {
+    rc = flb_set_network_engine(c, best_engine);
+    if (rc) return rc;
+  }
   if (vec_out) *vec_out = best_vec;
   if (grid_out) *grid_out = best_grid;
   if (staged_out) *staged_out = best_staged;

@@ -39,6 +39,7 @@ struct ReplicaDesc {
   int64_t n_units;              // units_per_row * ny * nz
   int64_t block_begin;          // first virtual block of this replica in the step launch
   uint32_t seed_lo, seed_hi, stream, noise_mask;
+  uint32_t rkey[20];            // Philox round keys (k0 + r W0, k1 + r W1), r = 0..9, of the key (seed_lo, seed_hi)
   int32_t noise_mode;           // 0: independent noise (Eq. 8); 1: correlated (root in kCoNoiseR)
   uint32_t field_mask, n_fields;
   int32_t field_id[kMaxFields];     // slot -> field id
@@ -104,12 +105,26 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1
   return make_uint4(c0, c1, c2, c3);
 }
 
-// Box-Muller on a word pair.  FP64: u = (w + 1/2) 2^-32 (exact).  FP32: u = RN(w) 2^-32 + 2^-33,
-// which keeps a relative error <= 2^-24 for every u (small u included, where the log is
-// sensitive); u can round up to 1 only where the normal's radius is ~1e-4 anyway.  The FP32
-// log is the hardware one (__logf: absolute error <= 2^-21.4 on [1/2, 1], 3 ulp below), so
-// r = sqrt(-2 ln u) is within a few ulp for typical u and within ~7e-4 absolute in the worst
-// case (u within 1e-7 of 1, where r itself is below ~5e-4).
+// The same with the round keys precomputed (rk[2r], rk[2r + 1] = the keys of round r), so
+// that a kernel reading them from its constant bank spends no instruction on the schedule.
+__host__ __device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                           const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, rk[2 * r], rk[2 * r + 1]);
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// The hardware approximations (single MUFU operations, inputs flushed to zero below the
+// normal range, which these inputs never reach): log2 (absolute error <= 2^-22 on
+// [1/2, 2]), reciprocal square root (relative error <= 2^-22.9), sine and cosine (absolute
+// error <= 2^-20.9 on [-pi, pi]).
+__device__ __forceinline__ float lg2_approx(float x) { float y; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float rsqrt_approx(float x) { float y; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float sin_approx(float x) { float y; asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+__device__ __forceinline__ float cos_approx(float x) { float y; asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x)); return y; }
+
+// Box-Muller on a word pair: N0 = r cos(2 pi ub), N1 = r sin(2 pi ub), r = sqrt(-2 ln ua).
+// FP64: u = (w + 1/2) 2^-32 (exact).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
   const double ua = ((double)wa + 0.5) * 0x1p-32;
   const double ub = ((double)wb + 0.5) * 0x1p-32;
@@ -119,17 +134,24 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0,
   n0 = r * c; n1 = r * s;
 }
 
+// FP32: ua = RN(wa) 2^-32 + 2^-33 (relative error <= 2^-24 for every ua, small ua
+// included, where the log is sensitive; ua rounds up to 1 only where r is ~1e-4 anyway);
+// 2 ln ua = log2(ua) * 2 ln 2 with the hardware log2, so r is within a few ulp for typical
+// ua and within ~7e-4 absolute in the worst case (ua within 1e-7 of 1, r below ~5e-4).
+// -r = y / sqrt(-y), y = 2 ln ua <= 0 (clamped below 0).  The angle theta =
+// 2 pi (ub - 1/2) in [-pi, pi], the range of the hardware sine and cosine, is one
+// multiply-add of RN(wb); (cos, sin)(2 pi ub) = -(cos, sin)(theta), and the two signs
+// cancel: N = (-r) (cos, sin)(theta).
+constexpr float kBmLn4 = 1.38629436111989061883f;                  // 2 ln 2
+constexpr float kBmAngScale = (float)(6.283185307179586476925 / 4294967296.0);
+constexpr float kBmAngShift = (float)(6.283185307179586476925 * (1.0 / 8589934592.0 - 0.5));
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
   const float ua = fmaf(__uint2float_rn(wa), 0x1p-32f, 0x1p-33f);
-  const float ub = fmaf(__uint2float_rn(wb), 0x1p-32f, 0x1p-33f);
-  // r = sqrt(-2 ln ua); ua <= 1 so x >= 0, and x = 0 only when ua rounds to 1
-  const float x = fmaxf(-2.0f * __logf(ua), 1e-30f);
-  const float r = x * rsqrtf(x);
-  // (cos, sin)(2 pi ub) = -(cos, sin)(theta) with theta = 2 pi (ub - 1/2) in [-pi, pi],
-  // the range where the hardware sine and cosine are accurate to ~2^-21 absolute
-  float s, c;
-  __sincosf(6.283185307179586f * (ub - 0.5f), &s, &c);
-  n0 = -r * c; n1 = -r * s;
+  const float y = fminf(lg2_approx(ua) * kBmLn4, -1e-30f);
+  const float nr = y * rsqrt_approx(-y);
+  const float th = fmaf(__uint2float_rn(wb), kBmAngScale, kBmAngShift);
+  n0 = nr * cos_approx(th);
+  n1 = nr * sin_approx(th);
 }
 
 template <typename T> struct cplx { T x, y; };
@@ -163,6 +185,7 @@ struct StepLaunch {
   int sms = 0;                          // multiprocessors of the device
   const ReplicaDesc* desc0 = nullptr;   // host copy of descs[0] (kernel argument of one-replica launches)
   bool noise_general = false;           // some replica uses noise mode 1 or 2
+  int net_engine = FLB_NET_WARP;        // direct D2Q9 kernels with the network: FLB_NET_WARP or FLB_NET_TCGEN05
   // kernel flavour: 0 = one replica, noise mode 0; 1 = one replica, any mode; 2 = batched
   int flavor() const { return n_reps > 1 ? 2 : (noise_general ? 1 : 0); }
 };

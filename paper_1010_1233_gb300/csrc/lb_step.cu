@@ -234,11 +234,16 @@ __global__ void k_philox(const uint32_t* site, int n, uint32_t step, uint32_t ca
 // Host launchers (called from api.cu).
 
 void launch_step_tc(int vec, const StepLaunch& L, bool sample, cudaStream_t st);
+void launch_step_wn(int vec, const StepLaunch& L, bool sample, cudaStream_t st);
 
 template <typename R, bool DEV, int VEC>
 static void launch_d2q9_vec(const StepLaunch& L, bool sample, bool mlp, cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
-    if (mlp) { launch_step_tc(VEC, L, sample, st); return; }
+    if (mlp) {
+      if (L.net_engine == FLB_NET_TCGEN05) launch_step_tc(VEC, L, sample, st);
+      else launch_step_wn(VEC, L, sample, st);
+      return;
+    }
   }
 #define FLB_L(S, F) k_step_d2q9<R, DEV, VEC, S, F><<<L.grid, kStepThreads, 0, st>>>( \
       L.descs, *L.desc0, L.vb_begin, L.n_reps, L.n_vblocks, L.ws, L.parity, L.step, L.step_dev)

@@ -278,6 +278,7 @@ k_step_d2q9_bulk(const ReplicaDesc* __restrict__ descs, const __grid_constant__ 
   }
   if (!(ok && (!NET || net.ok)) && atomicCAS(&status->error, 0, FLB_ETIMEOUT) == 0) status->replica = -1;
   if constexpr (NET) {
+    net.drain();
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");

@@ -137,6 +137,7 @@ k_step_d2q9_tc(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Re
     store_d2q9<R, VEC, SAMPLE>(d, ws, dst, plane, uc, f, fld);
   }
   if (!net.ok && atomicCAS(&status->error, 0, FLB_ETIMEOUT) == 0) status->replica = -1;
+  net.drain();
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");

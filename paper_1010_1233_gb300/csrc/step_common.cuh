@@ -166,16 +166,86 @@ __device__ __forceinline__ void pull_d2q9(const R* __restrict__ src, int64_t pla
   pull_finish<R, VEC>(raw, u, f);
 }
 
-// Density (as the sum of the stored values) and velocity of one site (Sec. 2).  In
-// deviation storage sum_i w_i rho0 = rho0 and sum_i w_i rho0 v_i = 0.
+// Explicitly rounded arithmetic on one "lane type": a float, a double, or a float2 that
+// carries two sites in the packed FP32 instructions of sm_100-class GPUs (fma.rn.f32x2,
+// add, mul).  The site update below is written once on these operations, so no
+// multiply-add is left for the compiler to contract: every kernel, vector width and
+// launch flavour computes bit-identical results, one site or two at a time.
+template <typename T> struct Lane;
+template <> struct Lane<float> {
+  using S = float;
+  static __device__ __forceinline__ float splat(float c) { return c; }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.f, a); }   // hardware reciprocal, 2 ulp
+  static __device__ __forceinline__ float sqrt_ratio(float a, float b) { return sqrtf(a / b); }
+};
+template <> struct Lane<double> {
+  using S = double;
+  static __device__ __forceinline__ double splat(double c) { return c; }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ double sqrt_ratio(double a, double b) { return sqrt(a / b); }
+};
+// Packed operations as inline PTX with the rounding mode spelled out (.rn): an operation
+// with an explicit rounding mode is never fused with another, so a product that feeds a
+// sum stays rounded on its own, as in the scalar operations above.
+__device__ __forceinline__ uint64_t f2bits(float2 a) {
+  return (uint64_t)__float_as_uint(a.x) | ((uint64_t)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ float2 bitsf2(uint64_t v) {
+  return make_float2(__uint_as_float((uint32_t)v), __uint_as_float((uint32_t)(v >> 32)));
+}
+template <> struct Lane<float2> {
+  using S = float;
+  static __device__ __forceinline__ float2 splat(float c) { return make_float2(c, c); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bitsf2(d);
+  }
+  // a - b = fma(b, -1, a): one rounding, the same value as a scalar subtraction
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return fma(b, make_float2(-1.f, -1.f), a); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)));
+    return bitsf2(d);
+  }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2bits(a)), "l"(f2bits(b)), "l"(f2bits(c)));
+    return bitsf2(d);
+  }
+  static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+  static __device__ __forceinline__ float2 sqrt_ratio(float2 a, float2 b) {
+    return make_float2(sqrtf(a.x / b.x), sqrtf(a.y / b.y));
+  }
+};
+
+// Density (as the sum of the stored values) and velocity (Sec. 2).  In deviation storage
+// sum_i w_i rho0 = rho0 and sum_i w_i rho0 v_i = 0.
+template <typename T, bool DEV>
+__device__ __forceinline__ void macro_site(const T (&g)[9], typename Lane<T>::S rho0, T& sum, T& ux, T& uy) {
+  using A = Lane<T>;
+  const T ax = A::add(g[1], g[3]), ay = A::add(g[2], g[4]);
+  const T dg = A::add(A::add(g[5], g[7]), A::add(g[6], g[8]));
+  sum = A::add(A::add(A::add(g[0], ax), ay), dg);
+  const T d57 = A::sub(g[5], g[7]), d86 = A::sub(g[8], g[6]);
+  const T jx = A::add(A::sub(g[1], g[3]), A::add(d57, d86));
+  const T jy = A::add(A::sub(g[2], g[4]), A::sub(d57, d86));
+  const T irho = A::rcp(DEV ? A::add(A::splat(rho0), sum) : sum);
+  ux = A::mul(jx, irho);
+  uy = A::mul(jy, irho);
+}
+
 template <typename R, bool DEV>
 __device__ __forceinline__ void macro_d2q9(const R (&g)[9], R rho0, R& sum, R& ux, R& uy) {
-  sum = ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-  const R jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-  const R jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
-  const R irho = (R)1 / (DEV ? rho0 + sum : sum);
-  ux = jx * irho;
-  uy = jy * irho;
+  macro_site<R, DEV>(g, rho0, sum, ux, uy);
 }
 
 // The six unit normals of a site (Philox counter: site, step, call 0/1, stream), in two
@@ -183,8 +253,8 @@ __device__ __forceinline__ void macro_d2q9(const R (&g)[9], R rho0, R& sum, R& u
 // then the Box-Muller transform of three word pairs.
 __device__ __forceinline__ void philox_words_d2q9(const ReplicaDesc& d, uint32_t site, uint32_t step, uint4& w0,
                                                   uint4& w1) {
-  w0 = philox4x32_10(site, step, 0u, d.stream, d.seed_lo, d.seed_hi);
-  w1 = philox4x32_10(site, step, 1u, d.stream, d.seed_lo, d.seed_hi);
+  w0 = philox4x32_10_rk(site, step, 0u, d.stream, d.rkey);
+  w1 = philox4x32_10_rk(site, step, 1u, d.stream, d.rkey);
 }
 
 template <typename R>
@@ -201,102 +271,128 @@ __device__ __forceinline__ void normals_d2q9(const ReplicaDesc& d, uint32_t site
   normals_from_words<R>(w0, w1, n);
 }
 
-// Collision of one site (Eqs. 5, 8, 10), in two parts.  collide_relax: the non-conserved
-// moments M^3..M^8 of Eq. 9, relaxed towards the equilibrium moments of Eq. 10 at rates
-// 1/tau^a: D[a - 3] = Delta M^a (and the sampled fields of the pre-collision state when
-// SAMPLE).  collide_apply: add xi^a = s_a amp_a N^a (noise mode 2: amp_a with the local
-// density rho in place of rho0; mode 1, correlated noise: xi^a = s_a sum_c R_ac N^c) and
-// the back transform
-// sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a, in place.
-template <typename R, bool DEV, bool SAMPLE>
-__device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)[9], R sum, R ux, R uy, R (&D)[6],
-                                              R (&fld)[kMaxFields]) {
-  const R S3 = (R)1.7320508075688772935, S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
-  const R g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4], g5 = g[5], g6 = g[6], g7 = g[7], g8 = g[8];
-  const R rho = DEV ? coef<R>(d, kCoRho0) + sum : sum;
+// Collision (Eqs. 5, 8, 10), in two parts.  relax_site: the non-conserved moments
+// M^3..M^8 of Eq. 9, relaxed towards the equilibrium moments of Eq. 10 at rates 1/tau^a:
+// D[a - 3] = Delta M^a (and the sampled fields of the pre-collision state when SAMPLE).
+// apply_site: add xi^a = s_a amp_a N^a (noise mode 2: amp_a with the local density rho in
+// place of rho0; mode 1, correlated noise: xi^a = s_a sum_c R_ac N^c) and the back
+// transform sum_a n_i^a (Delta M^a + xi^a) with n_i^a = w_i m_i^a, in place.
+//
+// No rounded product feeds a sum here unless the product is exact (a power of two) or
+// the sum is written as a fused multiply-add: a code generator that fuses a packed
+// multiply into the following packed add would otherwise round differently from the
+// scalar operations.
+template <typename T, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void relax_site(const ReplicaDesc& d, const T (&g)[9], T sum, T ux, T uy, T (&D)[6],
+                                           T (&fld)[kMaxFields]) {
+  using A = Lane<T>;
+  using S = typename Lane<T>::S;
+  const S S3 = (S)1.7320508075688772935, S32 = (S)1.2247448713915890491, S6 = (S)2.4494897427831780982;
+  const T rho = DEV ? A::add(A::splat(coef<S>(d, kCoRho0)), sum) : sum;
   // non-conserved moments of Eq. 9 (identical for f and f - w rho0)
-  const R ax = g1 + g3, ay = g2 + g4, dg = (g5 + g7) + (g6 + g8);
-  const R M3 = (R)1.5 * (ax - ay);
-  const R M4 = (R)3 * ((g5 + g7) - (g6 + g8));
-  const R M5 = (R)0.5 * (ax + ay) + (R)2 * dg - g0;
-  const R M6 = S32 * (g3 - g1) + S6 * ((g5 - g7) + (g8 - g6));
-  const R M7 = S32 * (g4 - g2) + S6 * ((g5 - g7) + (g6 - g8));
-  const R M8 = (R)0.5 * g0 - (ax + ay) + (R)2 * dg;
-  // equilibrium moments, Eq. 10
-  const R ux2 = ux * ux, uy2 = uy * uy;
-  const R E3 = (R)1.5 * rho * (ux2 - uy2);
-  const R E4 = (R)3 * rho * ux * uy;
-  const R E5 = (R)1.5 * rho * (ux2 + uy2);
+  const T ax = A::add(g[1], g[3]), ay = A::add(g[2], g[4]);
+  const T s57 = A::add(g[5], g[7]), s68 = A::add(g[6], g[8]);
+  const T dg = A::add(s57, s68), axy = A::add(ax, ay), dg2 = A::mul(A::splat((S)2), dg);
+  const T d57 = A::sub(g[5], g[7]), d86 = A::sub(g[8], g[6]);
+  const T axmy = A::sub(ax, ay), s57m = A::sub(s57, s68);
+  //   M3 = 3/2 axmy, M4 = 3 s57m; M5 and M8 with the exact 2 dg
+  const T M5 = A::fma(A::splat((S)0.5), axy, A::sub(dg2, g[0]));
+  const T M6 = A::fma(A::splat(S6), A::add(d57, d86), A::mul(A::splat(S32), A::sub(g[3], g[1])));
+  const T M7 = A::fma(A::splat(S6), A::sub(d57, d86), A::mul(A::splat(S32), A::sub(g[4], g[2])));
+  const T M8 = A::fma(A::splat((S)0.5), g[0], A::sub(dg2, axy));
+  // equilibrium moments of Eq. 10 minus the moments: E3 - M3, E4 - M4, E5 - M5
+  const T nuy = A::mul(uy, A::splat((S)-1));
+  const T u2d = A::fma(ux, ux, A::mul(uy, nuy));           // u_x^2 - u_y^2
+  const T u2s = A::fma(ux, ux, A::mul(uy, uy));            // u_x^2 + u_y^2
+  const T r15 = A::mul(A::splat((S)1.5), rho);
+  const T t3 = A::fma(r15, u2d, A::mul(A::splat((S)-1.5), axmy));
+  const T t4 = A::fma(A::mul(A::splat((S)3), rho), A::mul(ux, uy), A::mul(A::splat((S)-3), s57m));
+  const T nM5 = A::fma(A::splat((S)-0.5), axy, A::sub(g[0], dg2));   // -M5 exactly
+  const T t5 = A::fma(r15, u2s, nM5);
   if constexpr (SAMPLE) {
-    const R jx = ux * rho, jy = uy * rho;
-    const R mom[9] = {sum, S3 * jx, S3 * jy, M3, M4, M5, M6, M7, M8};
-#pragma unroll
-    for (int a = 0; a < 9; ++a) fld[a] = mom[a] - coef<R>(d, kCoMref + a);
-    fld[9] = ux - coef<R>(d, kCoU0x);
-    fld[10] = uy - coef<R>(d, kCoU0y);
+    const T jx = A::add(A::sub(g[1], g[3]), A::add(d57, d86));
+    const T jy = A::add(A::sub(g[2], g[4]), A::sub(d57, d86));
+    const T irho = A::rcp(rho);
+    fld[0] = A::sub(sum, A::splat(coef<S>(d, kCoMref + 0)));
+    fld[1] = A::fma(A::splat(S3), jx, A::splat(-coef<S>(d, kCoMref + 1)));
+    fld[2] = A::fma(A::splat(S3), jy, A::splat(-coef<S>(d, kCoMref + 2)));
+    fld[3] = A::fma(A::splat((S)1.5), axmy, A::splat(-coef<S>(d, kCoMref + 3)));
+    fld[4] = A::fma(A::splat((S)3), s57m, A::splat(-coef<S>(d, kCoMref + 4)));
+    fld[5] = A::sub(M5, A::splat(coef<S>(d, kCoMref + 5)));
+    fld[6] = A::sub(M6, A::splat(coef<S>(d, kCoMref + 6)));
+    fld[7] = A::sub(M7, A::splat(coef<S>(d, kCoMref + 7)));
+    fld[8] = A::sub(M8, A::splat(coef<S>(d, kCoMref + 8)));
+    fld[9] = A::fma(jx, irho, A::splat(-coef<S>(d, kCoU0x)));      // u - u0
+    fld[10] = A::fma(jy, irho, A::splat(-coef<S>(d, kCoU0y)));
   }
   // relaxation (Eq. 5)
-  D[0] = (E3 - M3) * coef<R>(d, kCoInvTau + 3);
-  D[1] = (E4 - M4) * coef<R>(d, kCoInvTau + 4);
-  D[2] = (E5 - M5) * coef<R>(d, kCoInvTau + 5);
-  D[3] = -M6 * coef<R>(d, kCoInvTau + 6);
-  D[4] = -M7 * coef<R>(d, kCoInvTau + 7);
-  D[5] = -M8 * coef<R>(d, kCoInvTau + 8);
+  D[0] = A::mul(t3, A::splat(coef<S>(d, kCoInvTau + 3)));
+  D[1] = A::mul(t4, A::splat(coef<S>(d, kCoInvTau + 4)));
+  D[2] = A::mul(t5, A::splat(coef<S>(d, kCoInvTau + 5)));
+  D[3] = A::mul(M6, A::splat(-coef<S>(d, kCoInvTau + 6)));
+  D[4] = A::mul(M7, A::splat(-coef<S>(d, kCoInvTau + 7)));
+  D[5] = A::mul(M8, A::splat(-coef<S>(d, kCoInvTau + 8)));
 }
 
 // GEN: the replica may use noise modes 1 and 2 (branch on d.noise_mode); without it only
 // mode 0 is compiled (the common case keeps its registers and instruction count).
+template <typename T, bool DEV, bool GEN>
+__device__ __forceinline__ void apply_site(const ReplicaDesc& d, T (&g)[9], T sum, bool noisy, const T (&n)[6],
+                                           const T (&sc)[6], const T (&Drel)[6]) {
+  using A = Lane<T>;
+  using S = typename Lane<T>::S;
+  const S S32 = (S)1.2247448713915890491, S6 = (S)2.4494897427831780982;
+  T D[6] = {Drel[0], Drel[1], Drel[2], Drel[3], Drel[4], Drel[5]};
+  if (GEN && noisy && d.noise_mode == 1) {              // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      T z = A::mul(A::splat(coef<S>(d, kCoNoiseR + 6 * c)), n[0]);
+#pragma unroll
+      for (int e = 1; e < 6; ++e) z = A::fma(A::splat(coef<S>(d, kCoNoiseR + 6 * c + e)), n[e], z);
+      D[c] = A::fma(sc[c], z, D[c]);
+    }
+  } else if (noisy) {                            // Eq. 8, scaled per moment by s
+    T fac = A::splat((S)1);
+    if (GEN && d.noise_mode == 2) {              // local density in Eq. 8: amp * sqrt(rho / rho0)
+      const T rho0 = A::splat(coef<S>(d, kCoRho0));
+      fac = A::sqrt_ratio(DEV ? A::add(rho0, sum) : sum, rho0);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      T s = A::mul(sc[c], A::splat(coef<S>(d, kCoAmp + 3 + c)));
+      if (GEN && d.noise_mode == 2) s = A::mul(s, fac);
+      D[c] = A::fma(s, n[c], D[c]);
+    }
+  }
+  // back transform of the moment change, n_i^a = w_i m_i^a (D[a - 3] = Delta M^a + xi^a)
+  const T w1 = A::splat((S)1 / (S)9), w5 = A::splat((S)1 / (S)36);
+  const T ax5 = A::sub(A::mul(A::splat((S)0.5), D[2]), D[5]);   // common to the axis populations
+  const T Ap = A::fma(A::splat((S)1.5), D[0], ax5), Bm = A::fma(A::splat((S)-1.5), D[0], ax5);
+  const T dcom = A::mul(A::splat((S)2), A::add(D[2], D[5]));      // common to the diagonal populations
+  const T P = A::fma(A::splat((S)3), D[1], dcom), Q = A::fma(A::splat((S)-3), D[1], dcom);
+  const T Rp = A::fma(A::splat(S6), D[3], A::mul(A::splat(S6), D[4]));      // q6 + q7
+  const T Rm = A::fma(A::splat(S6), D[3], A::mul(A::splat(-S6), D[4]));     // q6 - q7
+  g[0] = A::fma(A::splat((S)(4.0 / 9.0)), A::sub(A::mul(A::splat((S)0.5), D[5]), D[2]), g[0]);
+  g[1] = A::fma(w1, A::fma(A::splat(-S32), D[3], Ap), g[1]);
+  g[3] = A::fma(w1, A::fma(A::splat(S32), D[3], Ap), g[3]);
+  g[2] = A::fma(w1, A::fma(A::splat(-S32), D[4], Bm), g[2]);
+  g[4] = A::fma(w1, A::fma(A::splat(S32), D[4], Bm), g[4]);
+  g[5] = A::fma(w5, A::add(P, Rp), g[5]);
+  g[6] = A::fma(w5, A::sub(Q, Rm), g[6]);
+  g[7] = A::fma(w5, A::sub(P, Rp), g[7]);
+  g[8] = A::fma(w5, A::add(Q, Rm), g[8]);
+}
+
+template <typename R, bool DEV, bool SAMPLE>
+__device__ __forceinline__ void collide_relax(const ReplicaDesc& d, const R (&g)[9], R sum, R ux, R uy, R (&D)[6],
+                                              R (&fld)[kMaxFields]) {
+  relax_site<R, DEV, SAMPLE>(d, g, sum, ux, uy, D, fld);
+}
+
 template <typename R, bool DEV, bool GEN>
 __device__ __forceinline__ void collide_apply(const ReplicaDesc& d, R (&g)[9], R sum, bool noisy, const R (&n)[6],
                                               const R (&sc)[6], const R (&Drel)[6]) {
-  const R S32 = (R)1.2247448713915890491, S6 = (R)2.4494897427831780982;
-  R D3 = Drel[0], D4 = Drel[1], D5 = Drel[2], D6 = Drel[3], D7 = Drel[4], D8 = Drel[5];
-  if (GEN && noisy && d.noise_mode == 1) {              // correlated noise xi = R N (Eqs. 6-7 at u0), scaled by s
-    R z[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      R acc = coef<R>(d, kCoNoiseR + 6 * c) * n[0];
-#pragma unroll
-      for (int e = 1; e < 6; ++e) acc += coef<R>(d, kCoNoiseR + 6 * c + e) * n[e];
-      z[c] = acc;
-    }
-    D3 += sc[0] * z[0];
-    D4 += sc[1] * z[1];
-    D5 += sc[2] * z[2];
-    D6 += sc[3] * z[3];
-    D7 += sc[4] * z[4];
-    D8 += sc[5] * z[5];
-  } else if (noisy) {                            // Eq. 8, scaled per moment by s
-    R s0 = sc[0], s1 = sc[1], s2 = sc[2], s3 = sc[3], s4 = sc[4], s5 = sc[5];
-    if (GEN && d.noise_mode == 2) {              // local density in Eq. 8: amp * sqrt(rho / rho0)
-      const R rho0 = coef<R>(d, kCoRho0);
-      const R fac = sqrt((DEV ? rho0 + sum : sum) / rho0);
-      s0 *= fac; s1 *= fac; s2 *= fac; s3 *= fac; s4 *= fac; s5 *= fac;
-    }
-    D3 += s0 * coef<R>(d, kCoAmp + 3) * n[0];
-    D4 += s1 * coef<R>(d, kCoAmp + 4) * n[1];
-    D5 += s2 * coef<R>(d, kCoAmp + 5) * n[2];
-    D6 += s3 * coef<R>(d, kCoAmp + 6) * n[3];
-    D7 += s4 * coef<R>(d, kCoAmp + 7) * n[4];
-    D8 += s5 * coef<R>(d, kCoAmp + 8) * n[5];
-  }
-  // back transform of the moment change, n_i^a = w_i m_i^a
-  const R w1 = (R)1 / (R)9, w5 = (R)1 / (R)36;
-  const R c0 = (R)(4.0 / 9.0) * ((R)0.5 * D8 - D5);
-  const R ax5 = (R)0.5 * D5 - D8;                   // common to the axis populations
-  const R hx = (R)1.5 * D3;
-  const R p6 = S32 * D6, p7 = S32 * D7;
-  const R dcom = (R)2 * (D5 + D8);                  // common to the diagonal populations
-  const R q6 = S6 * D6, q7 = S6 * D7, q4 = (R)3 * D4;
-  g[0] = g[0] + c0;
-  g[1] = g[1] + w1 * (ax5 + hx - p6);
-  g[3] = g[3] + w1 * (ax5 + hx + p6);
-  g[2] = g[2] + w1 * (ax5 - hx - p7);
-  g[4] = g[4] + w1 * (ax5 - hx + p7);
-  g[5] = g[5] + w5 * (dcom + q4 + q6 + q7);
-  g[6] = g[6] + w5 * (dcom - q4 - q6 + q7);
-  g[7] = g[7] + w5 * (dcom + q4 - q6 - q7);
-  g[8] = g[8] + w5 * (dcom - q4 + q6 - q7);
+  apply_site<R, DEV, GEN>(d, g, sum, noisy, n, sc, Drel);
 }
 
 template <typename R, bool DEV, bool SAMPLE, bool GEN>

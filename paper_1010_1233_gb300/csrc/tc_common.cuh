@@ -91,6 +91,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
 
 __device__ __forceinline__ void wg_barrier(int wg) { asm volatile("bar.sync %0, 128;" :: "r"(1 + wg)); }
 
+// the warpgroup barrier that also ANDs a flag over its 128 threads
+__device__ __forceinline__ bool wg_barrier_and(int wg, bool v) {
+  uint32_t r;
+  asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred p, %2, 128, q;\nselp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(r) : "r"((uint32_t)v), "r"(1 + wg));
+  return r != 0;
+}
+
 __device__ __forceinline__ void tmem_st8(uint32_t a, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
                                          uint32_t r5, uint32_t r6, uint32_t r7) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
@@ -170,7 +178,8 @@ struct TcNet {
   uint64_t* bar;                 // the warpgroup's MMA mbarrier
   int wg, tw;
   uint32_t ph = 0;
-  bool ok = true;
+  bool ok = true;                // false (in every thread of the warpgroup) once a wait gave up
+  uint32_t pend = 2u;            // parity of the commit whose wait gave up (2: none)
 
   // Called by all threads after the block has built the B tiles, allocated tensor memory
   // (base `tmem`) and initialised `bar`, and synchronised.
@@ -186,6 +195,7 @@ struct TcNet {
     bar = wg_bar;
     ph = 0;
     ok = true;
+    pend = 2u;
 #pragma unroll
     for (int v = 0; v < VEC; ++v)        // constant columns 16..23 of A: (1, 0), zeros
       tmem_st8(trow + v * kTileCols + 32 + 16, 0x3F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u);
@@ -193,12 +203,25 @@ struct TcNet {
   }
 
   // the first warp of the warpgroup polls the mbarrier, the other three wait for it at
-  // the warpgroup barrier (polling costs issue slots the other warps of the SM could use)
+  // the warpgroup barrier (polling costs issue slots the other warps of the SM could use).
+  // A wait that gives up clears ok in the whole warpgroup (the barrier ANDs it): from then
+  // on no MMA is issued and no wait is made; drain() waits once more for that commit
+  // before the tensor memory is freed.
   __device__ void wait_mma() {
-    if (tw < 32 && ok) ok = mbar_wait(bar, ph);
-    wg_barrier(wg);
+    bool done = true;
+    if (tw < 32 && ok) done = mbar_wait(bar, ph);
+    const bool was_ok = ok;
+    ok = wg_barrier_and(wg, ok && done);
+    if (was_ok && !ok) pend = ph;
     ph ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
+  }
+
+  // after a wait gave up: one more bounded wait for the commit still pending, so that no
+  // MMA is left writing tensor memory when it is freed (the caller synchronises the block
+  // and frees it afterwards)
+  __device__ void drain() {
+    if (pend != 2u && tw < 32) mbar_wait(bar, pend);
   }
 
   // layer-1 rows of A: (u_x, u_y, rho - rho0, 1, 0, ...), then issue layer 1
@@ -209,7 +232,7 @@ struct TcNet {
     tmem_wait_st();
     asm volatile("tcgen05.fence::before_thread_sync;");
     wg_barrier(wg);
-    if (tw == 0) {
+    if (tw == 0 && ok) {
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int v = 0; v < VEC; ++v) mma_ts(tbase + v * kTileCols, tbase + v * kTileCols + 32, db1, instr_desc(128, 32), 0u);
@@ -228,7 +251,7 @@ struct TcNet {
     asm volatile("tcgen05.fence::before_thread_sync;");
     wg_barrier(wg);
     if (tw < 32) hook();
-    if (tw == 0) {
+    if (tw == 0 && ok) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint64_t db = L == 2 ? db2 : db3;
       constexpr uint32_t idesc = instr_desc(128, L == 2 ? 32 : 16);

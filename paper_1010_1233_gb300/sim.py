@@ -215,6 +215,16 @@ class Sim:
         L.check(L.lib().flb_get_step_config(self._ctx, ctypes.byref(v), ctypes.byref(g), ctypes.byref(s)))
         return int(v.value), int(g.value), int(s.value)
 
+    def set_network_engine(self, engine):
+        """'warp' (warp-level MMAs, default) or 'tcgen05' (tensor-memory MMAs)."""
+        e = {"warp": L.FLB_NET_WARP, "tcgen05": L.FLB_NET_TCGEN05}[engine] if isinstance(engine, str) else int(engine)
+        L.check(L.lib().flb_set_network_engine(self._ctx, e))
+
+    def network_engine(self):
+        e = ctypes.c_int()
+        L.check(L.lib().flb_get_network_engine(self._ctx, ctypes.byref(e)))
+        return "tcgen05" if e.value == L.FLB_NET_TCGEN05 else "warp"
+
     def set_graphs(self, enable=True):
         L.check(L.lib().flb_set_graphs(self._ctx, int(bool(enable))))
 
