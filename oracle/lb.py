@@ -29,8 +29,10 @@ Readings where the paper is silent or unit-specific:
   non-conserved moments is correlated, xi = s * (R N) with R from
   ``oracle.correlated`` (Eq. 6 with the covariance of Eq. 7 at f^0(rho0, u0)).
 
-Normals come from ``oracle.philox`` with counter (site, t, call | tag << 8,
-stream); D2Q9 uses normals 0..5 for moments 3..8, D1Q3 normal 0 for moment 2.
+Normals come from ``oracle.philox``: D2Q9 uses the six normals of
+``pair_normals`` (sites 2q, 2q + 1 share the counter (q, t, call, stream), calls
+0..2) for moments 3..8; D1Q3 normal 0 of ``site_normals`` (counter (site, t,
+call | tag << 8, stream)) for moment 2.
 
 Parity: pinned (conservation, shear-wave decay against the continuum viscosity
 and the exact linear eigenvalue, uniform-equilibrium fixed point, equal-time
@@ -194,8 +196,10 @@ def collide(p, f, t, return_parts=False, sites=None):
     mask = p.mask()
     active = [a for a in lat.nonconserved if (mask >> a) & 1]
     if active:
-        n_normals = 6 if lat.name == "D2Q9" else 1
-        N = _rng.site_normals(n_normals, sites, t, 0, p.stream, p.seed)
+        if lat.name == "D2Q9":
+            N = _rng.pair_normals(sites, t, 0, p.stream, p.seed)
+        else:
+            N = _rng.site_normals(1, sites, t, 0, p.stream, p.seed)
         s = noise_scale(p, rho, u)
         if p.noise_mode == 1:                                          # xi = R N (Eqs. 6-7 at u0)
             R, _, _ = _corr.noise_root(lat, tau, p.rho0, p.kT, p.u0_vec(), mask)

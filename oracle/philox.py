@@ -13,6 +13,10 @@ generator so that every draw is a pure function of (seed, step, site, stream):
 * Counter layout: word 0 = site index y*nx + x, word 1 = step index (mod 2^32),
   word 2 = call | tag << 8 (tag 0 = dynamics, tag 1 = thermal initial state),
   word 3 = stream id of the replica.  Key = (seed mod 2^32, seed >> 32).
+* D2Q9 dynamics (``pair_normals``): the six normals of a site need six words, so
+  the two sites 2q and 2q + 1 (the same row, nx even) share word 0 = q: calls 0, 1
+  and 2 give twelve words W0..W11, site 2q + h takes W_{6h} .. W_{6h+5}.  (A reading
+  of Eq. 8, whose N only needs zero mean and unit variance: every word is used once.)
 * Uniform: u = (w + 1/2) 2^-32 in FP64 (never 0 or 1).  Box-Muller on the pair
   (u_a, u_b): r = sqrt(-2 ln u_a), N = (r cos 2 pi u_b, r sin 2 pi u_b).
 
@@ -78,3 +82,25 @@ def site_normals(n_normals, site, step, tag, stream, seed):
         a, b = box_muller(uniform_fp64(words[2 * p]), uniform_fp64(words[2 * p + 1]))
         out.extend([a, b])
     return np.stack(out[:n_normals])
+
+
+def pair_normals(site, step, tag, stream, seed):
+    """The six unit normals of each D2Q9 site, array (6,) + site.shape.
+
+    Sites 2q and 2q + 1 share the counter index q; calls 0, 1, 2 give words
+    W0..W11 and site 2q + h takes W_{6h} .. W_{6h+5}; normals 2m and 2m + 1 of the
+    site come from the pair (W_{6h+2m}, W_{6h+2m+1}).
+    """
+    site = np.asarray(site, dtype=np.uint64)
+    q = site >> np.uint64(1)
+    h = (site & np.uint64(1)).astype(bool)
+    W = []
+    for call in range(3):
+        W.extend(philox4x32_10(q, step, call | (tag << 8), stream, seed))
+    out = []
+    for m in range(3):
+        wa = np.where(h, W[6 + 2 * m], W[2 * m])
+        wb = np.where(h, W[7 + 2 * m], W[2 * m + 1])
+        a, b = box_muller(uniform_fp64(wa), uniform_fp64(wb))
+        out.extend([a, b])
+    return np.stack(out)

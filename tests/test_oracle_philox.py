@@ -108,3 +108,37 @@ def test_site_normals_statistics():
         assert stats.kstest(x, "norm").pvalue > 1e-4
     C = np.corrcoef(N)
     assert np.abs(C - np.eye(6)).max() < 0.02
+
+
+def test_pair_normals_use_each_word_of_three_calls_once():
+    # sites 2q and 2q + 1 share counter index q; calls 0..2 give W0..W11; site 2q + h
+    # takes W_{6h}..W_{6h+5}: rebuilt here word by word from the generator itself
+    q = np.array([0, 7, 12345, 2**31 - 1], dtype=np.uint64)
+    step, stream, seed = 77, 5, 2**40 + 3
+    W = []
+    for call in range(3):
+        W.extend(P.philox4x32_10(q, step, call, stream, seed))
+    for h in (0, 1):
+        N = P.pair_normals(2 * q + h, step, 0, stream, seed)
+        for m in range(3):
+            a, b = P.box_muller(P.uniform_fp64(W[6 * h + 2 * m]), P.uniform_fp64(W[6 * h + 2 * m + 1]))
+            assert np.array_equal(N[2 * m], a) and np.array_equal(N[2 * m + 1], b)
+    # the first site of a pair draws exactly what site_normals draws for the index q
+    assert np.array_equal(P.pair_normals(2 * q, step, 0, stream, seed), P.site_normals(6, q, step, 0, stream, seed))
+
+
+def test_pair_normals_statistics():
+    # twelve normals of a site pair: unit normal, mutually uncorrelated, and independent
+    # of the neighbouring pair's
+    site = np.arange(200_000, dtype=np.uint64)
+    N = P.pair_normals(site, 17, 0, 3, 99)
+    assert N.shape == (6, 200_000)
+    for x in N:
+        assert abs(x.mean()) < 5 / np.sqrt(x.size)
+        assert abs(x.var() - 1) < 5 * np.sqrt(2 / x.size)
+        assert stats.kstest(x, "norm").pvalue > 1e-4
+    both = np.concatenate([N[:, 0::2], N[:, 1::2]])          # (12, pairs): even site, odd site
+    C = np.corrcoef(both)
+    assert np.abs(C - np.eye(12)).max() < 0.02
+    nxt = np.concatenate([N[:, 0:-2:2], N[:, 2::2]])         # pair q against pair q + 1
+    assert np.abs(np.corrcoef(nxt) - np.eye(12)).max() < 0.02

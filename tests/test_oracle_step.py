@@ -74,7 +74,7 @@ def test_noise_uses_generator_normals_per_moment():
     p = _params(tau=W.taus_d2q9(1.0), kT=0.2, nx=4, ny=3, seed=9, stream=2)
     f = lb.uniform_state(p)
     _, parts = lb.collide(p, f, 5, return_parts=True)
-    N = philox.site_normals(6, lb.site_index(p), 5, 0, 2, 9)
+    N = philox.pair_normals(lb.site_index(p), 5, 0, 2, 9)
     assert np.abs(parts["xi"][3:] - np.sqrt(3 * 0.2) * N).max() < 1e-14
 
 
