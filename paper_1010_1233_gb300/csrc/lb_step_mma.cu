@@ -89,12 +89,12 @@ k_step_d2q9_wn(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Re
         for (int i = 0; i < 9; ++i) g[i] = make_float2(f[i][2 * p], f[i][2 * p + 1]);
         float2 sum, ux, uy;
         macro_pair(g, rho0, sum, ux, uy);
-        // the Philox words of both sites (independent integer work the scheduler can place
-        // between the network's dependent MMAs; drawn even without noise, then unused)
+        // the Philox words of both sites: three calls (independent integer work the
+        // scheduler can place between the network's dependent MMAs; drawn even without
+        // noise, then unused)
         const uint32_t site = (uint32_t)uc.y * (uint32_t)d.nx + (uint32_t)(uc.x0 + 2 * p);
         uint4 w0a, w1a, w0b, w1b;
-        philox_words_d2q9(d, site, step, w0a, w1a);
-        philox_words_d2q9(d, site + 1u, step, w0b, w1b);
+        philox_words_pair(d, site, step, w0a, w1a, w0b, w1b);
         const uint32_t x[4] = {wn_pack2(ux.x, uy.x), wn_pack2(ux.y, uy.y), wn_pack2(sum.x, 1.f), wn_pack2(sum.y, 1.f)};
         float s0[6], s1[6];
         net.forward(x, scr, s0, s1);

@@ -248,13 +248,33 @@ __device__ __forceinline__ void macro_d2q9(const R (&g)[9], R rho0, R& sum, R& u
   macro_site<R, DEV>(g, rho0, sum, ux, uy);
 }
 
-// The six unit normals of a site (Philox counter: site, step, call 0/1, stream), in two
-// parts so that a kernel can spread them over independent work: the counter-based words,
-// then the Box-Muller transform of three word pairs.
+// The six unit normals of a site, in two parts so that a kernel can spread them over
+// independent work: the counter-based words, then the Box-Muller transform of three word
+// pairs.  Sites 2q and 2q + 1 (the same row: nx is even) share the Philox counter
+// (q, step, call, stream): calls 0, 1, 2 give twelve words W0..W11, and site 2q + h takes
+// W_{6h}..W_{6h+5}, whose pairs (W_{6h+2m}, W_{6h+2m+1}) give normals 2m, 2m + 1.
+// philox_words_d2q9: one site (two calls); on return its six words are w0.x..w0.w, w1.x,
+// w1.y in pair order.
 __device__ __forceinline__ void philox_words_d2q9(const ReplicaDesc& d, uint32_t site, uint32_t step, uint4& w0,
                                                   uint4& w1) {
-  w0 = philox4x32_10_rk(site, step, 0u, d.stream, d.rkey);
-  w1 = philox4x32_10_rk(site, step, 1u, d.stream, d.rkey);
+  const uint32_t q = site >> 1, h = site & 1u;
+  const uint4 a = philox4x32_10_rk(q, step, h, d.stream, d.rkey);         // call h
+  const uint4 b = philox4x32_10_rk(q, step, h + 1u, d.stream, d.rkey);    // call h + 1
+  w0 = h ? make_uint4(a.z, a.w, b.x, b.y) : a;
+  w1 = h ? make_uint4(b.z, b.w, 0u, 0u) : make_uint4(b.x, b.y, 0u, 0u);
+}
+
+// Both sites of a pair (site_even even): three calls; the words of each site as above.
+__device__ __forceinline__ void philox_words_pair(const ReplicaDesc& d, uint32_t site_even, uint32_t step, uint4& w0a,
+                                                  uint4& w1a, uint4& w0b, uint4& w1b) {
+  const uint32_t q = site_even >> 1;
+  const uint4 c0 = philox4x32_10_rk(q, step, 0u, d.stream, d.rkey);
+  const uint4 c1 = philox4x32_10_rk(q, step, 1u, d.stream, d.rkey);
+  const uint4 c2 = philox4x32_10_rk(q, step, 2u, d.stream, d.rkey);
+  w0a = c0;
+  w1a = make_uint4(c1.x, c1.y, 0u, 0u);
+  w0b = make_uint4(c1.z, c1.w, c2.x, c2.y);
+  w1b = make_uint4(c2.z, c2.w, 0u, 0u);
 }
 
 template <typename R>
