@@ -27,7 +27,10 @@ Galilean-invariant ideal gas).
 
 Parity: forward pinned by special cases (zero output layer gives s = 1, a
 single-unit network equals its closed form); backward pinned by central finite
-differences of the loss; Adam by its published update (Kingma & Ba, 2015).
+differences of the loss; Adam (Kingma & Ba, 2015) by the closed form of its first
+two steps on a gradient that flips sign (state carried, bias correction at t = 2)
+and against an installed independent implementation (torch.optim.Adam, FP64)
+over 40 steps.
 """
 import numpy as np
 

@@ -1,5 +1,6 @@
 """Pins of the oracle's noise-scale network, its loss gradient and Adam (CPU only)."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 from paper_1010_1233_gb300 import workloads as W
@@ -78,3 +79,37 @@ def test_adam_first_step_is_signed_lr():
     g = {"a": np.array([0.3, -1e-3, 2.0])}
     out = mlp.adam_step(w, g, {}, lr=0.01, eps=1e-8)
     assert np.allclose(out["a"], w["a"] - 0.01 * g["a"] / (np.abs(g["a"]) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_adam_alternating_gradient_closed_form():
+    # g, then -g: m2 = -(1 - b1)^2 g, v2 = (1 - b2^2) g^2, so the bias-corrected second step
+    # is -lr (1 - b1) / (1 + b1) sign(g) (up to eps): state carried, t = 2 in the correction
+    b1, b2, lr = 0.9, 0.999, 0.01
+    w = {"a": np.array([1.0, -2.0, 0.5, 3.0])}
+    g = np.array([0.3, -0.7, 2.0, 1e-2])
+    st = {}
+    w1 = mlp.adam_step(w, {"a": g}, st, lr=lr, beta1=b1, beta2=b2, eps=0.0)
+    w2 = mlp.adam_step(w1, {"a": -g}, st, lr=lr, beta1=b1, beta2=b2, eps=0.0)
+    assert st["t"] == 2
+    assert np.allclose(w1["a"] - w["a"], -lr * np.sign(g), rtol=0, atol=1e-15)
+    assert np.allclose(w2["a"] - w1["a"], lr * (1 - b1) / (1 + b1) * np.sign(g), rtol=0, atol=1e-15)
+
+
+def test_adam_matches_torch_optimizer_over_many_steps():
+    # an installed, independent Adam (torch.optim.Adam on the CPU, FP64) over 40 steps of
+    # varying gradients on two parameter arrays
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    w = {"a": rng.normal(size=(5, 3)), "b": rng.normal(size=7)}
+    params = {k: torch.tensor(v.copy(), dtype=torch.float64, requires_grad=True) for k, v in w.items()}
+    opt = torch.optim.Adam(list(params.values()), lr=3e-3, betas=(0.8, 0.99), eps=1e-7)
+    st = {}
+    for _ in range(40):
+        g = {k: rng.normal(size=v.shape) * rng.uniform(0.01, 3.0) for k, v in w.items()}
+        w = mlp.adam_step(w, g, st, lr=3e-3, beta1=0.8, beta2=0.99, eps=1e-7)
+        opt.zero_grad()
+        for k, p in params.items():
+            p.grad = torch.tensor(g[k], dtype=torch.float64)
+        opt.step()
+    for k, p in params.items():
+        assert np.abs(w[k] - p.detach().numpy()).max() < 1e-12, k
