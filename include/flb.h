@@ -340,9 +340,13 @@ int flb_spectra_accumulate(int precision, int nx, int ny, int n_fields, const vo
  * has no counterpart: this is a deployment variant.  Its scratch is a fixed
  * 8 MiB device array inside the library, held by every GPU that loads the
  * library until the process exits; sizes whose plan needs more return
- * FLB_EINVAL with a message.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Calls allocate nothing.  All calls on
+ * FLB_EINVAL with a message.  Each call outside a stream capture looks up the
+ * array's device address (cudaGetSymbolAddress) with the device current, so the
+ * address stays right after a cudaDeviceReset; a call made while its stream is
+ * being captured uses the address found by the last such call on that device, so
+ * make the first call on a device (and the first after a reset) before any
+ * capture.  Calls allocate nothing (the array's memory is taken when the library's
+ * module is loaded on the device, at the latest by the first call).  All calls on
  * a device share the array, which keeps the last call's contents (each call
  * rewrites what it reads); calls whose GPU work overlaps race on it and must be
  * serialised.  Outputs and semantics as flb_spectra_accumulate. */

@@ -28,17 +28,22 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_spectra_scratch[kStaticScratchBytes];
 
 // Device address of g_spectra_scratch on the current device.  In host code the
-// symbol names a host-side stand-in, so the address is looked up once per device,
-// with that device current, the first time the entry point runs there.
-static int static_scratch(char** out) {
+// symbol names a host-side stand-in, so the address is looked up with that device
+// current: on the first call there, and again on every call made outside a stream
+// capture (after a cudaDeviceReset the module is loaded again, possibly elsewhere);
+// a call made while its stream is being captured uses the address found last.
+static int static_scratch(cudaStream_t st, char** out) {
   static std::mutex mu;
   static char* addr[kMaxDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(FLB_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return set_error(FLB_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return set_error(FLB_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (!addr[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_spectra_scratch);
     if (e != cudaSuccess || !p)
@@ -65,7 +70,7 @@ extern "C" int flb_spectra_accumulate_static(int precision, int nx, int ny, int 
                      "flb_spectra_accumulate_static; use flb_spectra_accumulate with caller scratch",
                      n_fields, nx, ny, P.scratch_bytes, kStaticScratchBytes);
   char* scratch = nullptr;
-  rc = static_scratch(&scratch);
+  rc = static_scratch(static_cast<cudaStream_t>(cuda_stream), &scratch);
   if (rc) return rc;
   return spectra_launch(precision, P, scratch, fields_dev, pair_sums_dev, mean0_dev,
                         static_cast<cudaStream_t>(cuda_stream));

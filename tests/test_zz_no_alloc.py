@@ -5,8 +5,9 @@ whole memory budget, a memory-capped service, a loop that must not pay for
 cudaMalloc's synchronisation), this entry point keeps its scratch in a fixed
 8 MiB device array inside the library.  This test calls it through the C ABI
 and compares its sums with those of flb_spectra_accumulate (caller scratch) on
-the same inputs, after each of two calls in a row; it also checks the size
-limit.  The file is named to be collected last.
+the same inputs, after each of two calls in a row, including a plan within 14 %
+of the array's size; it checks that repeated calls leave the device's free
+memory unchanged, and the size limit.  The file is named to be collected last.
 """
 import ctypes
 
@@ -40,8 +41,10 @@ def lib():
     return lib
 
 
+# the last case's plan needs 7.2 MB, within 14 % of the 8 MiB array
 @pytest.mark.parametrize("dtype,F,ny,nx,tol", [(torch.float32, 3, 128, 256, 2e-6),
-                                               (torch.float64, 4, 2048, 8, 1e-12)])
+                                               (torch.float64, 4, 2048, 8, 1e-12),
+                                               (torch.float64, 11, 4096, 16, 1e-12)])
 def test_static_scratch_matches_caller_scratch(lib, dtype, F, ny, nx, tol):
     _, ns = spectra_sizes(F, ny, nx, "fp64" if dtype == torch.float64 else "fp32")
     ref_sums = ref_m0 = None
@@ -64,3 +67,21 @@ def test_static_scratch_rejects_oversize(lib):
     m0 = torch.zeros(F, dtype=torch.float64, device="cuda")
     assert _static(lib, x, sums, m0) == L.FLB_EINVAL
     assert b"static array" in lib.flb_last_error()
+
+
+def test_static_calls_allocate_nothing(lib):
+    # after one call (which may load the library's module and with it the array), further
+    # calls leave the device's free memory unchanged
+    F, ny, nx = 3, 256, 256
+    _, ns = spectra_sizes(F, ny, nx, "fp32")
+    x = torch.tensor(W.random_perturbation((F, ny, nx), 91), dtype=torch.float32, device="cuda")
+    sums = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    m0 = torch.zeros(F, dtype=torch.float64, device="cuda")
+    assert _static(lib, x, sums, m0) == L.FLB_OK, lib.flb_last_error()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert _static(lib, x, sums, m0) == L.FLB_OK, lib.flb_last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
