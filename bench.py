@@ -10,7 +10,14 @@ steps (K a multiple of 20 covers it exactly).
 Prints one JSON line (rank 0): MLUPS of the whole job, the HBM roofline of the
 dominant kernel (the fused stream-collide-noise step, 72 algorithmic bytes per
 site: 9 FP32 reads + 9 FP32 writes), the end-to-end number through the public
-API with host buffers, and the oracle's throughput on the host cores.
+API with host buffers (and the copy rates), the oracle's throughput on one host
+core and on all of them, and the accuracy half of the metric (``accuracy``: max
+|S_ab(k) - theory| at u0 = 0 on the 256^2 workload, and plain / learned /
+correlated noise at u0 = 0.2; skip with --no-accuracy).
+
+``--workload sweep64``: the 64-replica Galilean-invariance sweep (sizes 64^2 ..
+512^2, u0 0 .. 0.3, tau_s 0.55 .. 1, network off, three fields every 10 steps) in
+one batched launch per step, with per-replica finiteness.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 16384]
 Under torchrun every rank runs its own replica (weak scaling, no data-path
@@ -33,13 +40,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SAMPLE_EVERY = 20
+SWEEP_EVERY = 10                 # the Galilean-invariance sweep samples every 10 steps
 ALG_BYTES_PER_SITE = 72          # FP32 deviation storage: 9 reads + 9 writes of 4 B
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per site of one launch of the dominant kernel in the tuned
-# launch configuration (direct tensor-core step kernel, vec 2): ncu capture of
-# k_step_d2q9_tc<2,0,0> on the 4096^2 case (profiles/k_step_d2q9_tc_fp32_mlp_4096.md),
-# scaled by the site count; None for any other configuration.
-TRAFFIC_PER_SITE = {(2, 0): (604123904 + 560039168) / 4096**2}
+# DRAM bytes (read + write) per site of one launch of the dominant kernel, keyed by
+# (network engine, vec, staged), from ncu captures on the 4096^2 case scaled by the site
+# count (profiles/k_step_d2q9_tc_fp32_mlp_4096.md: the tensor-memory engine, vec 2;
+# profiles/k_step_d2q9_wn_fp32_mlp_4096.md: the warp engine, vec 4); None for any
+# other configuration.
+TRAFFIC_PER_SITE = {("tcgen05", 2, 0): (604123904 + 560039168) / 4096**2}
+KERNEL_NAME = {"warp": "k_step_d2q9_wn (fused pull-stream/collide/noise, network on warp-level tensor-core MMAs)",
+               "tcgen05": "k_step_d2q9_tc (fused pull-stream/collide/noise, network on tcgen05)"}
 # The same for the 3D step kernels (k_step_3d, one replica, tuned vec) from ncu captures at
 # 256^3 (profiles/k_step_3d_fp32_256.md), scaled by the site count; keyed by (workload, vec).
 TRAFFIC_PER_SITE_3D = {("d3q15_512", 4): (1006748000 + 958004736) / 256**3,
@@ -52,18 +63,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="d2q9_16384", choices=["d2q9_16384", "d3q15_512", "d3q19_512"])
+    ap.add_argument("--workload", default="d2q9_16384", choices=["d2q9_16384", "sweep64", "d3q15_512", "d3q19_512"])
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the correlator-accuracy runs")
     ap.add_argument("--n", type=int, default=None, help="lattice edge (default: that of the workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=400)
     ap.add_argument("--cpu-n", type=int, default=None, help="edge of the oracle's sample (256 for D2Q9, 24 for 3D)")
     args = ap.parse_args()
-    three_d = args.workload != "d2q9_16384"
+    three_d = args.workload.startswith("d3q")
     if args.n is None:
         args.n = 512 if three_d else 16384
     if args.cpu_n is None:
-        args.cpu_n = 24 if three_d else 256
+        args.cpu_n = 24 if three_d else (64 if args.workload == "sweep64" else 256)
     return args
 
 
@@ -182,13 +194,19 @@ def end_to_end(sim, K, V, world, local, barrier):
     L.check(lib.flb_save(sim._ctx, pout, ctypes.byref(size)))         # untimed: first use of the output
     barrier()
     t0 = time.perf_counter()
-    L.check(lib.flb_load(sim._ctx, pin, nb))
+    L.check(lib.flb_load(sim._ctx, pin, nb))          # synchronous copies in
+    t1 = time.perf_counter()
     sim.run(K, SAMPLE_EVERY)
-    L.check(lib.flb_save(sim._ctx, pout, ctypes.byref(size)))
+    sim.sync()
+    t2 = time.perf_counter()
+    L.check(lib.flb_save(sim._ctx, pout, ctypes.byref(size)))   # synchronous copies out
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t3 = time.perf_counter()
+    dt = t3 - t0
     value, _ = job_throughput(V, K, dt, world, device="cuda")
     return {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": nb / K, "d2h_bytes_per_step": nb / K,
+            "h2d_gbs": nb / (t1 - t0) / 1e9, "d2h_gbs": nb / (t3 - t2) / 1e9,
+            "seconds": {"load": t1 - t0, "steps": t2 - t1, "save": t3 - t2},
             "pinned": pinned, "host_buffers": n_buf, "local_cpus": local_cpus,
             "what": "flb_load(host state) + K steps + flb_save(host state)"}
 
@@ -202,21 +220,37 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def gpu_id(local):
+    """nvidia-smi's id of the CUDA device `local` of this process: its UUID (GPU-...), so
+    that the samples are of this GPU whatever CUDA_VISIBLE_DEVICES maps; the visible
+    device's own entry or index when the UUID is not available."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return vis[local] if local < len(vis) else str(local)
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region
+    (every 20 ms, so that even a short timed region gets several samples)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, local):
+        self.id = gpu_id(local)
         self.proc = None
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.id}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -250,29 +284,97 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu": self.id}
 
 
-def cpu_baseline(n, steps, args_threads=1):
-    """Time the FP64 oracle on the host (one thread) on an n x n sample of the workload."""
-    code = r"""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_code(workload, n, steps, every):
+    """The oracle timing script: one replica of the workload at edge n (d2q9_16384: the
+    headline parameters with the seeded network; sweep64: the sweep's first replica, tau_s
+    0.55, u0 0, resized to n); argv[1] (optional) shifts the seed."""
+    pick = ('p = dict(W.d2q9_16384(%d)["replicas"][0])' % n if workload == "d2q9_16384" else
+            'p = dict(W.sweep64()["replicas"][0], nx=%d, ny=%d)' % (n, n))
+    net = workload == "d2q9_16384"
+    return r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
 import numpy as np
 from oracle import lb
 from paper_1010_1233_gb300 import workloads as W
-wl = W.d2q9_16384(%d)
-p = dict(wl["replicas"][0])
-w = W.mlp_weights(1234, out_scale=0.1)
+%s
+if len(sys.argv) > 1:
+    p["seed"] = p["seed"] + int(sys.argv[1])
 P = lb.Params(**p)
-P.mlp = {k: v.astype(np.float64) for k, v in w.items()}
+if %r:
+    w = W.mlp_weights(1234, out_scale=0.1)
+    P.mlp = {k: v.astype(np.float64) for k, v in w.items()}
 r = lb.Run(P)
 r.run(1, %d)
 t0 = time.perf_counter()
 r.run(%d, %d)
 dt = time.perf_counter() - t0
 print(json.dumps({"seconds": dt, "sites": p["nx"] * p["ny"], "steps": %d}))
-""" % (ROOT, n, SAMPLE_EVERY, steps, SAMPLE_EVERY, steps)
+""" % (ROOT, pick, net, every, steps, every, steps)
+
+
+def _sample_text(workload, n, steps, every):
+    what = ("same taus/u0/network/fields" if workload == "d2q9_16384" else
+            "the sweep's first replica (tau_s 0.55, u0 0, 3 fields)")
+    return f"D2Q9 {n}x{n} FP64 oracle, {what}, {steps} steps incl. {max(1, steps // every)} direct-DFT samples"
+
+
+def cpu_baseline_all(n, steps, workload="d2q9_16384", every=SAMPLE_EVERY):
+    """The FP64 oracle on every host core at once: one single-threaded process per core,
+    each timing its own replica (seed + process index) of the n x n sample; throughput of
+    the whole host = processes x sites x steps / the slowest process's time."""
+    P = host_cores()
+    code = _oracle_code(workload, n, steps, every)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(i)], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True, env=env) for i in range(P)]
+    secs, sites, nsteps = [], None, None
+    for pr in procs:
+        out, err = pr.communicate(timeout=1800)
+        if pr.returncode != 0:
+            return {"error": err[-400:]}
+        d = json.loads(out.strip().splitlines()[-1])
+        secs.append(d["seconds"])
+        sites, nsteps = d["sites"], d["steps"]
+    mlups = P * sites * nsteps / max(secs) / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": P, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{P} single-threaded processes at once, each: " + _sample_text(workload, n, nsteps, every)
+                      + f" (own seed); slowest {max(secs):.1f} s, fastest {min(secs):.1f} s"}
+
+
+def cpu_baseline(n, steps, args_threads=1, workload="d2q9_16384", every=SAMPLE_EVERY):
+    """Time the FP64 oracle on the host (one thread) on an n x n sample of the workload."""
+    code = _oracle_code(workload, n, steps, every)
     env = dict(os.environ, OMP_NUM_THREADS=str(args_threads), OPENBLAS_NUM_THREADS=str(args_threads),
                MKL_NUM_THREADS=str(args_threads), CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
@@ -280,9 +382,9 @@ print(json.dumps({"seconds": dt, "sites": p["nx"] * p["ny"], "steps": %d}))
         return {"error": out.stderr[-400:]}
     d = json.loads(out.stdout.strip().splitlines()[-1])
     mlups = d["sites"] * d["steps"] / d["seconds"] / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": args_threads, "kind": "oracle",
-            "sample": f"D2Q9 {n}x{n} FP64 oracle, same taus/u0/network/fields, {steps} steps incl. "
-                      f"{max(1, steps // SAMPLE_EVERY)} direct-DFT samples, {d['seconds']:.1f} s"}
+    return {"value": mlups, "unit": "MLUPS", "cores": args_threads, "kind": "oracle", "cpu": cpu_model(),
+            "host_cores": host_cores(),
+            "sample": _sample_text(workload, n, steps, every) + f", {d['seconds']:.1f} s"}
 
 
 def cpu_baseline3(workload_name, n, steps, args_threads=1):
@@ -321,7 +423,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload != "d2q9_16384":
+    if args.workload.startswith("d3q"):
         n = args.cpu_n
         per = cpu_baseline3(args.workload, n, max(SAMPLE_EVERY, args.steps // 5) if args.steps > 0 else SAMPLE_EVERY)
         if "error" in per:
@@ -338,16 +440,17 @@ def run_reference(args):
         print(json.dumps(line))
         return
     n = args.cpu_n
-    per = cpu_baseline(n, max(SAMPLE_EVERY, args.steps // 5) if args.steps > 0 else SAMPLE_EVERY)
+    every = SWEEP_EVERY if args.workload == "sweep64" else SAMPLE_EVERY
+    per = cpu_baseline(n, max(every, args.steps // 5) if args.steps > 0 else every, workload=args.workload,
+                       every=every)
     if "error" in per:
         print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + per["error"][-200:]}))
         return
-    wl, p = workload(args.n)
     line = {
         "impl": "reference", "metric": "D2Q9 fluctuating-LB MLUPS", "value": per["value"], "unit": "MLUPS",
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "d2q9_16384 (bounded CPU sample)", "nx": n, "ny": n},
+        "config": {"workload": f"{args.workload} (bounded CPU sample)", "nx": n, "ny": n},
         "cpu_baseline": per,
         "e2e": {"value": per["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -445,8 +548,43 @@ def run_ours3(args):
         dist.destroy_process_group()
 
 
+def accuracy():
+    """The accuracy half of the metric (max S_ab(k) error against theory), two parts:
+
+    * D2Q9 256^2, FP32 deviation storage, thermal start, tau 0.8 / 0.8 / 1.0, u0 = 0,
+      all nine moment fields (45 pairs) every 10 steps, 2e5 steps in 10 batches: at u0 = 0
+      Eq. 7 makes delta_ab the exact equal-time value, so max |S - delta|, its k-mean and
+      the largest batch-means z score measure the method against its sampling noise;
+    * at u0 = 0.2 (held out of the training velocities): the plain method, the learned
+      noise scales (trained here on 16 plain 128^2 runs at u0 in [0, 0.3]) and the
+      correlated noise, max and RMS of |S - delta| over the six hydrodynamic pairs.
+    Wave vectors excluded: k = 0 and the neutral modes (pi, 0), (0, pi)."""
+    from paper_1010_1233_gb300 import experiments, learned
+    t0 = time.time()
+    a = experiments.d2q9_256(precision="fp32")
+    t1 = time.time()
+    res, _ = learned.experiment(heldout=(0.2,))
+    t2 = time.time()
+    return {
+        "equal_time_u0_0": {
+            "workload": "D2Q9 256x256 FP32, thermal start, tau 0.8/0.8/1.0, u0 0, kT 1e-4, 9 fields (45 pairs) "
+                        "every 10 steps", "steps": a["steps"], "samples": a["samples"], "batches": a["batches"],
+            "theory": "delta_ab (Eq. 7, exact at u0 = 0)", "max_abs_err": a["max_err"],
+            "kmean_abs_err": a["mean_err"], "max_z": a["max_z"], "mlups": a["mlups"], "seconds": t1 - t0},
+        "u0_0.2": {
+            "workload": "D2Q9 128x128 FP32, tau 0.8/0.8/1.0, kT 1e-4, 1e5 steps sampled every 10 after 1e4",
+            "pairs": "rho rho, rho u_x, rho u_y, u_x u_x, u_x u_y, u_y u_y; target: 1 for autos, 0 for cross pairs",
+            "plain": res["heldout"]["0.2"]["plain"], "learned": res["heldout"]["0.2"]["learned"],
+            "correlated": res["heldout"]["0.2"]["correlated"],
+            "train": {"u0": res["train_u0"], "loss_before": res["loss_before"], "loss_after": res["loss_after"],
+                      "collect_s": res["collect_s"], "train_s": res["train_s"]},
+            "seconds": t2 - t1},
+        "excluded_k": "k = 0, (pi, 0), (0, pi)",
+    }
+
+
 def run_ours(args):
-    if args.workload != "d2q9_16384":
+    if args.workload.startswith("d3q"):
         return run_ours3(args)
     import numpy as np
     import torch
@@ -461,14 +599,22 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     build.build()
-    wl, p = workload(args.n)
-    p = rank_replica(p, rank)
-    sim = Sim(p, precision="fp32")
-    wts = W.mlp_weights(1234, out_scale=0.1)
-    sim.set_mlp(wts)
+    sweep = args.workload == "sweep64"
+    every = SWEEP_EVERY if sweep else SAMPLE_EVERY
+    if sweep:
+        reps = [dict(q, seed=q["seed"] + 64 * rank, stream=q["stream"] + 64 * rank) for q in W.sweep64()["replicas"]]
+        sim = Sim(reps, precision="fp32")
+        V = sum(q["nx"] * q["ny"] for q in reps)
+        p = reps[0]
+    else:
+        wl, p = workload(args.n)
+        p = rank_replica(p, rank)
+        sim = Sim(p, precision="fp32")
+        sim.set_mlp(W.mlp_weights(1234, out_scale=0.1))
+        V = p["nx"] * p["ny"]
     tuned = sim.autotune(trials=5)
+    engine = sim.network_engine() if not sweep else None
     stream = sim.stream
-    V = p["nx"] * p["ny"]
     K, Wm = args.steps, max(3, args.warmup)
 
     def barrier():
@@ -477,18 +623,22 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    sim.run(Wm, SAMPLE_EVERY)
+    sim.run(Wm, every)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         e0.record(stream)
-        sim.run(K, SAMPLE_EVERY)
+        sim.run(K, every)
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
     value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
     ms_max = t_max * 1e3
-    launches = expected_launches(Wm, K, SAMPLE_EVERY, sample_kernels=3 if p["ny"] > 2048 else 2)
+    maxny = max(q["ny"] for q in (reps if sweep else [p]))
+    launches = expected_launches(Wm, K, every, sample_kernels=3 if maxny > 2048 else 2)
+    finite = None
+    if sweep:
+        finite = [bool(np.all(np.isfinite(sim.conserved(r)))) for r in range(len(reps))]
 
     # dominant kernel alone: plain (non-sampling) steps back to back, same launch configuration
     Kd = max(20, min(K, 100))
@@ -500,41 +650,65 @@ def run_ours(args):
     step_ms = d0.elapsed_time(d1) / Kd
     hbm, peak_kind = peaks()
     achieved = ALG_BYTES_PER_SITE * V / (step_ms * 1e-3) / 1e9
-    tps = TRAFFIC_PER_SITE.get((tuned[0], tuned[2]))
+    tps = None if sweep else TRAFFIC_PER_SITE.get((engine, tuned[0], tuned[2]))
     traffic = tps * V if tps else None
 
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(sim, K, V, world, local, barrier)
+    sim.close()
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(args.cpu_n, args.cpu_steps)
+        cpu_n = args.cpu_n
+        cpu = cpu_baseline(cpu_n, args.cpu_steps, workload=args.workload, every=every)
+        cpu_all = cpu_baseline_all(cpu_n, max(every, args.cpu_steps // 2), workload=args.workload, every=every)
+
+    acc = None
+    if rank == 0 and world == 1 and not sweep and not args.no_accuracy:
+        acc = accuracy()
 
     if rank == 0:
+        clocks = clk.summary()
+        if clocks:
+            clocks["mcycles_per_step"] = ms_max / K * clocks["sm_mhz"] / 1e3
+        if sweep:
+            config = {"workload": "sweep64", "lattice": "D2Q9", "replicas": len(reps), "sites": V,
+                      "sizes": "64/128/256/512 squared, 16 each", "u0_x": "0..0.30 in 0.02",
+                      "tau_shear": "0.55..1.0", "tau_ghost": 1.0, "kT": 1e-4, "mlp": "off",
+                      "storage": "fp32 deviation f - w rho0, FP64 correlator sums", "sample_every": every,
+                      "fields": ["rho", "u_x", "u_y"], "parallelism": f"64 replicas x{world}",
+                      "l2": "inputs larger than L2 (%.2f GB state), no flush" % (2 * 9 * 4 * V / 1e9)}
+            kernel = "k_step_d2q9 (fused pull-stream/collide/noise, batched replicas)"
+        else:
+            config = {"workload": "d2q9_16384", "lattice": "D2Q9", "nx": p["nx"], "ny": p["ny"],
+                      "storage": "fp32 deviation f - w rho0, FP64 correlator sums",
+                      "tau_shear": 0.6, "tau_ghost": 1.0, "u0": list(p["u0"]), "kT": p["kT"],
+                      "mlp": "3-32-32-6 seeded random weights", "sample_every": every,
+                      "fields": ["rho", "u_x", "u_y"], "parallelism": f"replica x{world}",
+                      "l2": "inputs larger than L2 (%.1f GB state), no flush" % (2 * 9 * 4 * V / 1e9)}
+            kernel = KERNEL_NAME[engine]
         line = {
             "metric": "D2Q9 fluctuating-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "d2q9_16384", "lattice": "D2Q9", "nx": p["nx"], "ny": p["ny"],
-                       "storage": "fp32 deviation f - w rho0, FP64 correlator sums",
-                       "tau_shear": 0.6, "tau_ghost": 1.0, "u0": list(p["u0"]), "kT": p["kT"],
-                       "mlp": "3-32-32-6 seeded random weights", "sample_every": SAMPLE_EVERY,
-                       "fields": ["rho", "u_x", "u_y"], "parallelism": f"replica x{world}",
-                       "l2": "inputs larger than L2 (%.1f GB state), no flush" % (2 * 9 * 4 * V / 1e9)},
+            "config": config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_step_d2q9_tc (fused pull-stream/collide/noise, network on tcgen05)",
-                         "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms,
+                         "kernel": kernel, "alg_bytes_per_launch": ALG_BYTES_PER_SITE * V, "avg_launch_ms": step_ms,
                          "launch": {"vec": tuned[0], "grid_blocks_requested": tuned[1], "staged": tuned[2],
-                                    "block": 256}},
+                                    "engine": engine}},
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
         }
+        if finite is not None:
+            line["replicas_finite"] = {"all": all(finite), "unstable": [r for r, ok in enumerate(finite) if not ok]}
+        if acc is not None:
+            line["accuracy"] = acc
         print(json.dumps(line))
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -32,6 +32,20 @@ def test_clock_summary_median_and_reasons():
                "garbage line",
                "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
     s = c.summary()
-    assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert {k: s[k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")} == \
+        {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert s["gpu"] == c.id
     c.lines = []
     assert c.summary() is None
+
+
+def test_gpu_id_follows_visible_devices(monkeypatch):
+    # without a CUDA device the sampler names the visible device's own entry (a UUID or
+    # a physical index), never this process's ordinal when a mapping is given
+    b = _bench()
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1111-aaaa,GPU-2222-bbbb")
+    assert b.gpu_id(1) == "GPU-2222-bbbb"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,3")
+    assert b.gpu_id(0) == "5"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert b.gpu_id(0) == "0"

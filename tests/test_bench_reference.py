@@ -12,7 +12,8 @@ KEYS = {"impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_
 
 
 @pytest.mark.parametrize("args", [["--cpu-n", "32"], ["--workload", "d3q15_512", "--cpu-n", "8"],
-                                  ["--workload", "d3q19_512", "--cpu-n", "8"]])
+                                  ["--workload", "d3q19_512", "--cpu-n", "8"],
+                                  ["--workload", "sweep64", "--cpu-n", "16"]])
 def test_reference_arm_prints_one_json_line(args):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "20", "--warmup", "3"] + args
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600,
