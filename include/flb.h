@@ -292,6 +292,16 @@ int flb_set_graphs(flb_ctx* ctx, int enable);
  * FLB_EINVAL for a limit out of range.  Asynchronous. */
 int flb_probe_wait_timeout(flb_ctx* ctx, uint64_t limit_clocks);
 
+/* Bounds-checked debug build only (built with python -m paper_1010_1233_gb300.build
+ * --checked, which compiles every kernel with -DFLB_CHECK_BOUNDS): every global and
+ * shared-memory index the step, sampling and 3D kernels compute is checked against its
+ * array, and a violating access is counted and skipped (no trap).  Synchronises the
+ * device, then returns in *violations the count since the last clear and in *first_site
+ * the code of the first violating site (0: none; the codes are listed with FLB_INB in
+ * the sources).  clear != 0 resets the counters.  FLB_ESTATE from a library built
+ * without the checks. */
+int flb_debug_bounds(uint64_t* violations, uint32_t* first_site, int clear);
+
 /* Destroy the context (does not free the caller's workspace). */
 void flb_destroy(flb_ctx* ctx);
 

@@ -9,6 +9,10 @@ from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_size_t, c_uint1
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libflb.so")
+# the bounds-checked debug build (build.py --checked); chosen with FLB_CHECKED=1
+CHECKED_LIB_PATH = os.path.join(HERE, "libflb_checked.so")
+if os.environ.get("FLB_CHECKED") == "1":
+    LIB_PATH = CHECKED_LIB_PATH
 
 FLB_OK, FLB_EINVAL, FLB_ENOMEM, FLB_ECUDA, FLB_EUNSTABLE, FLB_ETIMEOUT, FLB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 FLB_D1Q3, FLB_D2Q9, FLB_D3Q15, FLB_D3Q19 = 1, 2, 3, 4
@@ -64,6 +68,7 @@ _SIGS = {
     "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_set_graphs": (c_int, [c_void_p, c_int]),
     "flb_probe_wait_timeout": (c_int, [c_void_p, c_uint64]),
+    "flb_debug_bounds": (c_int, [POINTER(c_uint64), POINTER(c_uint32), c_int]),
     "flb_destroy": (None, [c_void_p]),
     "flb_last_error": (ctypes.c_char_p, []),
     "flb_spectra_scratch_bytes": (c_int, [c_int, c_int, c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),

@@ -1,11 +1,13 @@
 """Build libflb.so (the CUDA kernels and the C ABI of include/flb.h) in-tree for sm_103a.
 
-Usage: python -m paper_1010_1233_gb300.build  [--force]
+Usage: python -m paper_1010_1233_gb300.build  [--force] [--checked]
 
 Each .cu translation unit is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a), then linked into a shared library
 next to this file.  Rebuilds only when a source or header is newer than the
-library.  No torch headers are involved.
+library.  No torch headers are involved.  --checked builds the bounds-checked
+debug variant instead (-DFLB_CHECK_BOUNDS, libflb_checked.so; select it with
+FLB_CHECKED=1).
 """
 import concurrent.futures as cf
 import os
@@ -19,6 +21,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflb.so")
+OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libflb_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -39,15 +43,15 @@ def _deps():
     return deps + [os.path.abspath(__file__)]
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(nvcc, src, extra):
-    obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))
+def _compile(nvcc, src, extra, out_dir=OUT_DIR):
+    obj = os.path.join(out_dir, os.path.basename(src).replace(".cu", ".o"))
     cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-I", INCLUDE, "-c", src, "-o", obj] + extra
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -56,27 +60,29 @@ def _compile(nvcc, src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, ptxas_info=False):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, ptxas_info=False, checked=False):
+    lib, out_dir = (LIB_CHECKED, OUT_DIR_CHECKED) if checked else (LIB, OUT_DIR)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = nvcc_path()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, extra), sources()))
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DFLB_CHECK_BOUNDS"] if checked else [])
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda s: _compile(nvcc, s, extra, out_dir), sources()))
     objs = [o for o, _ in results]
     if verbose or ptxas_info:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -638,6 +638,19 @@ static int64_t time_corr_layout(const flb_ctx* c, int n_lags, int n_k, std::vect
   return off;
 }
 
+// Registry of the bounds-check counters of the translation units (checked build only).
+namespace flb {
+struct OobEntry { OobRead read; OobClear clear; };
+static std::vector<OobEntry>& oob_registry() {
+  static std::vector<OobEntry> v;
+  return v;
+}
+bool register_oob_counter(OobRead read, OobClear clear) {
+  oob_registry().push_back({read, clear});
+  return true;
+}
+}  // namespace flb
+
 extern "C" {
 
 static void drop_graphs(flb_ctx* c);
@@ -1363,6 +1376,28 @@ int flb_get_step_config(flb_ctx* c, int* vec, int* grid_blocks, int* staged) {
   *vec = c->L.vec;
   *staged = c->L.staged;
   *grid_blocks = (int)std::min<int64_t>(c->L.n_vb_step, c->step_grid > 0 ? (int64_t)c->step_grid : (int64_t)c->sms * 16);
+  return FLB_OK;
+}
+
+int flb_debug_bounds(uint64_t* violations, uint32_t* first_site, int clear) {
+  if (!violations || !first_site) return set_error(FLB_EINVAL, "NULL argument");
+  *violations = 0;
+  *first_site = 0;
+  if (oob_registry().empty())
+    return set_error(FLB_ESTATE, "this library was built without bounds checks (build with --checked)");
+  int rc = cuda_check(cudaDeviceSynchronize(), "bounds counters");
+  if (rc) return rc;
+  for (const OobEntry& e : oob_registry()) {
+    unsigned int v[2] = {0u, 0u};
+    rc = cuda_check((cudaError_t)e.read(v), "read bounds counters");
+    if (rc) return rc;
+    *violations += v[0];
+    if (!*first_site && v[1]) *first_site = v[1];
+    if (clear) {
+      rc = cuda_check((cudaError_t)e.clear(), "clear bounds counters");
+      if (rc) return rc;
+    }
+  }
   return FLB_OK;
 }
 

@@ -15,6 +15,7 @@ namespace flb {
 template <typename R, bool DEV, bool SAMPLE>
 __device__ __forceinline__ void d1q3_site(const ReplicaDesc& d, const R* __restrict__ src, R* __restrict__ dst,
                                           R* __restrict__ fields, int nx, int x, uint32_t step) {
+  if (!FLB_INB(x >= 0 && x < nx, 111)) return;
   const R g0 = src[x];
   const R g1 = src[nx + (x == 0 ? nx - 1 : x - 1)];
   const R g2 = src[2 * nx + (x == nx - 1 ? 0 : x + 1)];
@@ -28,6 +29,7 @@ __device__ __forceinline__ void d1q3_site(const ReplicaDesc& d, const R* __restr
   if constexpr (SAMPLE) {
     const R mom[3] = {sum, (R)1.7320508075688772935 * j, M2};
     for (int slot = 0; slot < (int)d.n_fields; ++slot) {
+      if (!FLB_INB(slot < kMaxFields, 111)) break;
       const int fid = d.field_id[slot];
       const R val = fid < 3 ? mom[fid] - coef<R>(d, kCoMref + fid) : u - coef<R>(d, kCoU0x);
       fields[(int64_t)slot * nx + x] = val;

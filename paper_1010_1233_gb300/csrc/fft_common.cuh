@@ -99,16 +99,18 @@ __device__ __forceinline__ void dit_pass(C<R>* data, int logn, int n_fft, int se
     const int i0 = ((q >> s) << (s + RS)) | low;
     C<R>* d = data + k * seq_stride;
     C<R> v[G];
+    // (checked build: the group's last element inside the sequence, a valid sequence)
+    const bool ok = FLB_INB(k < n_fft && i0 + ((G - 1) << s) < (1 << logn), 141);
 #pragma unroll
     for (int t = 0; t < G; ++t) {
       const int e = i0 + (t << s);
-      v[t] = d[e + (e >> pad_shift)];
+      v[t] = ok ? d[e + (e >> pad_shift)] : C<R>{};
     }
     dit_group<R, RS>(v, logn, s, low, tw, tw_stride);
 #pragma unroll
     for (int t = 0; t < G; ++t) {
       const int e = i0 + (t << s);
-      d[e + (e >> pad_shift)] = v[t];
+      if (ok) d[e + (e >> pad_shift)] = v[t];
     }
     q += dq;                                         // g += blockDim.x
     k += dk;

@@ -213,4 +213,37 @@ inline int column_split(int precision, int F, int ny) {
 // host-side helpers (api.cu)
 int set_error(int code, const char* fmt, ...);
 
+// ---------------------------------------------------------------------------
+// Bounds-checked debug build (compiled with -DFLB_CHECK_BOUNDS, python -m
+// paper_1010_1233_gb300.build --checked): at every global and shared-memory access
+// whose index the kernels compute, FLB_INB(condition, site) checks the index against
+// its array; a violation is counted, the first violating site's code is kept, and the
+// access is skipped (no trap, no fault).  Each translation unit has its own counters
+// (the library is compiled without relocatable device code); they register a reader
+// with api.cu, and flb_debug_bounds adds them up.  In the normal build FLB_INB is the
+// constant true and costs nothing.
+using OobRead = int (*)(unsigned int* out2);
+using OobClear = int (*)();
+bool register_oob_counter(OobRead read, OobClear clear);
+
+#ifdef FLB_CHECK_BOUNDS
+static __device__ unsigned int g_flb_oob[2];          // violations, first site code
+__device__ __forceinline__ bool flb_inb(bool ok, int site) {
+  if (!ok) {
+    atomicAdd(&g_flb_oob[0], 1u);
+    atomicCAS(&g_flb_oob[1], 0u, (unsigned int)site);
+  }
+  return ok;
+}
+static int flb_oob_read(unsigned int* out2) { return (int)cudaMemcpyFromSymbol(out2, g_flb_oob, sizeof(g_flb_oob)); }
+static int flb_oob_clear() {
+  const unsigned int z[2] = {0u, 0u};
+  return (int)cudaMemcpyToSymbol(g_flb_oob, z, sizeof(z));
+}
+static const bool flb_oob_registered = register_oob_counter(flb_oob_read, flb_oob_clear);
+#define FLB_INB(cond, site) flb_inb((cond), (site))
+#else
+#define FLB_INB(cond, site) true
+#endif
+
 }  // namespace flb

@@ -61,12 +61,18 @@ __device__ __forceinline__ void pull_3d(const R* __restrict__ src, int64_t vol, 
     ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
     zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
     const R* row = src + i * vol + ((int64_t)zs * ny + ys) * nx;
-    VecIO<R, VEC>::ld(row + x0, v[i]);
+    if (FLB_INB(ys >= 0 && ys < ny && zs >= 0 && zs < nz && x0 >= 0 && x0 + VEC <= nx, 171))
+      VecIO<R, VEC>::ld(row + x0, v[i]);
+#ifdef FLB_CHECK_BOUNDS
+    else for (int s = 0; s < VEC; ++s) v[i][s] = (R)0;
+#endif
     e[i] = (R)0;
     if (v3x<Q>(i) == 1) {
-      if (!u.left_in_warp) e[i] = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
+      const int xe = x0 == 0 ? nx - 1 : x0 - 1;
+      if (!u.left_in_warp && FLB_INB(xe >= 0 && xe < nx, 172)) e[i] = __ldg(row + xe);
     } else if (v3x<Q>(i) == -1) {
-      if (!u.right_in_warp) e[i] = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
+      const int xe = x0 + VEC == nx ? 0 : x0 + VEC;
+      if (!u.right_in_warp && FLB_INB(xe >= 0 && xe < nx, 172)) e[i] = __ldg(row + xe);
     }
   }
 #pragma unroll
@@ -361,7 +367,7 @@ k_step_3d(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Replica
       if constexpr (SAMPLE) {
         // the site's sampled fields, stored at once (scalar stores; the lanes of a warp
         // cover contiguous rows of each field plane)
-        if (u.active)
+        if (u.active && FLB_INB(off + s < vol, 174))
           for (int slot = 0; slot < (int)d.n_fields; ++slot) {
             const int fid = d.field_id[slot];
             R val = fl[0];
@@ -371,7 +377,7 @@ k_step_3d(const ReplicaDesc* __restrict__ descs, const __grid_constant__ Replica
           }
       }
     }
-    if (!u.active) continue;
+    if (!u.active || !FLB_INB(off >= 0 && off + VEC <= vol, 173)) continue;
 #pragma unroll
     for (int i = 0; i < Q; ++i) VecIO<R, VEC>::st(dst + i * vol + off, f[i]);
   }

@@ -88,7 +88,8 @@ k_d1q3_fused(const ReplicaDesc* __restrict__ descs, char* __restrict__ ws, uint6
           dit_group<R, 3>(v, logn, 0, 0, tw, 1);
           const int i0 = brev(x0, logn - 3) << 3;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) z[i0 + q + ((i0 + q) >> ps)] = v[q];
+          for (int q = 0; q < 8; ++q)
+            if (FLB_INB(i0 + q < nx, 181)) z[i0 + q + ((i0 + q) >> ps)] = v[q];
         }
         __syncthreads();
         dit_fft<R, sizeof(R) == 4 ? 4 : 3>(z, logn, 1, 0, tw, 1, ps, 3);
@@ -98,7 +99,7 @@ k_d1q3_fused(const ReplicaDesc* __restrict__ descs, char* __restrict__ ws, uint6
           v.x = xa[x];
           v.y = has_b ? xb[x] : (R)0;
           const int i = brev(x, logn);
-          z[i + (i >> ps)] = v;
+          if (FLB_INB(i < nx, 181)) z[i + (i >> ps)] = v;
         }
         __syncthreads();
         dit_fft<R>(z, logn, 1, 0, tw, 1, ps);
@@ -126,6 +127,7 @@ k_d1q3_fused(const ReplicaDesc* __restrict__ descs, char* __restrict__ ws, uint6
     for (int it = tid; it < items; it += nt) {
       const int pr = it / hn1, kx = it - pr * hn1;
       const int a = d.pair_a[pr], b = d.pair_b[pr];
+      if (!FLB_INB(pr < d.n_pairs && a < F && b < F, 182)) continue;
       const C<R> Xa = X[(size_t)a * hn1 + kx];
       const C<R> Xb = X[(size_t)b * hn1 + kx];
       if (a == b) {

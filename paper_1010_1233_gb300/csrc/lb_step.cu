@@ -173,7 +173,7 @@ __global__ void k_init(const ReplicaDesc* __restrict__ descs, int r, char* __res
         f[2] += (1.0 / 6.0) * (M[0] - S3 * M[1] + 2.0 * IS2 * M[2]);
       }
     }
-    for (int i = 0; i < d.q; ++i) {
+    for (int i = 0; i < d.q && FLB_INB(d.q <= 9, 191); ++i) {
       double v = f[i];
       if (DEV) v -= feq0[kFeqW + i];      // w_i rho0
       dst[i * V + s] = (R)v;

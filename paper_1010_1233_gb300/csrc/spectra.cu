@@ -75,13 +75,15 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int x = x0 + (((t & 1) << 2) | (t & 2) | ((t >> 2) & 1)) * n8;
-          v[t].x = xa[x];
-          v[t].y = has_b ? xb[x] : (R)0;
+          const bool in = FLB_INB(x >= 0 && x < nx, 131);
+          v[t].x = in ? xa[x] : (R)0;
+          v[t].y = has_b && in ? xb[x] : (R)0;
         }
         dit_group<R, 3>(v, logn, 0, 0, tw, 1);
         const int i0 = brev(x0, logn - 3) << 3;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) z[i0 + t + ((i0 + t) >> ps)] = v[t];
+        for (int t = 0; t < 8; ++t)
+          if (FLB_INB(i0 + t < nx, 132)) z[i0 + t + ((i0 + t) >> ps)] = v[t];
       }
       __syncthreads();
       dit_fft<R, sizeof(R) == 4 ? 4 : 3>(z, logn, 1, 0, tw, 1, ps, 3);   // FP32: four stages per pass
@@ -89,7 +91,7 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
       for (int x = threadIdx.x; x < nx; x += blockDim.x) {
         C<R> v; v.x = xa[x]; v.y = has_b ? xb[x] : (R)0;
         const int i = brev(x, logn);
-        z[i + (i >> ps)] = v;
+        if (FLB_INB(i < nx, 132)) z[i + (i >> ps)] = v;
       }
       __syncthreads();
       dit_fft<R>(z, logn, 1, 0, tw, 1, ps);
@@ -99,7 +101,9 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
     C<R>* ra = spec + fa * fplane + (int64_t)ya * d.wpitch;
     C<R>* rb = spec + fb * fplane + (int64_t)yb * d.wpitch;
     const int hn = nx >> 1;
-    for (int k = threadIdx.x; k <= hn; k += blockDim.x) {
+    const bool rows_ok = FLB_INB(fa < (int)d.n_fields && ya < d.ny && (!has_b || (fb < (int)d.n_fields && yb < d.ny)) &&
+                                 hn < d.wpitch, 133);
+    for (int k = threadIdx.x; k <= hn && rows_ok; k += blockDim.x) {
       const int km = (nx - k) & (nx - 1);
       const C<R> Z = z[k + (k >> ps)];
       const C<R> Zm = z[km + (km >> ps)];
@@ -163,13 +167,15 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
         const int i = i0 + u * blockDim.x;
         const int c = i & (ncol - 1), y1 = (i >> lc) & (n1 - 1), f = i >> (lc + logn1);
         v[u].x = (R)0; v[u].y = (R)0;
-        if (i < total && c < ncl) v[u] = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
+        if (i < total && c < ncl && FLB_INB(f < F && n2 * y1 + y2 < d.ny && kx0 + c < d.half_nx, 151))
+          v[u] = spec[f * fplane + (int64_t)(n2 * y1 + y2) * d.wpitch + kx0 + c];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u * blockDim.x;
         const int c = i & (ncol - 1), y1 = (i >> lc) & (n1 - 1), f = i >> (lc + logn1);
-        if (i < total) s[(f * ncol + c) * (n1 + 1) + brev(y1, logn1)] = v[u];
+        if (i < total && FLB_INB(f < F && c < ncol && brev(y1, logn1) < n1, 152))
+          s[(f * ncol + c) * (n1 + 1) + brev(y1, logn1)] = v[u];
       }
     }
     __syncthreads();
@@ -180,7 +186,7 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
       const int c = i & (ncol - 1);
       const int k1 = (i >> lc) & (n1 - 1);
       const int f = i >> (lc + logn1);
-      if (c >= ncl) continue;
+      if (c >= ncl || !FLB_INB(f < F && n2 * k1 + y2 < d.ny && kx0 + c < d.half_nx, 151)) continue;
       const int e = y2 * k1;                       // < ny
       C<R> w = tw[e < hn ? e : e - hn];
       if (e >= hn) { w.x = -w.x; w.y = -w.y; }
@@ -229,13 +235,15 @@ k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
         const int i = i0 + u * blockDim.x;
         const int c = i & (ncol - 1), y2 = (i >> lc) & (n2 - 1), f = i >> (lc + logn2);
         v[u].x = (R)0; v[u].y = (R)0;
-        if (i < total && c < ncl) v[u] = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
+        if (i < total && c < ncl && FLB_INB(f < F && n2 * k1 + y2 < d.ny && kx0 + c < d.half_nx, 161))
+          v[u] = spec[f * fplane + (int64_t)(n2 * k1 + y2) * d.wpitch + kx0 + c];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u * blockDim.x;
         const int c = i & (ncol - 1), y2 = (i >> lc) & (n2 - 1), f = i >> (lc + logn2);
-        if (i < total) s[(f * ncol + c) * (n2 + 1) + brev(y2, logn2)] = v[u];
+        if (i < total && FLB_INB(f < F && c < ncol && brev(y2, logn2) < n2, 162))
+          s[(f * ncol + c) * (n2 + 1) + brev(y2, logn2)] = v[u];
       }
     }
     __syncthreads();
@@ -257,6 +265,11 @@ k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
         if (it >= items || c >= ncl) continue;
         pt[u] = d.acc_ncol ? ((int64_t)(k1 * tiles + (kx0 >> lc)) * n2 + k2) * ncol + c   // contiguous per block
                            : (int64_t)(k1 + n1 * k2) * d.half_nx + kx0 + c;
+        if (!FLB_INB(pr < d.n_pairs && d.pair_a[pr] < F && d.pair_b[pr] < F &&
+                     pt[u] < (d.acc_ncol ? (int64_t)d.ny * tiles * ncol : (int64_t)d.ny * d.half_nx), 163)) {
+          pt[u] = -1;
+          continue;
+        }
         if (d.pair_a[pr] == d.pair_b[pr]) acc[u].x = reinterpret_cast<const double*>(ws + d.pair_off[pr])[pt[u]];
         else acc[u] = reinterpret_cast<const double2*>(ws + d.pair_off[pr])[pt[u]];
       }
@@ -288,6 +301,7 @@ k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
         const int j = i % tc.n_k, f = i / tc.n_k;
         const int kx = tc.kx[j], ky = tc.ky[j];
         if ((ky & (n1 - 1)) != k1 || kx < kx0 || kx >= kx0 + ncl) continue;
+        if (!FLB_INB(slot >= 0 && slot < tc.n_lags && (ky >> logn1) < n2, 164)) continue;
         const C<R> X = s[(f * ncol + (kx - kx0)) * (n2 + 1) + (ky >> logn1)];
         ring[((int64_t)slot * F + f) * tc.n_k + j] = make_double2((double)X.x, (double)X.y);
       }

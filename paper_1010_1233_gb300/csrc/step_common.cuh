@@ -126,12 +126,17 @@ __device__ __forceinline__ void pull_issue(const R* __restrict__ src, int64_t pl
     int ys = u.y - vel_y(i);
     ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
     const R* row = src + i * plane + (int64_t)ys * nx;
-    VecIO<R, VEC>::ld(row + x0, raw.v[i]);
+    if (FLB_INB(ys >= 0 && ys < ny && x0 >= 0 && x0 + VEC <= nx, 101)) VecIO<R, VEC>::ld(row + x0, raw.v[i]);
+#ifdef FLB_CHECK_BOUNDS
+    else for (int s = 0; s < VEC; ++s) raw.v[i][s] = (R)0;
+#endif
     raw.e[i] = (R)0;
     if (vel_x(i) == 1) {                          // needs x0 - 1
-      if (!u.left_in_warp) raw.e[i] = __ldg(row + (x0 == 0 ? nx - 1 : x0 - 1));
+      const int xe = x0 == 0 ? nx - 1 : x0 - 1;
+      if (!u.left_in_warp && FLB_INB(xe >= 0 && xe < nx, 102)) raw.e[i] = __ldg(row + xe);
     } else if (vel_x(i) == -1) {                  // needs x0 + VEC
-      if (!u.right_in_warp) raw.e[i] = __ldg(row + (x0 + VEC == nx ? 0 : x0 + VEC));
+      const int xe = x0 + VEC == nx ? 0 : x0 + VEC;
+      if (!u.right_in_warp && FLB_INB(xe >= 0 && xe < nx, 102)) raw.e[i] = __ldg(row + xe);
     }
   }
 }
@@ -429,12 +434,15 @@ __device__ __forceinline__ void store_d2q9(const ReplicaDesc& d, char* __restric
                                            int64_t plane, const UnitPos& u, const R (&f)[9][VEC],
                                            const R (&fld)[kMaxFields][VEC]) {
   if (!u.active) return;
+  if (!FLB_INB(u.y >= 0 && u.y < d.ny && u.x0 >= 0 && u.x0 + VEC <= d.nx && plane == (int64_t)d.nx * d.ny, 103))
+    return;
   const int64_t off = (int64_t)u.y * d.nx + u.x0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) VecIO<R, VEC>::st(dst + i * plane + off, f[i]);
   if constexpr (SAMPLE) {
     R* fields = reinterpret_cast<R*>(ws + d.off_fields);
     for (int slot = 0; slot < (int)d.n_fields; ++slot) {
+      if (!FLB_INB(slot < kMaxFields && d.field_id[slot] >= 0 && d.field_id[slot] < kMaxFields, 104)) continue;
       const int fid = d.field_id[slot];
       R v[VEC];
 #pragma unroll

@@ -134,14 +134,15 @@ struct WarpNet {
       const float2 o0 = Lane<float2>::add(make_float2(d3[0], d3[1]), c3p);
       const float2 o1 = Lane<float2>::add(make_float2(d3[2], d3[3]), c3p);
       // site (row g, slot) -> scr[slot][g][0][...], site (row g + 8, slot) -> scr[slot][g][1][...]
-      if (c < 3) {
+      if (c < 3 && FLB_INB((slot * 8 + g) * 12 + 2 * c + 7 < 4 * 8 * 12, 121)) {
         float* p = scr + (slot * 8 + g) * 12 + 2 * c;
         *reinterpret_cast<float2*>(p) = o0;
         *reinterpret_cast<float2*>(p + 6) = o1;
       }
     }
     __syncwarp();
-    const float4* q = reinterpret_cast<const float4*>(scr + (c * 8 + g) * 12);
+    const int qi = FLB_INB((c * 8 + g) * 12 + 12 <= 4 * 8 * 12, 122) ? (c * 8 + g) * 12 : 0;
+    const float4* q = reinterpret_cast<const float4*>(scr + qi);
     const float4 q0 = q[0], q1 = q[1], q2 = q[2];
     s0[0] = q0.x; s0[1] = q0.y; s0[2] = q0.z; s0[3] = q0.w; s0[4] = q1.x; s0[5] = q1.y;
     s1[0] = q1.z; s1[1] = q1.w; s1[2] = q2.x; s1[3] = q2.y; s1[4] = q2.z; s1[5] = q2.w;

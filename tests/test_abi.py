@@ -139,3 +139,13 @@ def test_d3q19_workspace_and_validation(lib):
     assert rc == 0
     rc, _ = _ws([W.replica3(8, 8, 8), W.replica3(8, 8, 8, lattice="D3Q19")])       # mixed lattices
     assert rc == L.FLB_EINVAL
+
+
+def test_bounds_counters_only_in_the_checked_build(lib):
+    # the normal build carries no index checks: the counter query answers FLB_ESTATE
+    # without touching the device; NULL arguments are rejected first
+    n, site = ctypes.c_uint64(7), ctypes.c_uint32(7)
+    assert lib.flb_debug_bounds(None, ctypes.byref(site), 0) == L.FLB_EINVAL
+    assert lib.flb_debug_bounds(ctypes.byref(n), ctypes.byref(site), 1) == L.FLB_ESTATE
+    assert n.value == 0 and site.value == 0
+    assert b"--checked" in lib.flb_last_error()
