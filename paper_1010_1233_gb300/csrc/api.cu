@@ -35,13 +35,14 @@ int fft_rows_smem(int precision, int nx);
 int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc);
+                     const TimeCorr& tc, int paths, int nslots);
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                       int paths, int slot);
 void launch_wait_probe(DevStatus* status, long long limit, cudaStream_t st);   // lb_step_tc.cu
 // D1Q3 runs of steps with their sampling in one launch (lb_d1q3_fused.cu)
 size_t d1q3_fused_smem(int precision, int nx, int F);
@@ -127,6 +128,8 @@ struct Layout {
   int64_t n_vb_step = 0, n_vb_rows = 0, n_vb_cols = 0, n_vb_cols_a = 0;
   std::vector<int64_t> vb_step, vb_rows, vb_cols, vb_cols_a;
   int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
+  int cols_a_paths = 0, cols_paths = 0;   // column-pass kernels the replicas need (cols16_b)
+  int fold = 1;               // 2: two spectrum slots, two samples per accumulation pass
   int staged = 0;             // 1: the step kernel of lb_step_bulk.cu (tiles of 256 vec sites)
   bool any_fields = false;
 };
@@ -409,6 +412,25 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   if (maxF) {
     L.ncol = kColsMax;
     while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
+    // the column-pass kernels: register-resident ones for FP32 columns of 16 .. 256
+    int maxn2 = 1;
+    for (const ReplicaDesc& d : L.desc) {
+      if (!d.n_pairs) continue;
+      const int b2 = precision == FLB_FP64 ? 0 : cols16_b(d.ny >> d.log2n1);
+      L.cols_paths |= b2 ? b2 : kColsGeneric;
+      maxn2 = std::max(maxn2, d.ny >> d.log2n1);
+      if (d.log2n1) {
+        const int b1 = precision == FLB_FP64 ? 0 : cols16_b(1 << d.log2n1);
+        L.cols_a_paths |= b1 ? b1 : kColsGeneric;
+      }
+    }
+    // two samples per pass over the FP32 sums when every sampled replica has register-
+    // resident columns and the two samples' tiles of at least 4 columns fit 4 blocks per SM
+    if (!(L.cols_paths & kColsGeneric)) {
+      int nc = std::min(L.ncol, 8);
+      while (nc >= 4 && fft_cols16_smem(maxF, maxn2, nc, 2) > kFoldSmemBudget) nc >>= 1;
+      if (nc >= 4) { L.fold = 2; L.ncol = nc; }
+    }
   }
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
@@ -417,7 +439,9 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     d.off_pop[1] = off; off = align256(off + L.q * V * rs);
     if (d.n_fields) { d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs); }
     if (d.n_pairs) {
-      d.off_spec = off; off = align256(off + (int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
+      const int64_t spec_bytes = align256((int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
+      d.off_spec = off; off += L.fold * spec_bytes;
+      d.spec_slot = L.fold == 2 ? spec_bytes : 0;
       d.acc_ncol = L.ncol;
       const int64_t padded_kx = (d.half_nx + L.ncol - 1) / L.ncol * L.ncol;
       for (int pr = 0; pr < d.n_pairs; ++pr) {
@@ -436,6 +460,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.rows_smem = fft_rows_smem(precision, maxnx);
     L.rows_block = std::max(32, std::min(kRowsBlockMax, maxnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
+    if (L.fold == 2) L.cols_smem = std::max(L.cols_smem, fft_cols16_smem(maxF, maxlen, L.ncol, 2));
   }
   plan_step(lat, L.vec, 0, L);
   for (int r = 0; r < n; ++r) {
@@ -447,7 +472,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
       const int64_t tiles = (d.half_nx + L.ncol - 1) / L.ncol;
       L.n_vb_rows += ((int64_t)d.n_fields * d.ny + 1) / 2;           // two row units per block
       L.n_vb_cols += tiles << d.log2n1;                       // (k1, tile)
-      if (d.log2n1) L.n_vb_cols_a += tiles * (d.ny >> d.log2n1);   // (y2, tile)
+      L.n_vb_cols_a += cols_a_blocks(precision, d.log2n1, (int)d.n_fields, d.half_nx, d.ny, L.ncol);
     }
   }
   L.off_descs = off; off = align256(off + n * (int64_t)sizeof(ReplicaDesc));
@@ -537,6 +562,7 @@ struct flb_ctx {
   char* ws = nullptr;
   cudaStream_t stream = nullptr;
   uint64_t step = 0, n_samples = 0;
+  int pending = 0;            // samples in spectrum slots whose products are not yet in the sums
   int sms = 1;
   int step_grid = 0;          // 0: min(virtual blocks, 16 x SMs)
   bool mlp_on = false;
@@ -888,6 +914,23 @@ static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S
   else launch_step(c->lattice, c->precision, vec, S, sample, c->mlp_on, st);
 }
 
+// The accumulation pass (pass 2b and the pair sums, then the time correlators) over the
+// samples waiting in the spectrum slots, slot 0 first; nothing when none is waiting.
+static void flush_samples(flb_ctx* c, const StepLaunch& S, cudaStream_t st) {
+  const Layout& L = c->L;
+  if (!c->pending) return;
+  const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
+  launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
+                  L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st, c->tc, L.cols_paths,
+                  c->pending);
+  c->pending = 0;
+  if (c->tc.base) {
+    int maxF = 0;
+    for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
+    launch_time_corr(S.descs, c->n, maxF, c->tc, st);
+  }
+}
+
 static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) {
   NvtxRange range(sample ? "flb step + sample" : "flb step");
   const Layout& L = c->L;
@@ -901,21 +944,21 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
       launch_time_corr(S.descs, c->n, maxF, c->tc, st);
     }
   } else if (sample) {
+    // the row and inner column transforms into the free spectrum slot; the accumulation
+    // pass once both slots hold a sample (or right away without folding: one slot, or
+    // time correlators, which take their ring entries one sample at a time)
+    const bool fold = L.fold == 2 && !c->tc.base;
+    const int slot = fold ? c->pending : 0;
     const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
-    const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
     const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
     launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
-                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st);
+                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st, slot);
     if (L.n_vb_cols_a)
       launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
-                        L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st);
-    launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
-                    L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st, c->tc);
-    if (c->tc.base) {
-      int maxF = 0;
-      for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
-      launch_time_corr(S.descs, c->n, maxF, c->tc, st);
-    }
+                        L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st,
+                        L.cols_a_paths, slot);
+    c->pending = slot + 1;
+    if (!fold || c->pending == 2) flush_samples(c, S, st);
   }
 }
 
@@ -963,6 +1006,7 @@ static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t
     S.step = o;
     issue_step(c, S, every && o % every == 0, c->cap_stream);
   }
+  flush_samples(c, S, c->cap_stream);           // a chunk leaves no sample waiting
   launch_advance_step(reinterpret_cast<uint64_t*>(c->ws + c->L.off_stepdev), len, c->cap_stream);
   cudaGraph_t graph = nullptr;
   rc = cuda_check(cudaStreamEndCapture(c->cap_stream, &graph), "end capture");
@@ -1013,14 +1057,17 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
   // captured graph; steps before the first aligned chunk and after the last one are
   // issued directly
   const uint32_t every = sampling ? sample_every : 0;
-  const uint32_t len = !sampling ? kGraphChunk
-                       : (sample_every >= kGraphChunk ? sample_every
-                                                      : sample_every * ((kGraphChunk + sample_every - 1) / sample_every));
+  // samples per chunk: enough for kGraphChunk steps, even when samples are folded in pairs
+  uint64_t per_chunk = sampling ? (kGraphChunk + sample_every - 1) / sample_every : 0;
+  if (sampling && c->L.fold == 2 && !c->tc.base) per_chunk += per_chunk & 1;
+  const uint64_t len64 = sampling ? per_chunk * sample_every : kGraphChunk;
   uint64_t i = 0;
-  if (c->use_graphs && n_steps >= 2 * (uint64_t)len && len <= kMaxGraphChunk) {
+  if (c->use_graphs && len64 <= kMaxGraphChunk && n_steps >= 2 * len64) {
+    const uint32_t len = (uint32_t)len64;
     while (i < n_steps && (c->step % len) != 0) { plain(); ++i; }
     const uint64_t chunks = (n_steps - i) / len;
     if (chunks) {
+      flush_samples(c, S, c->stream);            // the chunks start with no sample waiting
       cudaGraphExec_t exec = nullptr;
       int rc = chunk_graph(c, len, every, &exec);
       if (rc) return rc;
@@ -1036,6 +1083,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
     }
   }
   while (i < n_steps) { plain(); ++i; }
+  flush_samples(c, S, c->stream);                // a run leaves no sample waiting
   return cuda_check(cudaGetLastError(), "flb_run launch");
 }
 

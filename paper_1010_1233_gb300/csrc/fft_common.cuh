@@ -8,20 +8,29 @@ namespace flb {
 
 template <typename R> using C = typename vec2_of<R>::type;
 
+// the replica of virtual block vb (vb_begin: each replica's first block, ascending)
+__device__ __forceinline__ int find_rep(const int64_t* vb_begin, int n_reps, int64_t vb) {
+  int lo = 0, hi = n_reps - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (vb_begin[mid] <= vb) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Exact widening to FP64 with integer operations (GB300's FP64 pipe is slow, and the
-// column pass is bound by it): a normal float's sign, exponent (rebiased by 1023 - 127)
-// and significand placed in the double's fields; zero and subnormal floats give a signed
-// zero (a subnormal product is below 1.2e-38 and cannot change an FP64 sum of such
-// correlators), infinities and NaN stay infinities and NaN.
+// accumulation pass is bound by it), on the two 32-bit halves of the double: the high
+// word takes the sign, the exponent rebiased by 1023 - 127 = 896 (0x380 << 20; 0x7FF for
+// infinities and NaN) and the top 20 significand bits, the low word the last 3.  Zero
+// and subnormal floats give a signed zero (a subnormal product is below 1.2e-38 and
+// cannot change an FP64 sum of such correlators).
 __device__ __forceinline__ double widen(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t e = (b >> 23) & 0xFFu;
-  const uint64_t sign = (uint64_t)(b >> 31) << 63;
-  uint64_t bits;
-  if (e == 0u) bits = sign;
-  else if (e == 0xFFu) bits = sign | (0x7FFull << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
-  else bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)bits);
+  const uint32_t b = __float_as_uint(x), a = b & 0x7FFFFFFFu;
+  uint32_t hi = (a >> 3) + (a >= 0x7F800000u ? 0x70000000u : 0x38000000u);
+  uint32_t lo = b << 29;
+  if (a < 0x00800000u) { hi = 0u; lo = 0u; }
+  hi |= b & 0x80000000u;
+  return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 

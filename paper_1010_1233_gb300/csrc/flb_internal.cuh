@@ -53,6 +53,8 @@ struct ReplicaDesc {
   int64_t off_pop[2];               // population buffers (ping-pong)
   int64_t off_fields;               // [n_fields][nz][ny][nx] Real
   int64_t off_spec;                 // [n_fields][ny][wpitch] complex Real (row-transformed)
+  int64_t spec_slot;                // bytes from spectrum slot 0 to slot 1 (two samples folded
+                                    // into one accumulation pass; 0: one slot)
   int64_t off_mean0;                // [n_fields] double: sum over samples of X(k=0)
   int64_t off_tw_x, off_tw_y;       // twiddles exp(-2 pi i m / n), m < n/2, complex Real
   int32_t half_nx;                  // nx / 2 + 1
@@ -202,6 +204,30 @@ constexpr int kColsBlock = 256;
 #define FLB_COLS_MAX 16
 #endif
 constexpr int kColsMax = FLB_COLS_MAX;   // widest column tile (halved until it fits the budget)
+// B of the register-resident FP32 column pass (spectra_cols.cu) for a column of length
+// len = 16 B, B = 1, 2, 4, 8, 16; 0 if there is none (the shared-memory pass of spectra.cu).
+// The launches take a mask of the passes they need: bit B for each B, kColsGeneric for
+// the shared-memory pass.
+__host__ __device__ __forceinline__ int cols16_b(int len) {
+  return (len >= 16 && len <= 256 && (len & (len - 1)) == 0) ? len >> 4 : 0;
+}
+constexpr int kColsGeneric = 32;
+// The register-resident pass-2a kernel takes tiles of kColsA16 columns of one field
+// (pass 2a needs no field pairs); the shared-memory kernel tiles of the layout's ncol
+// columns of all fields.  Virtual blocks of pass 2a of a replica:
+constexpr int kColsA16 = 16;
+// shared memory of the register-resident pass 2b: nslots samples' tiles of F fields x
+// ncol columns of length L (rows padded to L + 1) and a table of L roots of unity
+inline int fft_cols16_smem(int F, int L, int ncol, int nslots) {
+  return (nslots * F * ncol * (L + 1) + L) * 8;
+}
+constexpr int kFoldSmemBudget = 56 * 1024;   // four blocks per SM
+inline int64_t cols_a_blocks(int precision, int log2n1, int n_fields, int half_nx, int ny, int ncol) {
+  if (!log2n1) return 0;
+  const bool reg = precision != FLB_FP64 && cols16_b(1 << log2n1);
+  const int w = reg ? kColsA16 : ncol;
+  return (int64_t)((half_nx + w - 1) / w) * (ny >> log2n1) * (reg ? n_fields : 1);
+}
 inline int column_split(int precision, int F, int ny) {
   const int cs = precision == FLB_FP64 ? 16 : 8;
   if ((int64_t)F * (ny + 1) * 4 * cs <= kColsSmemBudget) return 0;

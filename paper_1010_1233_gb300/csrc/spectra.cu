@@ -14,24 +14,15 @@
 // pass 2a does the inner length-N1 transforms and the W_N^(y2 k1) twiddle in
 // place (rows N2 y1 + y2 -> N2 k1 + y2), pass 2b the outer length-N2 transforms.
 #include <algorithm>
-#include "fft_common.cuh"
+#include "spectra_acc.cuh"
 
 namespace flb {
-
-__device__ __forceinline__ int find_rep(const int64_t* vb_begin, int n_reps, int64_t vb) {
-  int lo = 0, hi = n_reps - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (vb_begin[mid] <= vb) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Pass 1: one block per (replica, packed pair of row units).
 template <typename R>
 __global__ void __launch_bounds__(kRowsBlockMax)
 k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
-                           int n_reps, int64_t n_vblocks, char* __restrict__ ws) {
+                           int n_reps, int64_t n_vblocks, char* __restrict__ ws, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* z = reinterpret_cast<C<R>*>(smem_raw);
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
@@ -96,7 +87,7 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
       __syncthreads();
       dit_fft<R>(z, logn, 1, 0, tw, 1, ps);
     }
-    C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
+    C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec + slot * d.spec_slot);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     C<R>* ra = spec + fa * fplane + (int64_t)ya * d.wpitch;
     C<R>* rb = spec + fb * fplane + (int64_t)yb * d.wpitch;
@@ -120,13 +111,15 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
 
 // Pass 2a (four-step only): one block per (replica, y2, tile of ncol columns).
 template <typename R>
-__global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
-                             int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol) {
+__global__ void __launch_bounds__(kColsBlock, sizeof(R) == 4 ? 4 : 2)
+k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin,
+                             int n_reps, int64_t n_vblocks, char* __restrict__ ws, int ncol, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<R>* s = reinterpret_cast<C<R>*>(smem_raw);
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
+    if (sizeof(R) == 4 && cols16_b(1 << d.log2n1)) continue;        // a register-resident kernel's block
     const int lc = 31 - __clz(ncol);                    // ncol is a power of two
     const int tiles = (d.half_nx + ncol - 1) >> lc;
     const int64_t local = vb - vb_begin[r];
@@ -134,7 +127,7 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
     const int kx0 = (int)(local - (int64_t)y2 * tiles) << lc;
     const int ncl = min(ncol, d.half_nx - kx0);
     const int logn1 = d.log2n1, n1 = 1 << logn1, n2 = d.ny >> logn1, F = (int)d.n_fields;
-    C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec);
+    C<R>* spec = reinterpret_cast<C<R>*>(ws + d.off_spec + slot * d.spec_slot);
     const int64_t fplane = (int64_t)d.ny * d.wpitch;
     const int total = F * n1 * ncol;
     // the next tile of this block into L2 (one bulk prefetch per (field, y1) segment)
@@ -149,7 +142,7 @@ __global__ void k_fft_cols_a(const ReplicaDesc* __restrict__ descs, const int64_
       const int ncn = min(ncol, dn.half_nx - kxn);
       const int l1n = dn.log2n1, n2n = dn.ny >> l1n;
       const uint32_t bytes = (uint32_t)(((ncn * (int)sizeof(C<R>)) + 15) & ~15);
-      const C<R>* sp = reinterpret_cast<const C<R>*>(ws + dn.off_spec);
+      const C<R>* sp = reinterpret_cast<const C<R>*>(ws + dn.off_spec + slot * dn.spec_slot);
       const int64_t fpn = (int64_t)dn.ny * dn.wpitch;
       const int segs = (int)dn.n_fields << l1n;
       for (int i = threadIdx.x; i < segs; i += blockDim.x) {
@@ -207,6 +200,7 @@ k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
+    if (sizeof(R) == 4 && cols16_b(d.ny >> d.log2n1)) continue;     // a register-resident kernel's block
     const int lc = 31 - __clz(ncol);                    // ncol is a power of two
     const int tiles = (d.half_nx + ncol - 1) >> lc;
     const int64_t local = vb - vb_begin[r];
@@ -248,69 +242,7 @@ k_fft_cols_acc(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
     }
     __syncthreads();
     dit_fft<R>(s, logn2, F * ncol, n2 + 1, reinterpret_cast<const C<R>*>(ws + d.off_tw_y), n1);
-    // accumulate pair products in FP64: one work item per (pair, point) of the block,
-    // pair-major so that a warp works on one pair (uniform auto/cross branch) and 32
-    // consecutive points; four items per thread are loaded before any is stored
-    const int lp = lc + logn2, npts = 1 << lp;
-    const int items = d.n_pairs << lp;
-    for (int it0 = threadIdx.x; it0 < items; it0 += 4 * blockDim.x) {
-      double2 acc[4];
-      int64_t pt[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int it = it0 + u * blockDim.x;
-        const int pr = it >> lp, i = it & (npts - 1);
-        const int c = i & (ncol - 1), k2 = i >> lc;
-        pt[u] = -1;
-        if (it >= items || c >= ncl) continue;
-        pt[u] = d.acc_ncol ? ((int64_t)(k1 * tiles + (kx0 >> lc)) * n2 + k2) * ncol + c   // contiguous per block
-                           : (int64_t)(k1 + n1 * k2) * d.half_nx + kx0 + c;
-        if (!FLB_INB(pr < d.n_pairs && d.pair_a[pr] < F && d.pair_b[pr] < F &&
-                     pt[u] < (d.acc_ncol ? (int64_t)d.ny * tiles * ncol : (int64_t)d.ny * d.half_nx), 163)) {
-          pt[u] = -1;
-          continue;
-        }
-        if (d.pair_a[pr] == d.pair_b[pr]) acc[u].x = reinterpret_cast<const double*>(ws + d.pair_off[pr])[pt[u]];
-        else acc[u] = reinterpret_cast<const double2*>(ws + d.pair_off[pr])[pt[u]];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (pt[u] < 0) continue;
-        const int it = it0 + u * blockDim.x;
-        const int pr = it >> lp, i = it & (npts - 1);
-        const int c = i & (ncol - 1), k2 = i >> lc;
-        const int a = d.pair_a[pr], b = d.pair_b[pr];
-        const C<R> Xa = s[(a * ncol + c) * (n2 + 1) + k2];
-        const C<R> Xb = s[(b * ncol + c) * (n2 + 1) + k2];
-        // the product in the transform's precision (exact to its rounding), the sum in FP64
-        if (a == b) {
-          acc[u].x += widen(Xa.x * Xa.x + Xa.y * Xa.y);
-          reinterpret_cast<double*>(ws + d.pair_off[pr])[pt[u]] = acc[u].x;
-        } else {
-          acc[u].x += widen(Xa.x * Xb.x + Xa.y * Xb.y);       // X_a X_b^*
-          acc[u].y += widen(Xa.y * Xb.x - Xa.x * Xb.y);
-          reinterpret_cast<double2*>(ws + d.pair_off[pr])[pt[u]] = acc[u];
-        }
-      }
-    }
-    // time correlators: this sample's X_f(k_j) of the selected wave vectors in this tile
-    if (tc.base) {
-      const int slot = (int)(tc.count[r] % (uint64_t)tc.n_lags);
-      double2* ring = reinterpret_cast<double2*>(tc.base + d.off_tc_ring);
-      for (int i = threadIdx.x; i < tc.n_k * F; i += blockDim.x) {
-        const int j = i % tc.n_k, f = i / tc.n_k;
-        const int kx = tc.kx[j], ky = tc.ky[j];
-        if ((ky & (n1 - 1)) != k1 || kx < kx0 || kx >= kx0 + ncl) continue;
-        if (!FLB_INB(slot >= 0 && slot < tc.n_lags && (ky >> logn1) < n2, 164)) continue;
-        const C<R> X = s[(f * ncol + (kx - kx0)) * (n2 + 1) + (ky >> logn1)];
-        ring[((int64_t)slot * F + f) * tc.n_k + j] = make_double2((double)X.x, (double)X.y);
-      }
-    }
-    // k = 0 sums for the mean subtraction
-    if (k1 == 0 && kx0 == 0 && threadIdx.x == 0) {
-      double* m0 = reinterpret_cast<double*>(ws + d.off_mean0);
-      for (int f = 0; f < F; ++f) m0[f] += (double)s[(f * ncol) * (n2 + 1)].x;
-    }
+    accumulate_tile<R, 0>(d, ws, s, n2 + 1, r, k1, kx0, ncl, ncol, tiles, tc);
     __syncthreads();
   }
 }
@@ -359,6 +291,12 @@ __global__ void k_twiddles(C<R>* tw, int n) {
 }
 
 // ---------------------------------------------------------------------------
+void launch_fft_cols_a16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
+                         char* ws, int grid, cudaStream_t st, int slot);
+void launch_fft_cols_acc16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
+                           char* ws, int ncol, int grid, int smem, cudaStream_t st, const TimeCorr& tc, int nslots);
+cudaError_t set_fft16_smem_limits();
+
 void launch_twiddles(int precision, void* tw, int n, cudaStream_t st) {
   if (n < 2) return;
   const int half = n / 2;
@@ -369,7 +307,9 @@ void launch_twiddles(int precision, void* tw, int n, cudaStream_t st) {
 }
 
 int fft_rows_smem(int precision, int nx) { return (nx + 32) * (precision == FLB_FP64 ? 16 : 8); }
-int fft_cols_smem(int precision, int F, int ny, int ncol) { return F * (ny + 1) * ncol * (precision == FLB_FP64 ? 16 : 8); }
+// the columns of every field of a tile, plus a table of up to 256 roots of unity
+// (the register-resident passes of spectra_cols.cuh)
+int fft_cols_smem(int precision, int F, int ny, int ncol) { return (F * (ny + 1) * ncol + 256) * (precision == FLB_FP64 ? 16 : 8); }
 
 cudaError_t set_fft_smem_limits() {
   cudaError_t e;
@@ -384,32 +324,46 @@ cudaError_t set_fft_smem_limits() {
   if ((e = cudaFuncSetAttribute(k_fft_cols_acc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_a<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
-  return cudaFuncSetAttribute(k_fft_cols_acc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+  if ((e = cudaFuncSetAttribute(k_fft_cols_acc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
+  return set_fft16_smem_limits();
 }
 
+// slot: the spectrum slot (0 or 1) the sample's transforms go to
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st) {
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot) {
   if (precision == FLB_FP64)
-    k_fft_rows<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws);
+    k_fft_rows<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
   else
-    k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws);
+    k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
 }
 
+// paths: kColsGeneric for the shared-memory kernel, bit B for the register-resident
+// kernel of columns of 16 B (FP32 only; see cols16_b).  The register-resident pass-2a
+// kernel takes one block per field of a (y2, tile) unit (cols_a_units), tiles of kColsA16
+// columns; the shared-memory kernel tiles of ncol.
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st) {
-  if (precision == FLB_FP64)
-    k_fft_cols_a<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
-  else
-    k_fft_cols_a<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol);
+                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                       int paths, int slot) {
+  if (precision == FLB_FP64) {
+    k_fft_cols_a<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, slot);
+    return;
+  }
+  if (paths & kColsGeneric)
+    k_fft_cols_a<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, slot);
+  launch_fft_cols_a16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws, grid, st, slot);
 }
 
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc) {
-  if (precision == FLB_FP64)
+                     const TimeCorr& tc, int paths, int nslots) {
+  if (precision == FLB_FP64) {
     k_fft_cols_acc<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
-  else
+    return;
+  }
+  if (paths & kColsGeneric)         // one slot (the host folds samples only without this kernel)
     k_fft_cols_acc<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
+  launch_fft_cols_acc16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws, ncol, grid, smem, st, tc,
+                        nslots);
 }
 
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st) {

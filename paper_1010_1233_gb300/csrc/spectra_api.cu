@@ -15,12 +15,13 @@ int fft_rows_smem(int precision, int nx);
 int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st);
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc);
+                     const TimeCorr& tc, int paths, int nslots);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st);
+                       int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
+                       int paths, int slot);
 
 static inline int64_t a256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
@@ -60,7 +61,7 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   const int64_t tiles = (d.half_nx + P.ncol - 1) / P.ncol;
   P.n_vb_rows = ((int64_t)F * ny + 1) / 2;                   // two row units per block
   P.n_vb_cols = tiles << l1;
-  P.n_vb_cols_a = l1 ? tiles * (ny >> l1) : 0;
+  P.n_vb_cols_a = cols_a_blocks(precision, l1, F, d.half_nx, ny, P.ncol);
   int64_t off = 0;
   P.off_desc = off; off = a256(off + (int64_t)sizeof(ReplicaDesc));
   P.off_vb = off; off = a256(off + 8 * 3);
@@ -109,14 +110,15 @@ int spectra_launch(int precision, SpectraPlan& P, char* scratch, const void* fie
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int gr = (int)std::min<int64_t>(P.n_vb_rows, (int64_t)sms * 8);
-  launch_fft_rows(precision, ddesc, vb, 1, P.n_vb_rows, scratch, gr, P.rows_block, P.rows_smem, st);
+  launch_fft_rows(precision, ddesc, vb, 1, P.n_vb_rows, scratch, gr, P.rows_block, P.rows_smem, st, 0);
   if (P.n_vb_cols_a) {
     const int ga = (int)std::min<int64_t>(P.n_vb_cols_a, (int64_t)sms * 8);
-    launch_fft_cols_a(precision, ddesc, vb + 1, 1, P.n_vb_cols_a, scratch, P.ncol, ga, kColsBlock, P.cols_smem, st);
+    launch_fft_cols_a(precision, ddesc, vb + 1, 1, P.n_vb_cols_a, scratch, P.ncol, ga, kColsBlock, P.cols_smem, st,
+                      cols16_b(1 << d.log2n1) ? cols16_b(1 << d.log2n1) : kColsGeneric, 0);
   }
   const int gc = (int)std::min<int64_t>(P.n_vb_cols, (int64_t)sms * 8);
   launch_fft_cols(precision, ddesc, vb + 2, 1, P.n_vb_cols, scratch, P.ncol, gc, kColsBlock, P.cols_smem, st,
-                  TimeCorr{});
+                  TimeCorr{}, cols16_b(d.ny >> d.log2n1) ? cols16_b(d.ny >> d.log2n1) : kColsGeneric, 1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FLB_ECUDA, "spectra launch: %s", cudaGetErrorString(e));
   return FLB_OK;

@@ -131,6 +131,33 @@ def test_d1q3_correlators_match_oracle():
         assert np.abs(sim.correlator(0, a, b) - ref.acc.correlator(a, b)).max() < 1e-9
 
 
+@pytest.mark.parametrize("nx,ny", [(64, 256), (16, 4096)])
+def test_folded_samples_equal_single_sample_passes(nx, ny):
+    # FP32 with register-resident columns (one pass of 256; four-step 64 x 64) folds two
+    # samples into one pass over the FP64 sums (spectrum slots 0 and 1).  Each sum still
+    # gets the first sample's product added and then the second's, so one run of all the
+    # steps (pairs inside the captured chunks, a lone last sample at the end) must give
+    # the same sums, bit for bit, as one-step runs (a run leaves no sample waiting, so
+    # every sample there gets a pass of its own).
+    fields = (0, 3, W.FIELD_UX, W.FIELD_UY)
+    p = W.replica("D2Q9", nx, ny, W.taus_d2q9(0.7, 0.8, 1.1), kT=1e-3, u0=(0.05, 0.02), seed=41, init_mode=1,
+                  fields=fields)
+    a = Sim(p, precision="fp32")
+    a.run(133, 4)                      # graph chunks of 32 steps (8 samples), then direct steps
+    b = Sim(p, precision="fp32")
+    b.set_graphs(False)
+    for _ in range(133):
+        b.run(1, 4)
+    assert np.array_equal(a.populations(), b.populations())
+    for x, y in spectra.pairs(fields):
+        ga, na = a.correlator(0, x, y, with_count=True)
+        gb, nb = b.correlator(0, x, y, with_count=True)
+        assert na == nb == 34
+        assert np.array_equal(ga, gb), (x, y)
+    a.close()
+    b.close()
+
+
 # ---------------------------------------------------------------------------- batching, checkpoint
 def test_batched_replicas_equal_single():
     # a batched launch runs each replica exactly as a launch of that replica alone: the
