@@ -35,7 +35,8 @@ int fft_rows_smem(int precision, int nx);
 int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot);
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
+                     int paths);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
                      const TimeCorr& tc, int paths, int nslots);
@@ -129,6 +130,7 @@ struct Layout {
   std::vector<int64_t> vb_step, vb_rows, vb_cols, vb_cols_a;
   int vec = 1, q = 9, ncol = 0, rows_block = 32, rows_smem = 0, cols_smem = 0;
   int cols_a_paths = 0, cols_paths = 0;   // column-pass kernels the replicas need (cols16_b)
+  int rows_paths = 0;                     // row-pass kernels (launch_fft_rows)
   int fold = 1;               // 2: two spectrum slots, two samples per accumulation pass
   int staged = 0;             // 1: the step kernel of lb_step_bulk.cu (tiles of 256 vec sites)
   bool any_fields = false;
@@ -397,7 +399,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   }
   L.desc.resize(n);
   int64_t off = 0;
-  int maxF = 0, maxlen = 1, maxnx = 2;
+  int maxF = 0, maxlen = 1;
   for (int r = 0; r < n; ++r) {
     ReplicaDesc& d = L.desc[r];
     fill_desc(precision, reps[r], d);
@@ -405,7 +407,6 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     if (d.n_pairs) {
       maxF = std::max(maxF, (int)d.n_fields);
       maxlen = std::max(maxlen, std::max(1 << d.log2n1, d.ny >> d.log2n1));
-      maxnx = std::max(maxnx, d.nx);
     }
   }
   // column tile width of the sampling passes (it fixes the blocked layout of the pair sums)
@@ -416,6 +417,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     int maxn2 = 1;
     for (const ReplicaDesc& d : L.desc) {
       if (!d.n_pairs) continue;
+      L.rows_paths |= rows16(precision, d.nx) ? 1 << (ilog2(d.nx) - 12) : kColsGeneric;
       const int b2 = precision == FLB_FP64 ? 0 : cols16_b(d.ny >> d.log2n1);
       L.cols_paths |= b2 ? b2 : kColsGeneric;
       maxn2 = std::max(maxn2, d.ny >> d.log2n1);
@@ -427,7 +429,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     // two samples per pass over the FP32 sums when every sampled replica has register-
     // resident columns and the two samples' tiles of at least 4 columns fit 4 blocks per SM
     if (!(L.cols_paths & kColsGeneric)) {
-      int nc = std::min(L.ncol, 8);
+      int nc = L.ncol;
       while (nc >= 4 && fft_cols16_smem(maxF, maxn2, nc, 2) > kFoldSmemBudget) nc >>= 1;
       if (nc >= 4) { L.fold = 2; L.ncol = nc; }
     }
@@ -439,7 +441,8 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     d.off_pop[1] = off; off = align256(off + L.q * V * rs);
     if (d.n_fields) { d.off_fields = off; off = align256(off + (int64_t)d.n_fields * V * rs); }
     if (d.n_pairs) {
-      const int64_t spec_bytes = align256((int64_t)d.n_fields * d.ny * d.wpitch * 2 * rs);
+      d.spec_tiled = spec_tiled_ok(precision, d.nx, d.ny, d.log2n1) ? 1 : 0;
+      const int64_t spec_bytes = align256(spec_elems(d) * 2 * rs);
       d.off_spec = off; off += L.fold * spec_bytes;
       d.spec_slot = L.fold == 2 ? spec_bytes : 0;
       d.acc_ncol = L.ncol;
@@ -457,8 +460,12 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
   // virtual-block prefixes of the three launches
   L.vb_step.resize(n); L.vb_rows.resize(n); L.vb_cols.resize(n); L.vb_cols_a.resize(n);
   if (maxF) {
-    L.rows_smem = fft_rows_smem(precision, maxnx);
-    L.rows_block = std::max(32, std::min(kRowsBlockMax, maxnx / 2));
+    // the shared-memory row kernel's launch (replicas the Stockham kernel does not take)
+    int gnx = 2;
+    for (const ReplicaDesc& d : L.desc)
+      if (d.n_pairs && !rows16(precision, d.nx)) gnx = std::max(gnx, d.nx);
+    L.rows_smem = fft_rows_smem(precision, gnx);
+    L.rows_block = std::max(32, std::min(kRowsBlockMax, gnx / 2));
     L.cols_smem = fft_cols_smem(precision, maxF, maxlen, L.ncol);
     if (L.fold == 2) L.cols_smem = std::max(L.cols_smem, fft_cols16_smem(maxF, maxlen, L.ncol, 2));
   }
@@ -470,7 +477,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     L.vb_cols_a[r] = L.n_vb_cols_a;
     if (d.n_pairs) {
       const int64_t tiles = (d.half_nx + L.ncol - 1) / L.ncol;
-      L.n_vb_rows += ((int64_t)d.n_fields * d.ny + 1) / 2;           // two row units per block
+      L.n_vb_rows += rows_blocks(precision, d.nx, (int)d.n_fields, d.ny);
       L.n_vb_cols += tiles << d.log2n1;                       // (k1, tile)
       L.n_vb_cols_a += cols_a_blocks(precision, d.log2n1, (int)d.n_fields, d.half_nx, d.ny, L.ncol);
     }
@@ -949,10 +956,10 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
     // time correlators, which take their ring entries one sample at a time)
     const bool fold = L.fold == 2 && !c->tc.base;
     const int slot = fold ? c->pending : 0;
-    const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
-    const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
+    const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 2);   // resident blocks
+    const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 4);   // resident blocks loop over their units
     launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
-                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st, slot);
+                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st, slot, L.rows_paths);
     if (L.n_vb_cols_a)
       launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
                         L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st,

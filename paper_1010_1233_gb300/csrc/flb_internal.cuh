@@ -55,6 +55,8 @@ struct ReplicaDesc {
   int64_t off_spec;                 // [n_fields][ny][wpitch] complex Real (row-transformed)
   int64_t spec_slot;                // bytes from spectrum slot 0 to slot 1 (two samples folded
                                     // into one accumulation pass; 0: one slot)
+  int32_t spec_tiled;               // spectrum layout: 0 = [n_fields][ny][wpitch]; 1 = column tiles
+                                    // [n_fields][ceil(half_nx / 16)][ny][16] (kSpecTile)
   int64_t off_mean0;                // [n_fields] double: sum over samples of X(k=0)
   int64_t off_tw_x, off_tw_y;       // twiddles exp(-2 pi i m / n), m < n/2, complex Real
   int32_t half_nx;                  // nx / 2 + 1
@@ -212,10 +214,46 @@ __host__ __device__ __forceinline__ int cols16_b(int len) {
   return (len >= 16 && len <= 256 && (len & (len - 1)) == 0) ? len >> 4 : 0;
 }
 constexpr int kColsGeneric = 32;
+// The FP32 row pass of spectra_rows.cu (one real row per block, Stockham radix-16) for
+// nx = 4096 .. 32768; the shared-memory radix-2 pass of spectra.cu (two rows per block)
+// otherwise.  Virtual blocks of the row pass of a replica:
+inline bool rows16(int precision, int nx) {
+  return precision != FLB_FP64 && nx >= 4096 && nx <= 32768 && (nx & (nx - 1)) == 0;
+}
+inline int64_t rows_blocks(int precision, int nx, int n_fields, int ny) {
+  return rows16(precision, nx) ? (int64_t)n_fields * ny : ((int64_t)n_fields * ny + 1) / 2;
+}
 // The register-resident pass-2a kernel takes tiles of kColsA16 columns of one field
 // (pass 2a needs no field pairs); the shared-memory kernel tiles of the layout's ncol
 // columns of all fields.  Virtual blocks of pass 2a of a replica:
 constexpr int kColsA16 = 16;
+// Column-tiled spectrum (ReplicaDesc::spec_tiled): the row transforms of a field are
+// stored in tiles of kSpecTile columns, each tile [ny][kSpecTile], so that a column pass
+// reading the rows of a tile reads one contiguous slab instead of 128-byte pieces of
+// rows a whole row apart.  Used when every pass of the replica runs on the
+// register-resident / Stockham kernels (FP32 rows of 4096 .. 32768, columns of 16 ..
+// 256); the shared-memory kernels keep the row-major layout.
+constexpr int kSpecTile = 16;
+static_assert(kColsA16 == kSpecTile, "a pass-2a tile is one spectrum tile");
+// element (f, y, kx) of a spectrum slot, the distance between rows y, y + 1, and the
+// complex elements of a slot
+__host__ __device__ __forceinline__ int64_t spec_index(const ReplicaDesc& d, int f, int y, int kx) {
+  if (d.spec_tiled) {
+    const int nt = (d.half_nx + kSpecTile - 1) / kSpecTile;
+    return (((int64_t)f * nt + kx / kSpecTile) * d.ny + y) * kSpecTile + kx % kSpecTile;
+  }
+  return ((int64_t)f * d.ny + y) * d.wpitch + kx;
+}
+__host__ __device__ __forceinline__ int spec_row_stride(const ReplicaDesc& d) {
+  return d.spec_tiled ? kSpecTile : d.wpitch;
+}
+inline bool spec_tiled_ok(int precision, int nx, int ny, int log2n1) {
+  return rows16(precision, nx) && cols16_b(ny >> log2n1) && (log2n1 == 0 || cols16_b(1 << log2n1));
+}
+__host__ __device__ __forceinline__ int64_t spec_elems(const ReplicaDesc& d) {
+  if (d.spec_tiled) return (int64_t)d.n_fields * ((d.half_nx + kSpecTile - 1) / kSpecTile) * d.ny * kSpecTile;
+  return (int64_t)d.n_fields * d.ny * d.wpitch;
+}
 // shared memory of the register-resident pass 2b: nslots samples' tiles of F fields x
 // ncol columns of length L (rows padded to L + 1) and a table of L roots of unity
 inline int fft_cols16_smem(int F, int L, int ncol, int nslots) {

@@ -28,6 +28,7 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
+    if (sizeof(R) == 4 && d.nx >= 4096 && d.nx <= 32768) continue;   // k_fft_rows16's row
     // block vb packs the row units u = 2 local and u + 1 (unit u: field u / ny, row u % ny;
     // ny is a power of two), so an odd field count leaves at most one half-empty transform
     const int64_t ua = 2 * (vb - vb_begin[r]), ub = ua + 1;
@@ -296,6 +297,9 @@ void launch_fft_cols_a16(int mask, const ReplicaDesc* descs, const int64_t* vb_b
 void launch_fft_cols_acc16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
                            char* ws, int ncol, int grid, int smem, cudaStream_t st, const TimeCorr& tc, int nslots);
 cudaError_t set_fft16_smem_limits();
+void launch_fft_rows16(const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks, char* ws,
+                       int grid, int nx, cudaStream_t st, int slot);
+cudaError_t set_rows16_smem_limits();
 
 void launch_twiddles(int precision, void* tw, int n, cudaStream_t st) {
   if (n < 2) return;
@@ -306,9 +310,14 @@ void launch_twiddles(int precision, void* tw, int n, cudaStream_t st) {
     k_twiddles<float><<<(half + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2*>(tw), n);
 }
 
-int fft_rows_smem(int precision, int nx) { return (nx + 32) * (precision == FLB_FP64 ? 16 : 8); }
+// shared memory of the row pass for rows of nx: k_fft_rows16 holds nx / 2 complex values
+// (one pad slot per 16), k_fft_rows nx plus 32 pad slots
+int fft_rows_smem(int precision, int nx) {
+  if (rows16(precision, nx)) return (nx / 2 + nx / 32) * 8;
+  return (nx + 32) * (precision == FLB_FP64 ? 16 : 8);
+}
 // the columns of every field of a tile, plus a table of up to 256 roots of unity
-// (the register-resident passes of spectra_cols.cuh)
+// (the register-resident passes of spectra_cols.cu)
 int fft_cols_smem(int precision, int F, int ny, int ncol) { return (F * (ny + 1) * ncol + 256) * (precision == FLB_FP64 ? 16 : 8); }
 
 cudaError_t set_fft_smem_limits() {
@@ -325,16 +334,22 @@ cudaError_t set_fft_smem_limits() {
   if ((e = cudaFuncSetAttribute(k_fft_cols_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_a<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_acc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb))) return e;
+  if ((e = set_rows16_smem_limits())) return e;
   return set_fft16_smem_limits();
 }
 
-// slot: the spectrum slot (0 or 1) the sample's transforms go to
+// slot: the spectrum slot (0 or 1) the sample's transforms go to.  paths: kColsGeneric
+// for the shared-memory kernel, bit b for k_fft_rows16 on rows of nx = 4096 << b (FP32).
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot) {
-  if (precision == FLB_FP64)
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
+                     int paths) {
+  if (precision == FLB_FP64) {
     k_fft_rows<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
-  else
-    k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
+    return;
+  }
+  if (paths & kColsGeneric) k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
+  for (int b = 0; b < 4; ++b)
+    if (paths & (1 << b)) launch_fft_rows16(descs, vb_begin, n_reps, n_vblocks, ws, grid, 4096 << b, st, slot);
 }
 
 // paths: kColsGeneric for the shared-memory kernel, bit B for the register-resident

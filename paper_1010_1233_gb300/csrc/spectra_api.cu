@@ -15,7 +15,8 @@ int fft_rows_smem(int precision, int nx);
 int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
-                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot);
+                     int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
+                     int paths);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
                      const TimeCorr& tc, int paths, int nslots);
@@ -59,7 +60,7 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   P.rows_block = std::max(32, std::min(kRowsBlockMax, nx / 2));
   P.cols_smem = fft_cols_smem(precision, F, len, P.ncol);
   const int64_t tiles = (d.half_nx + P.ncol - 1) / P.ncol;
-  P.n_vb_rows = ((int64_t)F * ny + 1) / 2;                   // two row units per block
+  P.n_vb_rows = rows_blocks(precision, nx, F, ny);
   P.n_vb_cols = tiles << l1;
   P.n_vb_cols_a = cols_a_blocks(precision, l1, F, d.half_nx, ny, P.ncol);
   int64_t off = 0;
@@ -67,7 +68,8 @@ int spectra_plan(int precision, int nx, int ny, int F, SpectraPlan& P) {
   P.off_vb = off; off = a256(off + 8 * 3);
   P.off_tw_x = off; off = a256(off + (int64_t)(nx / 2) * cs + 16);
   P.off_tw_y = off; off = a256(off + (int64_t)(ny / 2) * cs + 16);
-  P.off_spec = off; off = a256(off + (int64_t)F * ny * d.wpitch * cs);
+  d.spec_tiled = spec_tiled_ok(precision, nx, ny, l1) ? 1 : 0;
+  P.off_spec = off; off = a256(off + spec_elems(d) * cs);
   P.scratch_bytes = (size_t)off;
   int64_t sums = 0;
   for (int pr = 0; pr < np; ++pr) sums += (int64_t)ny * d.half_nx * (d.pair_a[pr] == d.pair_b[pr] ? 1 : 2);
@@ -109,10 +111,11 @@ int spectra_launch(int precision, SpectraPlan& P, char* scratch, const void* fie
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int gr = (int)std::min<int64_t>(P.n_vb_rows, (int64_t)sms * 8);
-  launch_fft_rows(precision, ddesc, vb, 1, P.n_vb_rows, scratch, gr, P.rows_block, P.rows_smem, st, 0);
+  const int gr = (int)std::min<int64_t>(P.n_vb_rows, (int64_t)sms * 2);
+  launch_fft_rows(precision, ddesc, vb, 1, P.n_vb_rows, scratch, gr, P.rows_block, P.rows_smem, st, 0,
+                  rows16(precision, d.nx) ? 1 << (d.log2nx - 12) : kColsGeneric);
   if (P.n_vb_cols_a) {
-    const int ga = (int)std::min<int64_t>(P.n_vb_cols_a, (int64_t)sms * 8);
+    const int ga = (int)std::min<int64_t>(P.n_vb_cols_a, (int64_t)sms * 4);
     launch_fft_cols_a(precision, ddesc, vb + 1, 1, P.n_vb_cols_a, scratch, P.ncol, ga, kColsBlock, P.cols_smem, st,
                       cols16_b(1 << d.log2n1) ? cols16_b(1 << d.log2n1) : kColsGeneric, 0);
   }

@@ -55,56 +55,67 @@ __device__ __forceinline__ void stage1(const float2* __restrict__ src, int64_t j
   for (int q = 1; q < 16; ++q) e[q * B] = B > 1 ? cmul<float>(v[q], wl[r * q]) : v[q];
 }
 
-// Pass 2a tile (four-step, N1 = L) of one field f: the columns kx0 .. kx0 + ncl - 1 of
-// the rows N2 y1 + y2, transformed over y1, times W_ny^(y2 k1), back to rows N2 k1 + y2.
-// (Pass 2a needs no field pairs, so a block takes one field: a quarter of the shared
-// memory of an all-field tile, and four times the blocks per SM.)  All threads call it;
-// it ends with a barrier.
+// Pass 2a (four-step, N1 = L): one unit per (replica, field f, y2, tile of kColsA16
+// columns); pass 2a needs no field pairs, so a tile holds one field.  A block loads the
+// columns kx0 .. kx0 + 15 of the rows N2 y1 + y2 (y1 < L), transforms over y1,
+// multiplies by W_ny^(y2 k1) and stores back to rows N2 k1 + y2.  The loads go through
+// shared memory by asynchronous 16-byte copies (cp.async) issued units ahead, so a
+// block keeps its next units' copies in flight while it transforms (the copies are the
+// block's only reads of the spectrum).
+struct A16Unit {
+  int rep, f, y2, kx0;
+};
+
+__device__ __forceinline__ A16Unit a16_unit(const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                                            int64_t vb) {
+  A16Unit u;
+  u.rep = find_rep(vb_begin, n_reps, vb);
+  const ReplicaDesc& d = descs[u.rep];
+  const int tiles = (d.half_nx + kColsA16 - 1) / kColsA16;
+  const int64_t per_field = (int64_t)tiles * (d.ny >> d.log2n1);
+  const int64_t local = vb - vb_begin[u.rep];
+  u.f = (int)(local / per_field);
+  const int64_t lf = local - u.f * per_field;
+  if (d.spec_tiled) {               // y2 fastest: neighbouring units, neighbouring rows of a slab
+    const int n2 = d.ny >> d.log2n1;
+    const int t = (int)(lf / n2);
+    u.y2 = (int)(lf - (int64_t)t * n2);
+    u.kx0 = t * kColsA16;
+  } else {                          // tile fastest: neighbouring units, neighbouring columns of rows
+    u.y2 = (int)(lf / tiles);
+    u.kx0 = (int)(lf - (int64_t)u.y2 * tiles) * kColsA16;
+  }
+  return u;
+}
+
+// the block's next unit of this kernel (blocks of replicas with other column lengths
+// are skipped), or n_vblocks
 template <int B>
-__device__ __forceinline__ void cols_a16_tile(const ReplicaDesc& d, char* __restrict__ ws, float2* s, int f, int y2,
-                                              int kx0, int ncl, int ncol, int slot) {
-  constexpr int L = 16 * B, SS = L + 1, QN = 16 / B, LB = log2_ct<B>();
-  const int lc = 31 - __clz(ncol);
-  const int n2 = d.ny >> d.log2n1, hn = d.ny >> 1;
-  const float2* tw = reinterpret_cast<const float2*>(ws + d.off_tw_y);
-  float2* spec = reinterpret_cast<float2*>(ws + d.off_spec + slot * d.spec_slot) + f * (int64_t)d.ny * d.wpitch;
-  float2* wl = s + ncol * SS;
-  fill_wl(wl, L, tw, d.ny);
-  __syncthreads();
-  const int items = 1 << (lc + LB);
-  // stage 1: rows y = N2 (r + B j) + y2
-  const int64_t jstride = (int64_t)n2 * B * d.wpitch;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it & (ncol - 1), r = it >> lc;
-    const bool in = c < ncl && FLB_INB(f < (int)d.n_fields && n2 * (r + B * 15) + y2 < d.ny && kx0 + c < d.half_nx, 201);
-    stage1<B>(spec + (int64_t)(n2 * r + y2) * d.wpitch + kx0 + c, jstride, in, s + c * SS + r, wl, r);
+__device__ __forceinline__ int64_t a16_next(const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
+                                            int64_t n_vblocks, int64_t vb) {
+  for (; vb < n_vblocks; vb += gridDim.x)
+    if (cols16_b(1 << descs[find_rep(vb_begin, n_reps, vb)].log2n1) == B) break;
+  return vb;
+}
+
+// the asynchronous copies of a unit's L x kColsA16 complex values into a staging
+// buffer [L][kColsA16]: 16-byte chunks (two columns), chunks past the row pitch skipped
+template <int B>
+__device__ __forceinline__ void a16_issue(const ReplicaDesc& d, const A16Unit& u, const char* ws, int slot,
+                                          float2* buf) {
+  constexpr int L = 16 * B, CH = kColsA16 / 2;          // chunks per row
+  const int n2 = d.ny >> d.log2n1;
+  const float2* spec = reinterpret_cast<const float2*>(ws + d.off_spec + slot * d.spec_slot) +
+                       spec_index(d, u.f, 0, u.kx0);
+  const int rs = spec_row_stride(d), cols = d.spec_tiled ? kSpecTile : d.wpitch - u.kx0;   // columns present
+  for (int i = threadIdx.x; i < L * CH; i += blockDim.x) {
+    const int y1 = i / CH, ch = i - y1 * CH;
+    if (2 * ch >= cols) continue;
+    if (!FLB_INB(u.f < (int)d.n_fields && n2 * y1 + u.y2 < d.ny, 204)) continue;
+    const float2* src = spec + (int64_t)(n2 * y1 + u.y2) * rs + 2 * ch;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + y1 * kColsA16 + 2 * ch);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
   }
-  __syncthreads();
-  // stage 2, then the twiddle W_ny^(y2 k1) and the store to row N2 k1 + y2
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it & (ncol - 1), t = it >> lc;
-    const float2* e = s + c * SS;
-    float2* dst = spec + (int64_t)y2 * d.wpitch + kx0 + c;
-#pragma unroll
-    for (int qi = 0; qi < QN; ++qi) {
-      const int q = t * QN + qi;
-      float2 u[B];
-#pragma unroll
-      for (int r = 0; r < B; ++r) u[r] = e[q * B + r];
-      dft_reg<float, B>(u);
-      if (c >= ncl) continue;
-#pragma unroll
-      for (int p = 0; p < B; ++p) {
-        const int k1 = q + 16 * p;
-        const int ex = y2 * k1;                     // < ny
-        float2 w = tw[ex < hn ? ex : ex - hn];
-        if (ex >= hn) { w.x = -w.x; w.y = -w.y; }
-        if (FLB_INB(f < (int)d.n_fields && n2 * k1 + y2 < d.ny && kx0 + c < d.half_nx, 203))
-          dst[(int64_t)n2 * k1 * d.wpitch] = cmul<float>(u[p], w);
-      }
-    }
-  }
-  __syncthreads();
 }
 
 // Pass 2b tile (N2 = L; one-pass columns are N1 = 1): the rows N2 k1 + y2 of the tile
@@ -117,7 +128,7 @@ __device__ __forceinline__ void cols_acc16_tile(const ReplicaDesc& d, char* __re
   constexpr int L = 16 * B, SS = L + 1, QN = 16 / B, LB = log2_ct<B>();
   const int lc = 31 - __clz(ncol);
   const int n2 = d.ny >> d.log2n1, F = (int)d.n_fields;
-  const int64_t fplane = (int64_t)d.ny * d.wpitch;
+  const int rs = spec_row_stride(d);
   const int slot_elems = F * ncol * SS;                 // shared-memory rows of one sample
   float2* wl = s + nslots * slot_elems;
   fill_wl(wl, L, reinterpret_cast<const float2*>(ws + d.off_tw_y), d.ny);
@@ -131,7 +142,7 @@ __device__ __forceinline__ void cols_acc16_tile(const ReplicaDesc& d, char* __re
     const float2* spec = reinterpret_cast<const float2*>(ws + d.off_spec + k * d.spec_slot);
     const bool in = c < ncl && FLB_INB(f < F && n2 * k1 + r + B * 15 < d.ny && kx0 + c < d.half_nx, 211);
     if (!FLB_INB((f * ncol + c + 1) * SS <= slot_elems, 212)) continue;
-    stage1<B>(spec + f * fplane + (int64_t)(n2 * k1 + r) * d.wpitch + kx0 + c, (int64_t)B * d.wpitch, in,
+    stage1<B>(spec + spec_index(d, f, n2 * k1 + r, kx0) + c, (int64_t)B * rs, in,
               s + k * slot_elems + (f * ncol + c) * SS + r, wl, r);
   }
   __syncthreads();
@@ -158,27 +169,109 @@ __device__ __forceinline__ void cols_acc16_tile(const ReplicaDesc& d, char* __re
   __syncthreads();
 }
 
-// One block per (replica, field, y2, tile of kColsA16 columns).
+// kA16Stages staging buffers of (L + 1) kColsA16 complex values: a unit's copies land in
+// one as [y1][c]; once its values are in registers the same buffer takes the exchange
+// rows [c][L + 1], so every buffer serves one unit from its copies to its stores and
+// the copies of the next kA16Stages - 1 units are in flight meanwhile.
+constexpr int kA16Stages = 3;
+
 template <int B>
-__global__ void __launch_bounds__(kCols16Block, 4)
+__global__ void __launch_bounds__(kColsA16 * 16, 64 / kColsA16)     // 64 registers a thread
 k_fft_cols_a16(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb_begin, int n_reps,
                int64_t n_vblocks, char* __restrict__ ws, int slot) {
+  constexpr int L = 16 * B, SS = L + 1, QN = 16 / B, ncol = kColsA16, lc = log2_ct<kColsA16>();
+  constexpr int BUF = ncol * SS;                         // >= L ncol
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* s = reinterpret_cast<float2*>(smem_raw);
-  constexpr int ncol = kColsA16, lc = log2_ct<kColsA16>();
-  for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
-    const int rp = find_rep(vb_begin, n_reps, vb);
-    const ReplicaDesc& d = descs[rp];
-    if (cols16_b(1 << d.log2n1) != B) continue;
-    const int tiles = (d.half_nx + ncol - 1) >> lc;
-    const int64_t per_field = (int64_t)tiles * (d.ny >> d.log2n1);
-    const int64_t local = vb - vb_begin[rp];
-    const int f = (int)(local / per_field);
-    const int64_t lf = local - f * per_field;
-    const int y2 = (int)(lf / tiles);
-    const int kx0 = (int)(lf - (int64_t)y2 * tiles) << lc;
-    cols_a16_tile<B>(d, ws, s, f, y2, kx0, min(ncol, d.half_nx - kx0), ncol, slot);
+  float2* stage = reinterpret_cast<float2*>(smem_raw);   // [kA16Stages][BUF]
+  float2* wl = stage + kA16Stages * BUF;                 // [L]: W_L^m
+  float2* wy = wl + L;                                   // [L]: W_ny^(y2 k1) of the current unit
+  // the block's units: the current one (u0, buffer cb) and the next two (u1, u2), whose
+  // copies are in flight; vb: the unit after u2
+  static_assert(kA16Stages == 3, "the current unit and two ahead");
+  A16Unit u0{}, u1{}, u2{};
+  int64_t v0 = a16_next<B>(descs, vb_begin, n_reps, n_vblocks, blockIdx.x);
+  int64_t v1 = v0 < n_vblocks ? a16_next<B>(descs, vb_begin, n_reps, n_vblocks, v0 + gridDim.x) : n_vblocks;
+  int64_t vb = v1 < n_vblocks ? a16_next<B>(descs, vb_begin, n_reps, n_vblocks, v1 + gridDim.x) : n_vblocks;
+  if (v0 < n_vblocks) {
+    u0 = a16_unit(descs, vb_begin, n_reps, v0);
+    a16_issue<B>(descs[u0.rep], u0, ws, slot, stage);
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (v1 < n_vblocks) {
+    u1 = a16_unit(descs, vb_begin, n_reps, v1);
+    a16_issue<B>(descs[u1.rep], u1, ws, slot, stage + BUF);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int cb = 0; v0 < n_vblocks; cb = cb == kA16Stages - 1 ? 0 : cb + 1) {
+    const A16Unit cur = u0;
+    const ReplicaDesc& d = descs[cur.rep];
+    // the unit two ahead into the buffer the previous unit left
+    const int nb = cb == 0 ? kA16Stages - 1 : cb - 1;
+    const int64_t v2 = vb;
+    if (v2 < n_vblocks) {
+      u2 = a16_unit(descs, vb_begin, n_reps, v2);
+      a16_issue<B>(descs[u2.rep], u2, ws, slot, stage + nb * BUF);
+      vb = a16_next<B>(descs, vb_begin, n_reps, n_vblocks, v2 + gridDim.x);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const float2* tw = reinterpret_cast<const float2*>(ws + d.off_tw_y);
+    const int n2 = d.ny >> d.log2n1, hn = d.ny >> 1;
+    fill_wl(wl, L, tw, d.ny);
+    for (int k1 = threadIdx.x; k1 < L; k1 += blockDim.x) {   // the unit's twiddles, y2 k1 < ny
+      const int ex = cur.y2 * k1;
+      float2 w = tw[ex < hn ? ex : ex - hn];
+      if (ex >= hn) { w.x = -w.x; w.y = -w.y; }
+      wy[k1] = w;
+    }
+    asm volatile("cp.async.wait_group %0;" :: "n"(kA16Stages - 1) : "memory");
+    __syncthreads();
+    const int ncl = min(ncol, d.half_nx - cur.kx0);
+    float2* buf = stage + cb * BUF;
+    // stage 1: thread (c, r) transforms y1 = r + B j, j < 16
+    const int it0 = threadIdx.x, c0 = it0 & (ncol - 1), r0 = it0 >> lc;
+    const bool act = it0 < ncol * B;                      // blockDim.x >= ncol B
+    float2 v[16];
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = buf[(r0 + B * j) * ncol + c0];
+      dft_reg<float, 16>(v);
+    }
+    __syncthreads();                                     // the copied values are all in registers
+    if (act) {
+      float2* e = buf + c0 * SS + r0;
+      e[0] = v[0];
+#pragma unroll
+      for (int q = 1; q < 16; ++q) e[q * B] = B > 1 ? cmul<float>(v[q], wl[r0 * q]) : v[q];
+    }
+    __syncthreads();
+    // stage 2, then the twiddle W_ny^(y2 k1) and the store to row N2 k1 + y2
+    float2* spec = reinterpret_cast<float2*>(ws + d.off_spec + slot * d.spec_slot);
+    const int rs = spec_row_stride(d);
+    if (act) {
+      const int c = c0, t = r0;
+      const float2* e = buf + c * SS;
+      float2* dst = spec + spec_index(d, cur.f, cur.y2, cur.kx0) + c;
+#pragma unroll
+      for (int qi = 0; qi < QN; ++qi) {
+        const int q = t * QN + qi;
+        float2 w8[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) w8[r] = e[q * B + r];
+        dft_reg<float, B>(w8);
+        if (c >= ncl) continue;
+#pragma unroll
+        for (int p = 0; p < B; ++p) {
+          const int k1 = q + 16 * p;
+          if (FLB_INB(cur.f < (int)d.n_fields && n2 * k1 + cur.y2 < d.ny && cur.kx0 + c < d.half_nx, 203))
+            dst[(int64_t)n2 * k1 * rs] = cmul<float>(w8[p], wy[k1]);
+        }
+      }
+    }
+    __syncthreads();                                     // buffer cb free for a new unit
+    u0 = u1; v0 = v1;
+    u1 = u2; v1 = v2;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 #ifndef FLB_ACC16_MIN_BLOCKS
@@ -227,15 +320,20 @@ cudaError_t set_fft16_smem_limits() {
   return e;
 }
 
-// one launch per B in the mask (bits 1, 2, 4, 8, 16); kColsA16 B threads (at least a warp,
-// at most kCols16Block) and the shared memory of one field's tile
+// shared memory of the pass-2a kernel: the staging buffers and two twiddle tables
+static int a16_smem(int B) {
+  const int L = 16 * B;
+  return (kA16Stages * kColsA16 * (L + 1) + 2 * L) * (int)sizeof(float2);
+}
+
+// one launch per B in the mask (bits 1, 2, 4, 8, 16); kColsA16 B threads (at least a warp)
+// and the shared memory of one field's tiles
 void launch_fft_cols_a16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
                          char* ws, int grid, cudaStream_t st, int slot) {
 #define FLB_L(B)                                                                                         \
   if (mask & B)                                                                                          \
-    k_fft_cols_a16<B><<<grid, std::max(32, std::min(kCols16Block, kColsA16 * B)),                        \
-                        (kColsA16 * (16 * B + 1) + 16 * B) * (int)sizeof(float2), st>>>(descs, vb_begin, \
-                                                                                         n_reps, n_vblocks, ws, slot);
+    k_fft_cols_a16<B><<<grid, std::max(32, kColsA16 * B), a16_smem(B), st>>>(                                \
+        descs, vb_begin, n_reps, n_vblocks, ws, slot);
   FLB_L(1) FLB_L(2) FLB_L(4) FLB_L(8) FLB_L(16)
 #undef FLB_L
 }

@@ -12,7 +12,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("precision,F,ny,nx,tol", [
     ("fp64", 3, 16, 32, 1e-12), ("fp64", 4, 2048, 8, 1e-12),      # one-pass / four-step columns
-    ("fp32", 5, 64, 128, 2e-6), ("fp32", 1, 8, 16384, 2e-6), ("fp32", 3, 4096, 8, 2e-6)])
+    ("fp32", 5, 64, 128, 2e-6), ("fp32", 1, 8, 16384, 2e-6), ("fp32", 3, 4096, 8, 2e-6),
+    # rows of the Stockham row pass: passes 16-16-8 (4096), 16-16-16-2 (8192), 16-16-16-4 (32768)
+    ("fp32", 2, 4, 4096, 2e-6), ("fp32", 2, 4, 8192, 2e-6), ("fp32", 1, 2, 32768, 2e-6)])
 def test_spectra_accumulate_matches_oracle(precision, F, ny, nx, tol):
     dt = torch.float64 if precision == "fp64" else torch.float32
     p = lb.Params(**W.replica(nx=nx, ny=ny, fields=list(range(F))))
