@@ -36,14 +36,14 @@ int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
-                     int paths);
+                     int paths, int sms);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc, int paths, int nslots);
+                     const TimeCorr& tc, int paths, int nslots, int max_fields);
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                       int paths, int slot);
+                       int paths, int slot, int sms);
 void launch_wait_probe(DevStatus* status, long long limit, cudaStream_t st);   // lb_step_tc.cu
 // D1Q3 runs of steps with their sampling in one launch (lb_d1q3_fused.cu)
 size_t d1q3_fused_smem(int precision, int nx, int F);
@@ -132,6 +132,7 @@ struct Layout {
   int cols_a_paths = 0, cols_paths = 0;   // column-pass kernels the replicas need (cols16_b)
   int rows_paths = 0;                     // row-pass kernels (launch_fft_rows)
   int fold = 1;               // 2: two spectrum slots, two samples per accumulation pass
+  int max_fields = 0;         // the most sampled fields of a replica with pair sums
   int staged = 0;             // 1: the step kernel of lb_step_bulk.cu (tiles of 256 vec sites)
   bool any_fields = false;
 };
@@ -410,6 +411,7 @@ static int plan(int precision, const flb_replica* reps, int n, Layout& L) {
     }
   }
   // column tile width of the sampling passes (it fixes the blocked layout of the pair sums)
+  L.max_fields = maxF;
   if (maxF) {
     L.ncol = kColsMax;
     while (L.ncol > 1 && fft_cols_smem(precision, maxF, maxlen, L.ncol) > kColsSmemBudget) L.ncol >>= 1;
@@ -929,7 +931,7 @@ static void flush_samples(flb_ctx* c, const StepLaunch& S, cudaStream_t st) {
   const int cols_grid = (int)std::min<int64_t>(L.n_vb_cols, (int64_t)c->sms * 8);
   launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
                   L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st, c->tc, L.cols_paths,
-                  c->pending);
+                  c->pending, L.max_fields);
   c->pending = 0;
   if (c->tc.base) {
     int maxF = 0;
@@ -956,14 +958,14 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
     // time correlators, which take their ring entries one sample at a time)
     const bool fold = L.fold == 2 && !c->tc.base;
     const int slot = fold ? c->pending : 0;
-    const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 2);   // resident blocks
-    const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 4);   // resident blocks loop over their units
+    const int rows_grid = (int)std::min<int64_t>(L.n_vb_rows, (int64_t)c->sms * 8);
+    const int cols_a_grid = (int)std::min<int64_t>(L.n_vb_cols_a, (int64_t)c->sms * 8);
     launch_fft_rows(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_rows), c->n,
-                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st, slot, L.rows_paths);
+                    L.n_vb_rows, c->ws, rows_grid, L.rows_block, L.rows_smem, st, slot, L.rows_paths, c->sms);
     if (L.n_vb_cols_a)
       launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
                         L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st,
-                        L.cols_a_paths, slot);
+                        L.cols_a_paths, slot, c->sms);
     c->pending = slot + 1;
     if (!fold || c->pending == 2) flush_samples(c, S, st);
   }

@@ -295,7 +295,8 @@ __global__ void k_twiddles(C<R>* tw, int n) {
 void launch_fft_cols_a16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
                          char* ws, int grid, cudaStream_t st, int slot);
 void launch_fft_cols_acc16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
-                           char* ws, int ncol, int grid, int smem, cudaStream_t st, const TimeCorr& tc, int nslots);
+                           char* ws, int ncol, int grid, int max_fields, cudaStream_t st, const TimeCorr& tc,
+                           int nslots);
 cudaError_t set_fft16_smem_limits();
 void launch_fft_rows16(const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks, char* ws,
                        int grid, int nx, cudaStream_t st, int slot);
@@ -340,16 +341,19 @@ cudaError_t set_fft_smem_limits() {
 
 // slot: the spectrum slot (0 or 1) the sample's transforms go to.  paths: kColsGeneric
 // for the shared-memory kernel, bit b for k_fft_rows16 on rows of nx = 4096 << b (FP32).
+// grid: blocks of the shared-memory kernel; the Stockham kernel takes at most two blocks
+// per SM of the sms SMs (its blocks loop over their rows)
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
-                     int paths) {
+                     int paths, int sms) {
   if (precision == FLB_FP64) {
     k_fft_rows<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
     return;
   }
   if (paths & kColsGeneric) k_fft_rows<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, slot);
+  const int g16 = (int)std::min<int64_t>((int64_t)grid, 2 * (int64_t)sms);
   for (int b = 0; b < 4; ++b)
-    if (paths & (1 << b)) launch_fft_rows16(descs, vb_begin, n_reps, n_vblocks, ws, grid, 4096 << b, st, slot);
+    if (paths & (1 << b)) launch_fft_rows16(descs, vb_begin, n_reps, n_vblocks, ws, g16, 4096 << b, st, slot);
 }
 
 // paths: kColsGeneric for the shared-memory kernel, bit B for the register-resident
@@ -358,27 +362,29 @@ void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_
 // columns; the shared-memory kernel tiles of ncol.
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                       int paths, int slot) {
+                       int paths, int slot, int sms) {
   if (precision == FLB_FP64) {
     k_fft_cols_a<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, slot);
     return;
   }
   if (paths & kColsGeneric)
     k_fft_cols_a<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, slot);
-  launch_fft_cols_a16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws, grid, st, slot);
+  // the pipelined kernel: its resident blocks (4 per SM) loop over their units
+  launch_fft_cols_a16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws,
+                      (int)std::min<int64_t>((int64_t)grid, 4 * (int64_t)sms), st, slot);
 }
 
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc, int paths, int nslots) {
+                     const TimeCorr& tc, int paths, int nslots, int max_fields) {
   if (precision == FLB_FP64) {
     k_fft_cols_acc<double><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
     return;
   }
   if (paths & kColsGeneric)         // one slot (the host folds samples only without this kernel)
     k_fft_cols_acc<float><<<grid, block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc);
-  launch_fft_cols_acc16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws, ncol, grid, smem, st, tc,
-                        nslots);
+  launch_fft_cols_acc16(paths & (kColsGeneric - 1), descs, vb_begin, n_reps, n_vblocks, ws, ncol, grid, max_fields, st,
+                        tc, nslots);
 }
 
 void launch_time_corr(const ReplicaDesc* descs, int n_reps, int max_fields, const TimeCorr& tc, cudaStream_t st) {

@@ -16,13 +16,13 @@ int fft_cols_smem(int precision, int F, int ny, int ncol);
 cudaError_t set_fft_smem_limits();
 void launch_fft_rows(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int grid, int block, int smem, cudaStream_t st, int slot,
-                     int paths);
+                     int paths, int sms);
 void launch_fft_cols(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                      int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                     const TimeCorr& tc, int paths, int nslots);
+                     const TimeCorr& tc, int paths, int nslots, int max_fields);
 void launch_fft_cols_a(int precision, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps,
                        int64_t n_vblocks, char* ws, int ncol, int grid, int block, int smem, cudaStream_t st,
-                       int paths, int slot);
+                       int paths, int slot, int sms);
 
 static inline int64_t a256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
@@ -111,17 +111,17 @@ int spectra_launch(int precision, SpectraPlan& P, char* scratch, const void* fie
   int sms = 1, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int gr = (int)std::min<int64_t>(P.n_vb_rows, (int64_t)sms * 2);
+  const int gr = (int)std::min<int64_t>(P.n_vb_rows, (int64_t)sms * 8);
   launch_fft_rows(precision, ddesc, vb, 1, P.n_vb_rows, scratch, gr, P.rows_block, P.rows_smem, st, 0,
-                  rows16(precision, d.nx) ? 1 << (d.log2nx - 12) : kColsGeneric);
+                  rows16(precision, d.nx) ? 1 << (d.log2nx - 12) : kColsGeneric, sms);
   if (P.n_vb_cols_a) {
-    const int ga = (int)std::min<int64_t>(P.n_vb_cols_a, (int64_t)sms * 4);
+    const int ga = (int)std::min<int64_t>(P.n_vb_cols_a, (int64_t)sms * 8);
     launch_fft_cols_a(precision, ddesc, vb + 1, 1, P.n_vb_cols_a, scratch, P.ncol, ga, kColsBlock, P.cols_smem, st,
-                      cols16_b(1 << d.log2n1) ? cols16_b(1 << d.log2n1) : kColsGeneric, 0);
+                      cols16_b(1 << d.log2n1) ? cols16_b(1 << d.log2n1) : kColsGeneric, 0, sms);
   }
   const int gc = (int)std::min<int64_t>(P.n_vb_cols, (int64_t)sms * 8);
   launch_fft_cols(precision, ddesc, vb + 2, 1, P.n_vb_cols, scratch, P.ncol, gc, kColsBlock, P.cols_smem, st,
-                  TimeCorr{}, cols16_b(d.ny >> d.log2n1) ? cols16_b(d.ny >> d.log2n1) : kColsGeneric, 1);
+                  TimeCorr{}, cols16_b(d.ny >> d.log2n1) ? cols16_b(d.ny >> d.log2n1) : kColsGeneric, 1, (int)d.n_fields);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(FLB_ECUDA, "spectra launch: %s", cudaGetErrorString(e));
   return FLB_OK;

@@ -338,12 +338,15 @@ void launch_fft_cols_a16(int mask, const ReplicaDesc* descs, const int64_t* vb_b
 #undef FLB_L
 }
 
-// nslots = 2: the tiles of the samples in spectrum slots 0 and 1 in one pass (smem for both)
+// nslots = 2: the tiles of the samples in spectrum slots 0 and 1 in one pass; each launch
+// with the shared memory of its column length (max_fields: the most fields of a replica)
 void launch_fft_cols_acc16(int mask, const ReplicaDesc* descs, const int64_t* vb_begin, int n_reps, int64_t n_vblocks,
-                           char* ws, int ncol, int grid, int smem, cudaStream_t st, const TimeCorr& tc, int nslots) {
+                           char* ws, int ncol, int grid, int max_fields, cudaStream_t st, const TimeCorr& tc,
+                           int nslots) {
 #define FLB_L(B)                                                                                            \
   if (mask & B)                                                                                             \
-    k_fft_cols_acc16<B><<<grid, kCols16Block, smem, st>>>(descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc, nslots);
+    k_fft_cols_acc16<B><<<grid, kCols16Block, fft_cols16_smem(max_fields, 16 * B, ncol, nslots), st>>>(     \
+        descs, vb_begin, n_reps, n_vblocks, ws, ncol, tc, nslots);
   FLB_L(1) FLB_L(2) FLB_L(4) FLB_L(8) FLB_L(16)
 #undef FLB_L
 }
