@@ -96,27 +96,6 @@ def job_throughput(sites_per_rank, steps, seconds_local, world, device="cpu"):
     return world * sites_per_rank * steps / tmax / 1e6, tmax
 
 
-def expected_launches(start, K, every, sample_kernels, graph_max=4096):
-    """Kernels flb_run issues for K steps from step `start` (sampling every `every` steps):
-    one step kernel per step, `sample_kernels` FFT kernels per sample, and with CUDA graphs
-    (chunks of `every` steps once aligned, K >= 2 every) one step-counter kernel per
-    chunk plus one that sets the counter before the first."""
-    n = 0
-    i, t = 0, start
-    if K >= 2 * every and every <= graph_max:
-        while i < K and t % every:
-            n += 1 + (sample_kernels if t % every == 0 else 0)
-            i, t = i + 1, t + 1
-        chunks = (K - i) // every
-        if chunks:
-            n += 1 + chunks * (every + sample_kernels + 1)
-            i, t = i + chunks * every, t + chunks * every
-    while i < K:
-        n += 1 + (sample_kernels if t % every == 0 else 0)
-        i, t = i + 1, t + 1
-    return n
-
-
 def workload(n):
     from paper_1010_1233_gb300 import workloads as W
     wl = W.d2q9_16384(n)
@@ -491,15 +470,15 @@ def run_ours3(args):
     sim.run(Wm, SAMPLE_EVERY)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = sim.kernel_launches()
     with ClockSampler(local) as clk:
         e0.record(stream)
         sim.run(K, SAMPLE_EVERY)
         e1.record(stream)
         barrier()
+    launches = sim.kernel_launches() - n0             # the library's own count of the timed run
     ms = e0.elapsed_time(e1)
     value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
-    # per sample: point transform, its finishing pass, the lagged products, the ring advance
-    launches = expected_launches(Wm, K, SAMPLE_EVERY, sample_kernels=4)
 
     Kd = max(20, min(K, 100))
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -627,16 +606,16 @@ def run_ours(args):
     sim.run(Wm, every)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = sim.kernel_launches()
     with ClockSampler(local) as clk:
         e0.record(stream)
         sim.run(K, every)
         e1.record(stream)
         barrier()
+    launches = sim.kernel_launches() - n0             # the library's own count of the timed run
     ms = e0.elapsed_time(e1)
     value, t_max = job_throughput(V, K, ms * 1e-3, world, device="cuda")
     ms_max = t_max * 1e3
-    maxny = max(q["ny"] for q in (reps if sweep else [p]))
-    launches = expected_launches(Wm, K, every, sample_kernels=3 if maxny > 2048 else 2)
     finite = None
     if sweep:
         finite = [bool(np.all(np.isfinite(sim.conserved(r)))) for r in range(len(reps))]

@@ -282,6 +282,11 @@ int flb_autotune(flb_ctx* ctx, int trials, int* vec_out, int* grid_out, int* sta
  * kernel of every step directly. */
 int flb_set_graphs(flb_ctx* ctx, int enable);
 
+/* Kernels flb_run has issued on this context so far (a library bookkeeping value,
+ * no counterpart in the paper): every kernel launched directly, and for a
+ * replayed CUDA graph the kernels captured in it.  count: host uint64_t. */
+int flb_kernel_launches(flb_ctx* ctx, uint64_t* count);
+
 /* Failure-detection check: launches on the context's stream one bounded
  * mbarrier wait that nothing completes (the wait the network step kernels use
  * for their MMAs and copies, here limited to limit_clocks SM clocks, 1 .. 2^32)

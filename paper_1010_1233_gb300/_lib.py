@@ -67,6 +67,7 @@ _SIGS = {
     "flb_get_network_engine": (c_int, [c_void_p, POINTER(c_int)]),
     "flb_autotune": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     "flb_set_graphs": (c_int, [c_void_p, c_int]),
+    "flb_kernel_launches": (c_int, [c_void_p, POINTER(c_uint64)]),
     "flb_probe_wait_timeout": (c_int, [c_void_p, c_uint64]),
     "flb_debug_bounds": (c_int, [POINTER(c_uint64), POINTER(c_uint32), c_int]),
     "flb_destroy": (None, [c_void_p]),

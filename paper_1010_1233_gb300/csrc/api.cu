@@ -578,7 +578,10 @@ struct flb_ctx {
   int net_engine = FLB_NET_WARP;   // network of the direct D2Q9 kernels
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
-  struct Graph { uint32_t len, every; cudaGraphExec_t exec; };
+  struct Graph { uint32_t len, every; cudaGraphExec_t exec; uint64_t kernels; };
+  uint64_t launches = 0;      // kernels flb_run has issued (a replayed graph counts its kernels)
+  bool capturing = false;     // issue_step / flush_samples are being captured into a graph
+  uint64_t captured = 0;      // kernels in the graph being captured
   std::vector<Graph> graphs;
   std::vector<float> mlp_host;
   TimeCorr tc;                                 // time correlators (off: tc.base == nullptr)
@@ -917,6 +920,14 @@ int flb_create(int precision, const flb_replica* reps, int n_replicas, void* dev
 
 // Issue one step (and its sampling) on stream st.  With S.step_dev set, S.step is the
 // offset from the device step counter (graph capture); otherwise the absolute step.
+// kernels issued on behalf of flb_run: counted, or, during a capture, added to the graph's count
+static void count_kernels(flb_ctx* c, uint64_t n) {
+  if (c->capturing) c->captured += n;
+  else c->launches += n;
+}
+// launches of a multi-path pass: one per bit of the path mask (FP64: the one kernel)
+static int path_launches(int precision, int paths) { return precision == FLB_FP64 ? 1 : __builtin_popcount(paths); }
+
 static void launch_step_any(flb_ctx* c, int vec, int staged, const StepLaunch& S, bool sample, cudaStream_t st) {
   if (is3d(c->lattice)) launch_step3(c->L.q, c->precision, vec, S, sample, st);
   else if (staged) launch_step_bulk(vec, S, sample, c->mlp_on, st);
@@ -932,11 +943,13 @@ static void flush_samples(flb_ctx* c, const StepLaunch& S, cudaStream_t st) {
   launch_fft_cols(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols), c->n,
                   L.n_vb_cols, c->ws, L.ncol, cols_grid, kColsBlock, L.cols_smem, st, c->tc, L.cols_paths,
                   c->pending, L.max_fields);
+  count_kernels(c, path_launches(c->precision, L.cols_paths));
   c->pending = 0;
   if (c->tc.base) {
     int maxF = 0;
     for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
     launch_time_corr(S.descs, c->n, maxF, c->tc, st);
+    count_kernels(c, 2);
   }
 }
 
@@ -944,6 +957,7 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
   NvtxRange range(sample ? "flb step + sample" : "flb step");
   const Layout& L = c->L;
   launch_step_any(c, L.vec, L.staged, S, sample, st);
+  count_kernels(c, 1);
   if (sample && is3d(c->lattice)) {
     // direct transforms at the chosen wave vectors, then the time correlators
     if (c->tc.base) {
@@ -951,6 +965,7 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
       for (const ReplicaDesc& d : L.desc) maxF = std::max(maxF, (int)d.n_fields);
       launch_point_dft(c->precision, S.descs, c->n, maxF * c->tc.n_k, c->ws, c->tc, c->tc_smem, st);
       launch_time_corr(S.descs, c->n, maxF, c->tc, st);
+      count_kernels(c, 4);              // point transforms, their finishing pass, lagged products, ring advance
     }
   } else if (sample) {
     // the row and inner column transforms into the free spectrum slot; the accumulation
@@ -966,6 +981,8 @@ static void issue_step(flb_ctx* c, StepLaunch& S, bool sample, cudaStream_t st) 
       launch_fft_cols_a(c->precision, S.descs, reinterpret_cast<const int64_t*>(c->ws + L.off_vb_cols_a), c->n,
                         L.n_vb_cols_a, c->ws, L.ncol, cols_a_grid, kColsBlock, L.cols_smem, st,
                         L.cols_a_paths, slot, c->sms);
+    count_kernels(c, path_launches(c->precision, L.rows_paths) +
+                         (L.n_vb_cols_a ? path_launches(c->precision, L.cols_a_paths) : 0));
     c->pending = slot + 1;
     if (!fold || c->pending == 2) flush_samples(c, S, st);
   }
@@ -1000,9 +1017,9 @@ static void drop_graphs(flb_ctx* c) {
 // A chunk of `len` steps starting at a step that is a multiple of len, sampling at its
 // steps o with o % every == 0 (every = 0: no sampling; len is a multiple of every); it
 // ends by advancing the device step counter by len.
-static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t* out) {
+static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t* out, uint64_t* kernels) {
   for (auto& g : c->graphs)
-    if (g.len == len && g.every == every) { *out = g.exec; return FLB_OK; }
+    if (g.len == len && g.every == every) { *out = g.exec; *kernels = g.kernels; return FLB_OK; }
   if (!c->cap_stream) {
     int rc = cuda_check(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
     if (rc) return rc;
@@ -1011,12 +1028,16 @@ static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t
   S.step_dev = reinterpret_cast<const uint64_t*>(c->ws + c->L.off_stepdev);
   int rc = cuda_check(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc) return rc;
+  c->capturing = true;
+  c->captured = 0;
   for (uint32_t o = 0; o < len; ++o) {
     S.step = o;
     issue_step(c, S, every && o % every == 0, c->cap_stream);
   }
   flush_samples(c, S, c->cap_stream);           // a chunk leaves no sample waiting
   launch_advance_step(reinterpret_cast<uint64_t*>(c->ws + c->L.off_stepdev), len, c->cap_stream);
+  count_kernels(c, 1);
+  c->capturing = false;
   cudaGraph_t graph = nullptr;
   rc = cuda_check(cudaStreamEndCapture(c->cap_stream, &graph), "end capture");
   if (rc) return rc;
@@ -1024,7 +1045,8 @@ static int chunk_graph(flb_ctx* c, uint32_t len, uint32_t every, cudaGraphExec_t
   rc = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "instantiate graph");
   cudaGraphDestroy(graph);
   if (rc) return rc;
-  c->graphs.push_back({len, every, exec});
+  c->graphs.push_back({len, every, exec, c->captured});
+  *kernels = c->captured;
   *out = exec;
   return FLB_OK;
 }
@@ -1043,6 +1065,7 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
       int rc = cuda_check(launch_d1q3_fused(c->precision, descs_dev(c), c->n, c->ws, c->step, n, every,
                                             c->fused_smem, c->stream), "fused D1Q3 launch");
       if (rc) return rc;
+      count_kernels(c, 1);
       if (every) {               // samples at the steps t in [step, step + n) with t % every == 0
         const uint64_t first = (c->step + every - 1) / every * every;
         if (first < c->step + n) c->n_samples += (c->step + n - 1 - first) / every + 1;
@@ -1078,9 +1101,11 @@ int flb_run(flb_ctx* c, uint64_t n_steps, uint32_t sample_every) {
     if (chunks) {
       flush_samples(c, S, c->stream);            // the chunks start with no sample waiting
       cudaGraphExec_t exec = nullptr;
-      int rc = chunk_graph(c, len, every, &exec);
+      uint64_t per_chunk_kernels = 0;
+      int rc = chunk_graph(c, len, every, &exec, &per_chunk_kernels);
       if (rc) return rc;
       launch_set_step(reinterpret_cast<uint64_t*>(c->ws + L.off_stepdev), c->step, c->stream);
+      count_kernels(c, 1 + chunks * per_chunk_kernels);
       NvtxRange chunks_range(sampling ? "flb graph chunks (sampling)" : "flb graph chunks");
       for (uint64_t k = 0; k < chunks; ++k) {
         rc = cuda_check(cudaGraphLaunch(exec, c->stream), "graph launch");
@@ -1102,6 +1127,12 @@ int flb_probe_wait_timeout(flb_ctx* c, uint64_t limit_clocks) {
     return set_error(FLB_EINVAL, "limit_clocks must be in 1 .. 2^32");
   launch_wait_probe(status_dev(c), (long long)limit_clocks, c->stream);
   return cuda_check(cudaGetLastError(), "wait probe launch");
+}
+
+int flb_kernel_launches(flb_ctx* c, uint64_t* count) {
+  if (!c || !count) return set_error(FLB_EINVAL, "NULL argument");
+  *count = c->launches;
+  return FLB_OK;
 }
 
 int flb_set_graphs(flb_ctx* c, int enable) {

@@ -225,6 +225,12 @@ class Sim:
         L.check(L.lib().flb_get_network_engine(self._ctx, ctypes.byref(e)))
         return "tcgen05" if e.value == L.FLB_NET_TCGEN05 else "warp"
 
+    def kernel_launches(self):
+        """Kernels flb_run has issued on this context (replayed graphs count their kernels)."""
+        n = ctypes.c_uint64()
+        L.check(L.lib().flb_kernel_launches(self._ctx, ctypes.byref(n)))
+        return int(n.value)
+
     def set_graphs(self, enable=True):
         L.check(L.lib().flb_set_graphs(self._ctx, int(bool(enable))))
 

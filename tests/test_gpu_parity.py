@@ -158,6 +158,27 @@ def test_folded_samples_equal_single_sample_passes(nx, ny):
     b.close()
 
 
+def test_kernel_launch_count():
+    # flb_kernel_launches (the count bench.py reports as gpu_launches) against the schedule
+    # flb_run follows: one step kernel per step; per sample the row transform (16-point rows:
+    # the shared-memory kernel) and, every second sample and at the end of a run, one
+    # accumulation pass (16-point columns: the register-resident kernel, two samples folded)
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8), kT=1e-4, seed=3, init_mode=1,
+                  fields=(0, W.FIELD_UX, W.FIELD_UY))
+    sim = Sim(p, precision="fp32")
+    sim.set_graphs(False)
+    n0 = sim.kernel_launches()
+    sim.run(3, 1)                          # 3 steps, 3 row passes, accumulations after samples 2 and 3
+    assert sim.kernel_launches() - n0 == 3 + 3 + 2
+    sim.set_graphs(True)
+    n0 = sim.kernel_launches()
+    sim.run(64, 1)                         # from step 3: 29 direct steps, then a 32-step chunk
+    direct = 29 + 29 + 15                  # steps, row passes, the (29 + 1) / 2 accumulations
+    chunk = 32 + 32 + 16 + 1               # steps, row passes, accumulations, step-counter advance
+    assert sim.kernel_launches() - n0 == direct + 1 + chunk + 3 + 3 + 2
+    sim.close()
+
+
 # ---------------------------------------------------------------------------- batching, checkpoint
 def test_batched_replicas_equal_single():
     # a batched launch runs each replica exactly as a launch of that replica alone: the
