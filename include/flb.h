@@ -195,7 +195,9 @@ int flb_get_step(flb_ctx* ctx, uint64_t* step_out);
 int flb_set_mlp(flb_ctx* ctx, const uint16_t* w_bf16, const float* biases, int enable);
 
 /* Checkpoint: the state is the populations, the step counter and the
- * correlator sums.  flb_save with host_buf = NULL reports the size. */
+ * correlator sums.  flb_save with host_buf = NULL reports the size.  Both
+ * calls return when the copies are complete (host_buf: host memory, pinned
+ * for full copy speed; the copies run as 64 MiB pieces on four streams). */
 int flb_save(flb_ctx* ctx, void* host_buf, size_t* bytes_inout);
 int flb_load(flb_ctx* ctx, const void* host_buf, size_t bytes);
 

@@ -578,6 +578,7 @@ struct flb_ctx {
   int net_engine = FLB_NET_WARP;   // network of the direct D2Q9 kernels
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t copy_streams[4] = {nullptr, nullptr, nullptr, nullptr};   // checkpoint copies
   struct Graph { uint32_t len, every; cudaGraphExec_t exec; uint64_t kernels; };
   uint64_t launches = 0;      // kernels flb_run has issued (a replayed graph counts its kernels)
   bool capturing = false;     // issue_step / flush_samples are being captured into a graph
@@ -1354,6 +1355,33 @@ int flb_set_mlp(flb_ctx* c, const uint16_t* w_bf16, const float* biases, int ena
   return FLB_OK;
 }
 
+// Checkpoint copies between host memory and the workspace: the regions are cut into
+// 64 MiB pieces issued round-robin on four streams (one cudaMemcpyAsync each), so that
+// several copy engines work at once, then all four streams are waited for.
+struct CopyStripe {
+  static constexpr size_t kPiece = 64ull << 20;
+  flb_ctx* c;
+  int next = 0;
+  int rc = FLB_OK;
+  void copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    for (size_t o = 0; o < bytes && rc == FLB_OK; o += kPiece) {
+      cudaStream_t& s = c->copy_streams[next];
+      next = (next + 1) % 4;
+      if (!s && (rc = cuda_check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "copy stream"))) return;
+      rc = cuda_check(cudaMemcpyAsync(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o,
+                                      std::min(kPiece, bytes - o), kind, s), "checkpoint copy");
+    }
+  }
+  int finish() {
+    for (cudaStream_t s : c->copy_streams) {
+      if (!s) continue;
+      const int e = cuda_check(cudaStreamSynchronize(s), "checkpoint copy");
+      if (!rc) rc = e;
+    }
+    return rc;
+  }
+};
+
 int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
   NvtxRange range("flb_save");
   if (!c || !bytes_inout) return set_error(FLB_EINVAL, "NULL argument");
@@ -1373,19 +1401,20 @@ int flb_save(flb_ctx* c, void* host_buf, size_t* bytes_inout) {
                      (uint64_t)need, (uint64_t)c->lattice, 0};
   memcpy(p, hdr, 64);
   p += 64;
+  CopyStripe cs{c};
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
     const size_t pb = d.q * (size_t)volume(d) * rs;
-    rc = cuda_check(cudaMemcpy(p, c->ws + d.off_pop[c->step & 1], pb, cudaMemcpyDeviceToHost), "save");
-    if (rc) return rc;
+    cs.copy(p, c->ws + d.off_pop[c->step & 1], pb, cudaMemcpyDeviceToHost);
     p += pb;
     if (d.n_pairs) {
       const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
-      rc = cuda_check(cudaMemcpy(p, c->ws + d.pair_off[0], ab, cudaMemcpyDeviceToHost), "save");
-      if (rc) return rc;
+      cs.copy(p, c->ws + d.pair_off[0], ab, cudaMemcpyDeviceToHost);
       p += ab;
     }
   }
+  rc = cs.finish();
+  if (rc) return rc;
   *bytes_inout = need;
   return FLB_OK;
 }
@@ -1408,19 +1437,20 @@ int flb_load(flb_ctx* c, const void* host_buf, size_t bytes) {
   p += 64;
   const uint64_t step = hdr[3];
   const int64_t rs = c->precision == FLB_FP64 ? 8 : 4;
+  CopyStripe cs{c};
   for (int r = 0; r < c->n; ++r) {
     const ReplicaDesc& d = c->L.desc[r];
     const size_t pb = d.q * (size_t)volume(d) * rs;
-    rc = cuda_check(cudaMemcpy(c->ws + d.off_pop[step & 1], p, pb, cudaMemcpyHostToDevice), "load");
-    if (rc) return rc;
+    cs.copy(c->ws + d.off_pop[step & 1], p, pb, cudaMemcpyHostToDevice);
     p += pb;
     if (d.n_pairs) {
       const size_t ab = (size_t)(d.off_mean0 + 8 * d.n_fields - d.pair_off[0]);
-      rc = cuda_check(cudaMemcpy(c->ws + d.pair_off[0], p, ab, cudaMemcpyHostToDevice), "load");
-      if (rc) return rc;
+      cs.copy(c->ws + d.pair_off[0], p, ab, cudaMemcpyHostToDevice);
       p += ab;
     }
   }
+  rc = cs.finish();
+  if (rc) return rc;
   c->step = step;
   c->n_samples = hdr[4];
   return FLB_OK;
@@ -1589,6 +1619,8 @@ void flb_destroy(flb_ctx* c) {
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t s : c->copy_streams)
+    if (s) cudaStreamDestroy(s);
   delete c;
 }
 
