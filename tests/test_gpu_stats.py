@@ -33,9 +33,14 @@ def measure(p, precision, batches, steps, warmup, every=1):
     return {pr: (np.mean(v, 0), np.std(v, 0, ddof=1) / np.sqrt(len(v))) for pr, v in out.items()}
 
 
-def compare(p, meas, floor=2e-3):
+def compare(p, meas, floor=1e-9, also_exclude=()):
+    # z = |measured - theory| / standard error of the batch means; the floor only guards
+    # against a zero standard error.  also_exclude: further neutral modes (ky, kx)
     P = lb.Params(**p)
     S, ex = theory.theory_spectra(P, p["fields"])
+    ex = ex.copy()
+    for ky, kx in also_exclude:
+        ex[ky, kx] = True
     zmax, dmax = 0.0, 0.0
     for pr, (m, se) in meas.items():
         d = np.abs(m - S[pr])[~ex]
@@ -58,7 +63,11 @@ def test_ladd_spectra():
     p = W.replica("D2Q9", 16, 16, W.taus_d2q9(1.0), kT=1e-4, seed=8, noise_mask=LADD,
                   fields=(0, W.FIELD_UX, W.FIELD_UY))
     meas = measure(p, "fp32", 20, 20000, 2000)
-    zmax, dmax, S, ex = compare(p, meas)
+    # Without ghost noise k = (pi, pi) is neutral too: the lattice divergence of the
+    # stress noise vanishes there (sin pi = 0) and nothing damps the checkerboard momentum,
+    # so the velocity keeps its initial amplitude (a constant |u|^2 ~ 1e-4 with a batch
+    # error ~ 2e-7) while the stationary theory gives 0
+    zmax, dmax, S, ex = compare(p, meas, also_exclude=[(8, 8)])
     rmax = np.abs(meas[(9, 10)][0])[~ex].max()
     print(f"Ladd: max |S - theory| = {dmax:.4f}, max z = {zmax:.2f}, max |R_xy| = {rmax:.3f}")
     assert zmax < 5.0
