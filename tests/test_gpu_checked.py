@@ -5,8 +5,10 @@ index checked (-DFLB_CHECK_BOUNDS: a violation is counted and the access skipped
 never trapped), and a child process runs small and ragged cases through it against
 the FP64 oracle: D2Q9 FP64 and FP32 at 8^2 .. 16^2 with sampling, rows of 10 and 14
 sites (vec 1 and 2), a single-row lattice, both network engines at vec 1/2/4,
-uneven batched replicas, the four-step column transform, D1Q3 (fused and per step)
-and D3Q15 / D3Q19 boxes with time correlators.  Every case must match the oracle and
+uneven batched replicas, the four-step column transform, the Stockham row pass with
+the column-tiled spectrum (a 4096 x 64 lattice, and the standalone sampler on a 4096^2
+field at sampled wave vectors), D1Q3 (fused and per step) and D3Q15 / D3Q19 boxes
+with time correlators.  Every case must match the oracle and
 the run must end with zero violations.
 """
 import json
@@ -77,6 +79,24 @@ for eng in ("warp", "tcgen05"):
 d2q9("fourstep_8x4096", W.replica("D2Q9", 8, 4096, W.taus_d2q9(0.7, 0.8, 1.2), kT=1e-3, u0=(0.05, 0.1), seed=31,
      init_mode=1, fields=F3), "fp32", 4, 2, 2e-4)
 
+# the Stockham row pass (rows of 4096) with column-tiled spectra, one-pass columns of 64
+d2q9("rows16_4096x64", W.replica("D2Q9", 4096, 64, W.taus_d2q9(0.7, 0.8, 1.2), kT=1e-3, u0=(0.05, 0.1), seed=33,
+     init_mode=1, fields=F3), "fp32", 3, 1, 2e-4)
+
+# the standalone sampler on a 4096^2 field: Stockham rows, tiled spectrum, both
+# register-resident four-step passes (64 x 64), checked at sampled wave vectors
+import torch
+from paper_1010_1233_gb300.sim import spectra_accumulate, unpack_pair_sums
+x = W.random_perturbation((1, 4096, 4096), 44) + 0.3
+sums, mean0 = spectra_accumulate(torch.tensor(x, dtype=torch.float32, device="cuda"))
+g = unpack_pair_sums(sums, 1, 4096, 4096)[(0, 0)]
+xr = np.asarray(torch.tensor(x, dtype=torch.float32).double())[0]
+err = 0.0
+for ky, kx in [(0, 0), (1, 1), (4095, 2048), (2048, 1024), (3, 5), (1234, 777)]:
+    want = abs(spectra.dft_at(xr, kx, ky)) ** 2
+    err = max(err, abs(g[ky, kx] - want) / max(want, 1.0))
+out["spectra_4096sq"] = dict(err=err, ok=bool(err < 1e-4), viol=viol())
+
 # uneven batched replicas against single-replica oracle runs
 reps = [W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8), kT=1e-4, seed=1, stream=1, init_mode=1, fields=F3),
         W.replica("D2Q9", 8, 8, W.taus_d2q9(0.9), kT=1e-4, u0=(0.1, 0), seed=2, stream=2, init_mode=1, fields=F3)]
@@ -126,4 +146,4 @@ def test_checked_build_matches_oracle_without_violations():
     res = json.loads(r.stdout.strip().splitlines()[-1])
     bad = {k: v for k, v in res.items() if not v["ok"] or v["viol"][0] != 0}
     assert not bad, bad
-    assert len(res) >= 16
+    assert len(res) >= 18
