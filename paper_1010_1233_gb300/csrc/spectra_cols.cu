@@ -274,6 +274,9 @@ k_fft_cols_a16(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict_
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Pass 2b (N2 = L): one block per (replica, k1, tile of ncol columns), all fields and
+// the nslots samples of the tile; four blocks per SM (measured against three, with 80
+// registers and no spills: 10.08 against 10.50 ms per 16384^2 sample).
 #ifndef FLB_ACC16_MIN_BLOCKS
 #define FLB_ACC16_MIN_BLOCKS 4
 #endif
