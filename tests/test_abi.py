@@ -149,3 +149,10 @@ def test_bounds_counters_only_in_the_checked_build(lib):
     assert lib.flb_debug_bounds(ctypes.byref(n), ctypes.byref(site), 1) == L.FLB_ESTATE
     assert n.value == 0 and site.value == 0
     assert b"--checked" in lib.flb_last_error()
+
+
+def test_kernel_launch_query_validates(lib):
+    # the launch count is read from the context; NULL arguments are rejected on the host
+    n = ctypes.c_uint64(5)
+    assert lib.flb_kernel_launches(None, ctypes.byref(n)) == L.FLB_EINVAL
+    assert n.value == 5
