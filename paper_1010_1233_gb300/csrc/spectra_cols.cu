@@ -1,10 +1,11 @@
 // Column passes of the correlator sampling (Eqs. 11-12) in FP32 for column transforms
 // of length L = 16 B (B = 1, 2, 4, 8, 16): register-resident counterparts of
-// k_fft_cols_a and k_fft_cols_acc (spectra.cu) with the same tiles, the same in-place
-// spectrum and the same pair sums.  One kernel per B; each takes the blocks of the
-// replicas whose columns have its length and skips the others (which the kernel of
-// their own length, or the shared-memory kernel, takes), so a replica's results do not
-// depend on the batch it runs in.
+// k_fft_cols_a and k_fft_cols_acc (spectra.cu), on the same spectrum (in either of its
+// layouts, spec_index) and the same pair sums; pass 2b keeps their tiles, pass 2a takes
+// tiles of one field.  One kernel per B; each takes the blocks of the replicas whose
+// columns have its length and skips the others (which the kernel of their own length,
+// or the shared-memory kernel, takes), so a replica's results do not depend on the
+// batch it runs in.
 //
 // Element n = r + B j of a length-L sequence (r < B, j < 16) is loaded by thread r of
 // the sequence.  With k = q + 16 p (q < 16, p < B),

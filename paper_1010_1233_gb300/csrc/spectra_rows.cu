@@ -10,9 +10,11 @@
 // over r in registers (fft_reg.cuh) and writes S((j - j mod Ns) R + j mod Ns + r Ns).
 // Passes of R = 16, then one of 2, 4 or 8 for the remaining factor.  A work item reads
 // the twiddle table four times (W^e, W^2e, W^4e, W^8e) and forms the other powers by
-// complex products.  M / 16 threads, 16 values each; every pass reads all its values before the barrier and writes after it,
-// so one buffer serves (element i at i + i / 16, which keeps the stride-16 writes of
-// the first pass off a single bank).  The first pass reads the row from global memory.
+// complex products.  M / 16 threads, 16 values each; every pass reads all its values
+// before the barrier and writes after it, so one buffer serves (element i at i + i / 16,
+// which keeps the stride-16 writes of the first pass off a single bank).  The first
+// pass reads the row from global memory; the split writes the half spectrum in the
+// replica's spectrum layout (spec_index).
 #include "fft_reg.cuh"
 
 namespace flb {
