@@ -99,3 +99,26 @@ def test_time_correlators_match_theory():
             worst = max(worst, (np.abs(part(m) - part(F[pr])) / np.maximum(se, 2e-3)).max())
     print(f"time correlators vs theory: max z = {worst:.2f}")
     assert worst < 5.0
+
+
+def test_kernel_launch_count_with_time_correlators():
+    # flb_kernel_launches with time correlators, which take every sample on its own: per
+    # sample the row transform, the column pass with the pair sums and the ring entries,
+    # the lagged products and the ring advance (D2Q9); the direct transforms at the wave
+    # vectors, their finishing pass, the lagged products and the ring advance (D3Q15)
+    p = W.replica("D2Q9", 16, 16, W.taus_d2q9(0.8), kT=1e-4, seed=3, init_mode=1, fields=(0, W.FIELD_UX))
+    sim = Sim(p, precision="fp32")
+    sim.set_graphs(False)
+    sim.set_time_correlator([(1, 2), (3, 0)], 2)
+    n0 = sim.kernel_launches()
+    sim.run(3, 1)
+    assert sim.kernel_launches() - n0 == 3 + 3 * (1 + 1 + 2)
+    sim.close()
+    q = W.replica3(8, 6, 4, W.taus_d3q15(0.8), kT=1e-4, seed=3, init_mode=1, fields=(0, 4))
+    sim = Sim(q, precision="fp32")
+    sim.set_graphs(False)
+    sim.set_time_correlator([(0, 0, 1), (1, 2, 3)], 2)
+    n0 = sim.kernel_launches()
+    sim.run(3, 1)
+    assert sim.kernel_launches() - n0 == 3 + 3 * 4
+    sim.close()
