@@ -217,9 +217,10 @@ constexpr int kColsGeneric = 32;
 // The FP32 row pass of spectra_rows.cu (one real row per block, Stockham radix-16) for
 // nx = 4096 .. 32768; the shared-memory radix-2 pass of spectra.cu (two rows per block)
 // otherwise.  Virtual blocks of the row pass of a replica:
-inline bool rows16(int precision, int nx) {
-  return precision != FLB_FP64 && nx >= 4096 && nx <= 32768 && (nx & (nx - 1)) == 0;
+__host__ __device__ __forceinline__ bool rows16_nx(int nx) {
+  return nx >= 4096 && nx <= 32768 && (nx & (nx - 1)) == 0;
 }
+inline bool rows16(int precision, int nx) { return precision != FLB_FP64 && rows16_nx(nx); }
 inline int64_t rows_blocks(int precision, int nx, int n_fields, int ny) {
   return rows16(precision, nx) ? (int64_t)n_fields * ny : ((int64_t)n_fields * ny + 1) / 2;
 }

@@ -28,7 +28,7 @@ k_fft_rows(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ vb
   for (int64_t vb = blockIdx.x; vb < n_vblocks; vb += gridDim.x) {
     const int r = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[r];
-    if (sizeof(R) == 4 && d.nx >= 4096 && d.nx <= 32768) continue;   // k_fft_rows16's row
+    if (sizeof(R) == 4 && rows16_nx(d.nx)) continue;   // k_fft_rows16's row
     // block vb packs the row units u = 2 local and u + 1 (unit u: field u / ny, row u % ny;
     // ny is a power of two), so an odd field count leaves at most one half-empty transform
     const int64_t ua = 2 * (vb - vb_begin[r]), ub = ua + 1;

@@ -88,7 +88,7 @@ k_fft_rows16(const ReplicaDesc* __restrict__ descs, const int64_t* __restrict__ 
     const int rp = find_rep(vb_begin, n_reps, vb);
     const ReplicaDesc& d = descs[rp];
     const int nx = d.nx, M = nx >> 1;
-    if (nx < 4096 || nx > 32768 || (M >> 4) != (int)blockDim.x) continue;   // the other row kernel's
+    if (!rows16_nx(nx) || (M >> 4) != (int)blockDim.x) continue;   // another launch's row
     const int64_t u = vb - vb_begin[rp];
     const int f = (int)(u >> d.log2ny), y = (int)(u & (d.ny - 1));
     if (!FLB_INB(f < (int)d.n_fields, 222)) continue;
