@@ -49,7 +49,7 @@ FALLBACK_HBM_GBS = 6800.0
 # profiles/k_step_d2q9_wn_fp32_mlp_4096.md: the warp engine, vec 4); None for any
 # other configuration.
 TRAFFIC_PER_SITE = {("tcgen05", 2, 0): (604123904 + 560039168) / 4096**2,
-                    ("warp", 4, 0): (604061696 + 555133952) / 4096**2}
+                    ("warp", 4, 0): (604215808 + 554892800) / 4096**2}
 KERNEL_NAME = {"warp": "k_step_d2q9_wn (fused pull-stream/collide/noise, network on warp-level tensor-core MMAs)",
                "tcgen05": "k_step_d2q9_tc (fused pull-stream/collide/noise, network on tcgen05)"}
 # The same for the 3D step kernels (k_step_3d, one replica, tuned vec) from ncu captures at
