@@ -324,7 +324,7 @@ int fft_cols_smem(int precision, int F, int ny, int ncol) { return (F * (ny + 1)
 cudaError_t set_fft_smem_limits() {
   cudaError_t e;
   const int maxb = 227 * 1024;
-  // the transforms want shared memory, not L1 (a preference; the driver may round it)
+  // the transforms want shared memory, not L1 (a preference the CUDA runtime rounds to a supported split)
   const int carve = (int)cudaSharedmemCarveoutMaxShared;
   if ((e = cudaFuncSetAttribute(k_fft_rows<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
   if ((e = cudaFuncSetAttribute(k_fft_cols_a<float>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
