@@ -49,3 +49,28 @@ def test_gpu_id_follows_visible_devices(monkeypatch):
     assert b.gpu_id(0) == "5"
     monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
     assert b.gpu_id(0) == "0"
+
+
+def _dram_bytes(profile):
+    """(read, write) DRAM bytes of each capture recorded in a committed ncu summary, in
+    the order the file lists them."""
+    import re
+    units = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    text = open(os.path.join(ROOT, "profiles", profile)).read()
+    rows = re.findall(r"\| `dram__bytes_(read|write)\.sum` \| (\w+) \| ([\d.]+) \|", text)
+    vals = [float(v) * units[u] for _, u, v in rows]
+    assert [k for k, _, _ in rows] == ["read", "write"] * (len(rows) // 2)
+    return list(zip(vals[0::2], vals[1::2]))
+
+
+def test_traffic_tables_match_the_profiles():
+    # the roofline's `traffic` field comes from bench.py's per-site tables; each entry is
+    # a committed capture's DRAM bytes divided by the sites of the captured launch
+    b = _bench()
+    (rd, wr), = _dram_bytes("k_step_d2q9_wn_fp32_mlp_4096.md")
+    assert abs(b.TRAFFIC_PER_SITE[("warp", 4, 0)] * 4096**2 - (rd + wr)) < 1.0
+    (rd, wr), = _dram_bytes("k_step_d2q9_tc_fp32_mlp_4096.md")
+    assert abs(b.TRAFFIC_PER_SITE[("tcgen05", 2, 0)] * 4096**2 - (rd + wr)) < 1.0
+    (r15, w15), (r19, w19) = _dram_bytes("k_step_3d_fp32_256.md")
+    assert abs(b.TRAFFIC_PER_SITE_3D[("d3q15_512", 4)] * 256**3 - (r15 + w15)) < 1.0
+    assert abs(b.TRAFFIC_PER_SITE_3D[("d3q19_512", 2)] * 256**3 - (r19 + w19)) < 1.0
