@@ -156,3 +156,23 @@ def test_kernel_launch_query_validates(lib):
     n = ctypes.c_uint64(5)
     assert lib.flb_kernel_launches(None, ctypes.byref(n)) == L.FLB_EINVAL
     assert n.value == 5
+
+
+def test_bench_workload_workspace(lib):
+    # HBM layout of the 16384^2 D2Q9 workload (FP32 deviations, rho/u_x/u_y sampled):
+    # two population buffers, the fields, two spectrum slots (two samples folded into one
+    # accumulation pass) in the column-tiled layout [F][ceil((nx/2+1)/16)][ny][16], and the
+    # FP64 pair sums (3 autos x 8 B + 3 cross pairs x 16 B per k point) over the half
+    # spectrum padded to the 8-column accumulation tiles; the rest (descriptors, twiddle
+    # tables, k = 0 sums, alignment) stays below 1 MB.  38.7 GB of the GPU's 288.
+    N, F = 16384, 3
+    p = W.d2q9_16384(N)["replicas"][0]
+    rc, n = _ws([p])
+    pops, fields = 2 * 9 * 4 * N * N, F * 4 * N * N
+    spec_slot = F * -(-(N // 2 + 1) // 16) * N * 16 * 8
+    sums = 72 * N * (-(-(N // 2 + 1) // 8) * 8)
+    assert rc == 0
+    assert 0 <= n - (pops + fields + 2 * spec_slot + sums) < 1 << 20, n
+    q = dict(p, fields=())
+    rc, m = _ws([q])
+    assert rc == 0 and 0 <= m - pops < 1 << 20, m                  # no sampling: populations only
